@@ -1,0 +1,241 @@
+"""FP64 CPU oracle of the layered unified tomographic reconstruction (UTR).
+
+TEST INFRASTRUCTURE ONLY.  Plain, slow, written to be checked against the paper by
+eye.  Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import it; the reconstruction library
+never does, and this module shares no code with it.
+
+What it computes, in the paper's order and notation (Sec. 2):
+
+1. Contrast g_n = ln(I_n / I_in) (Eq. 4's left side), or the image as given.
+2. G_n = 2D DFT of g_n zero-padded to P x P (F2 with kernel exp(-i 2 pi r.q), Eq. 3).
+3. For each depth layer k of direction n, the real part of Eq. 11's bracket at the
+   layer's own defocus R_n - z_k (Eq. 5 and Eq. 7 place a slice at depth z at
+   defocus R - z; Eq. 13 is the single-layer case):
+       chi_k(q) = pi*lambda*(R_n - z_k)*q^2 + (pi/2)*Cs*lambda^3*q^4 - omega,
+       omega = atan(sigma)                                         (Eq. 7)
+       H_k(q)   = lambda / (4 pi sqrt(1+sigma^2)) * sin chi / (sin^2 chi + eps)
+   The Cs term is the per-view aberration that Sec. 2 allows in the sine argument.
+4. The sampling-density weight of a single-axis scan, the ramp |q_x| (Sec. 2),
+   discretised as the band-limited Ram-Lak kernel and scaled by pi/D.
+5. Y_{n,k} = crop( Re IDFT[ G_n * H_k * W ] ): the layer stack.
+6. Backprojection: every voxel takes, from each direction, a bilinear sample of the
+   layer that contains its depth, and sums over directions.
+
+Readings where the paper is silent (each is listed in the design notes):
+* layers are Nz equal slabs over the volume's bounding-box extent along the beam,
+  centred on the rotation centre; the layer index is decided in 2^-24 fixed point
+  (``layer_constants``), so that every implementation takes the same decision;
+* P = smallest power of two >= 2*max(nu, nv), zero padding;
+* pixel and voxel centres at (index - (n-1)/2) * delta; bilinear, zero outside the
+  detector; nearest (containing) layer;
+* intensities are floored at 1e-6 before the logarithm.
+
+Every function states the passage it follows.  Pins (tests marked ``not gpu``) tie
+each step to closed forms, brute force and invariants; none re-types these
+formulas.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+INTENSITY_FLOOR = 1e-6
+LAYER_FRAC_BITS = 24
+
+FILTER_OFF = 0
+FILTER_TIKHONOV = 1
+INPUT_INTENSITY = 0
+INPUT_CONTRAST = 1
+
+
+def padded_size(n: int) -> int:
+    """Smallest power of two >= 2n (zero padding so that the circular filters act as
+    linear ones on the n-pixel field of view)."""
+    p = 1
+    while p < 2 * n:
+        p *= 2
+    return p
+
+
+def signed_freq(P: int) -> np.ndarray:
+    """DFT bin index -> signed integer frequency m in [-P/2, P/2)."""
+    m = np.arange(P)
+    return np.where(m < P // 2, m, m - P)
+
+
+# ----------------------------------------------------------------------------- geometry
+def pixel_coefficients(rot: np.ndarray, grid, nu: int, nv: int) -> tuple[np.ndarray, np.ndarray]:
+    """Affine maps voxel index -> detector pixel coordinate, a = A . (i, j, k, 1) and
+    b = B . (i, j, k, 1), from the beam-frame position Rot_n (r - centre) (the
+    plane-wave projection geometry of Sec. 2, any orientation)."""
+    nx, ny, nz = grid
+    c = np.array([(nx - 1) / 2.0, (ny - 1) / 2.0, (nz - 1) / 2.0])
+    A = np.zeros((rot.shape[0], 4))
+    B = np.zeros((rot.shape[0], 4))
+    A[:, :3] = rot[:, 0, :]
+    B[:, :3] = rot[:, 1, :]
+    A[:, 3] = (nu - 1) / 2.0 - rot[:, 0, :] @ c
+    B[:, 3] = (nv - 1) / 2.0 - rot[:, 1, :] @ c
+    return A, B
+
+
+def depth_extent(rot: np.ndarray, grid) -> np.ndarray:
+    """Extent, in voxel lengths, of the volume's bounding box along each beam axis:
+    sum_i |d_n . e_i| * N_i."""
+    nx, ny, nz = grid
+    r2 = rot[:, 2, :]
+    return np.abs(r2[:, 0]) * nx + np.abs(r2[:, 1]) * ny + np.abs(r2[:, 2]) * nz
+
+
+def layer_centres(rot: np.ndarray, grid, nz_layers: int, delta: float) -> np.ndarray:
+    """Depth z_k of each layer centre (metres, beam frame, rotation centre at 0): the
+    slabs of Eq. 5 placed as Nz equal slabs over the bounding-box extent."""
+    ext = depth_extent(rot, grid) * delta
+    k = np.arange(nz_layers)
+    return -ext[:, None] / 2.0 + (k[None, :] + 0.5) * (ext[:, None] / nz_layers)
+
+
+def layer_constants(rot: np.ndarray, grid, nz_layers: int) -> np.ndarray:
+    """Fixed-point (2^-24 layer) coefficients (T0, Ti, Tj, Tk) per direction, int64.
+
+    t = (z' + T/2) / h in layer units is affine in the voxel index; its FP64
+    coefficients are rounded to the nearest multiple of 2^-24 (ties to even), and
+    the layer is floor(t) of the exact integer sum.  Written so that the operations
+    and their order are fixed: ext, scale, ti/tj/tk, t0 as below."""
+    nx, ny, nz = grid
+    r2 = rot[:, 2, :]
+    ext = (np.abs(r2[:, 0]) * float(nx) + np.abs(r2[:, 1]) * float(ny)) + np.abs(r2[:, 2]) * float(nz)
+    scale = float(nz_layers) / ext
+    ti = r2[:, 0] * scale
+    tj = r2[:, 1] * scale
+    tk = r2[:, 2] * scale
+    t0 = 0.5 * float(nz_layers) - ((ti * (0.5 * (nx - 1)) + tj * (0.5 * (ny - 1))) + tk * (0.5 * (nz - 1)))
+    one = float(1 << LAYER_FRAC_BITS)
+    return np.stack([np.rint(t0 * one), np.rint(ti * one), np.rint(tj * one), np.rint(tk * one)],
+                    axis=1).astype(np.int64)
+
+
+def layer_index(T: np.ndarray, nz_layers: int, i, j, k) -> np.ndarray:
+    """Layer of voxel (i, j, k) for one direction's constants ``T`` (exact integers)."""
+    t = T[0] + T[1] * np.asarray(i, np.int64) + T[2] * np.asarray(j, np.int64) + T[3] * np.asarray(k, np.int64)
+    return np.clip(t >> LAYER_FRAC_BITS, 0, nz_layers - 1)
+
+
+# ----------------------------------------------------------------------------- filters
+def ramp_weights(P: int, delta: float, n_dir: int) -> np.ndarray:
+    """W[m], m = DFT bin: (pi/D) * delta * DFT_P[h](m) with the band-limited Ram-Lak
+    kernel h[0] = 1/(4 delta^2), h[odd n] = -1/(n^2 pi^2 delta^2), h[even n != 0] = 0,
+    for n in [-P/2, P/2).  This discretises the ramp |q_x| that Sec. 2 identifies as
+    the sampling-matrix inverse of a 180-degree single-axis scan; pi/D is the
+    angular step of the backprojection sum."""
+    n = signed_freq(P)
+    h = np.zeros(P)
+    h[n == 0] = 1.0 / (4.0 * delta * delta)
+    odd = (n % 2) != 0
+    h[odd] = -1.0 / (n[odd].astype(np.float64) ** 2 * math.pi ** 2 * delta * delta)
+    return (math.pi / n_dir) * delta * np.fft.fft(h).real
+
+
+def ctf_filter(P: int, delta: float, lam: float, r_eff: float, sigma: float, eps: float,
+               cs: float = 0.0) -> np.ndarray:
+    """H(q) on the P x P DFT grid for one layer at effective defocus ``r_eff``:
+    lambda / (4 pi sqrt(1+sigma^2)) * sin(chi) / (sin(chi)^2 + eps), the real part of
+    the bracket of Eq. 11 with chi = pi*lambda*r_eff*q^2 + (pi/2)*Cs*lambda^3*q^4 - omega
+    (omega = atan sigma, Eq. 7).  With eps = 0 it is Eq. 13's inverse sine."""
+    m = signed_freq(P).astype(np.float64)
+    q2 = (m[None, :] ** 2 + m[:, None] ** 2) / (P * delta) ** 2
+    chi = math.pi * lam * r_eff * q2 + 0.5 * math.pi * cs * lam ** 3 * q2 * q2 - math.atan(sigma)
+    s = np.sin(chi)
+    return lam / (4.0 * math.pi * math.sqrt(1.0 + sigma * sigma)) * s / (s * s + eps)
+
+
+# ----------------------------------------------------------------------------- stage A
+def contrast(image: np.ndarray, input_mode: int) -> np.ndarray:
+    """g = ln(I/I_in) (left side of Eq. 4), intensities floored at 1e-6, or the image
+    itself when it already is a contrast or a projection."""
+    img = np.asarray(image, dtype=np.float64)
+    if input_mode == INPUT_INTENSITY:
+        return np.log(np.maximum(img, INTENSITY_FLOOR))
+    return img
+
+
+def layer_stack(image: np.ndarray, *, delta: float, lam: float, r_n: float, z_layers: np.ndarray,
+                n_dir: int, sigma: float, eps: float, cs: float, filt: int, input_mode: int) -> np.ndarray:
+    """Layer stack Y_k (k over ``z_layers``) of one image, float64 ``(Nz, nv, nu)``:
+    crop(Re IDFT[G * H_k * W]) with G the DFT of the zero-padded contrast, image
+    centred in the P x P frame."""
+    nv, nu = image.shape
+    P = padded_size(max(nu, nv))
+    ou, ov = (P - nu) // 2, (P - nv) // 2
+    g = np.zeros((P, P))
+    g[ov:ov + nv, ou:ou + nu] = contrast(image, input_mode)
+    G = np.fft.fft2(g)
+    W = ramp_weights(P, delta, n_dir)[None, :]
+    out = np.empty((len(z_layers), nv, nu))
+    for k, z in enumerate(z_layers):
+        F = W * ctf_filter(P, delta, lam, r_n - z, sigma, eps, cs) if filt == FILTER_TIKHONOV else W
+        out[k] = np.fft.ifft2(G * F).real[ov:ov + nv, ou:ou + nu]
+    return out
+
+
+# ----------------------------------------------------------------------------- stage B
+def bilinear(img: np.ndarray, a: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Bilinear sample of img[v][u] at (u, v) = (a, b), zero outside the detector."""
+    nv, nu = img.shape
+    a0 = np.floor(a).astype(np.int64)
+    b0 = np.floor(b).astype(np.int64)
+    fa = a - a0
+    fb = b - b0
+
+    def tap(ii, jj):
+        ok = (ii >= 0) & (ii < nu) & (jj >= 0) & (jj < nv)
+        return np.where(ok, img[np.clip(jj, 0, nv - 1), np.clip(ii, 0, nu - 1)], 0.0)
+
+    return ((1 - fb) * ((1 - fa) * tap(a0, b0) + fa * tap(a0 + 1, b0))
+            + fb * ((1 - fa) * tap(a0, b0 + 1) + fa * tap(a0 + 1, b0 + 1)))
+
+
+def backproject_direction(stack: np.ndarray, A: np.ndarray, B: np.ndarray, T: np.ndarray,
+                          i, j, k) -> np.ndarray:
+    """One direction's contribution to voxels (i, j, k): bilinear sample of the layer
+    containing each voxel's depth (the real-space counterpart of gridding onto the
+    direction's Ewald patch, Sec. 2)."""
+    nz_layers = stack.shape[0]
+    a = A[0] * i + A[1] * j + A[2] * k + A[3]
+    b = B[0] * i + B[1] * j + B[2] * k + B[3]
+    lay = layer_index(T, nz_layers, i, j, k)
+    out = np.zeros(np.shape(a))
+    for L in np.unique(lay):
+        sel = lay == L
+        out[sel] = bilinear(stack[L], a[sel], b[sel])
+    return out
+
+
+def recon(images, rot, *, lam: float, delta: float, defocus, nz_layers: int, grid, sigma: float = 0.0,
+          eps: float = 0.1, cs: float = 0.0, filt: int = FILTER_TIKHONOV, input_mode: int = INPUT_INTENSITY,
+          voxels=None) -> np.ndarray:
+    """The whole operator, FP64.  ``images`` (D, nv, nu); ``rot`` (D, 3, 3);
+    ``defocus`` (D,).  Returns vol[z][y][x] float64, or, when ``voxels = (i, j, k)``
+    index arrays are given, the values at those voxels only."""
+    images = np.asarray(images)
+    rot = np.asarray(rot, dtype=np.float64)
+    D, nv, nu = images.shape
+    nx, ny, nz = grid
+    if voxels is None:
+        kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        i, j, k = ii.ravel(), jj.ravel(), kk.ravel()
+    else:
+        i, j, k = (np.asarray(x, np.int64) for x in voxels)
+    A, B = pixel_coefficients(rot, grid, nu, nv)
+    T = layer_constants(rot, grid, nz_layers)
+    zc = layer_centres(rot, grid, nz_layers, delta)
+    acc = np.zeros(i.shape)
+    for n in range(D):
+        st = layer_stack(images[n], delta=delta, lam=lam, r_n=float(defocus[n]), z_layers=zc[n], n_dir=D,
+                         sigma=sigma, eps=eps, cs=cs, filt=filt, input_mode=input_mode)
+        acc += backproject_direction(st, A[n], B[n], T[n], i, j, k)
+    if voxels is None:
+        return acc.reshape(nz, ny, nx)
+    return acc

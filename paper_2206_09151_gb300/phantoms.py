@@ -1,0 +1,298 @@
+"""Seeded synthetic inputs: scan geometries, phantoms and simulated transmission images.
+
+This module draws every random number the workloads use and turns phantoms into
+images with a forward simulator. It holds none of the reconstruction's arithmetic
+(no CTF inversion, no ramp, no layering, no backprojection); the reconstruction
+library and the FP64 oracle both consume what it produces.
+
+Conventions (shared by the C-ABI, the oracle and this module):
+
+* Volume ``vol[z][y][x]``; voxel ``(i, j, k)`` has its centre at
+  ``((i-(nx-1)/2)*delta, (j-(ny-1)/2)*delta, (k-(nz-1)/2)*delta)``.
+* ``rot[n]`` is a 3x3 row-major rotation, volume frame -> beam frame: its rows are
+  the detector ``u`` axis, the detector ``v`` axis and the beam direction, each
+  written in volume coordinates.
+* Image ``img[n][v][u]``; pixel ``(u, v)`` sits at beam-frame
+  ``((u-(nu-1)/2)*delta, (v-(nv-1)/2)*delta)``.
+* Defocus ``R_n`` is the distance from the plane through the rotation centre to
+  the image plane, positive downstream (the reading of Sec. 3, where the image
+  planes lie downstream of the object).
+
+The simulator is a multislice model (Fig. 1(a)): the object is cut into thin slabs
+normal to the beam, each slab multiplies the wave by its transmission function
+exp(-a + i*phi) with phi = (2*pi/lambda) * int delta dz and a = sigma * phi (the
+monomorphous object of Sec. 2), and free space between slabs and on to the image
+plane is crossed with the Fresnel propagator of Eq. 3, exp(-i*pi*lambda*R*q^2),
+optionally with a spherical-aberration phase (pi/2)*Cs*lambda^3*q^4 on the last
+leg.  Intensities get Poisson shot noise at a stated dose.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+__all__ = [
+    "single_axis_rotations",
+    "cone_rotations",
+    "Phantom",
+    "ball_phantom",
+    "blob_phantom",
+    "multislice_images",
+    "ball_projections",
+    "config_workload",
+]
+
+
+# ----------------------------------------------------------------------------- geometry
+def single_axis_rotations(n_dir: int, span: float = math.pi, start: float = 0.0) -> np.ndarray:
+    """Rotations for ``n_dir`` tilts about the volume y axis, evenly over ``[start, start+span)``.
+
+    The detector v axis stays the volume y axis, so this is the single-axis scan of
+    Sec. 2 for which the sampling density reduces to the ramp |q_x|.
+    """
+    th = start + span * np.arange(n_dir, dtype=np.float64) / max(n_dir, 1)
+    c, s = np.cos(th), np.sin(th)
+    rot = np.zeros((n_dir, 3, 3), dtype=np.float64)
+    rot[:, 0, 0] = c
+    rot[:, 0, 2] = s
+    rot[:, 1, 1] = 1.0
+    rot[:, 2, 0] = -s
+    rot[:, 2, 2] = c
+    return rot
+
+
+def _quat_to_rot(q: np.ndarray) -> np.ndarray:
+    w, x, y, z = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+    r = np.empty((q.shape[0], 3, 3))
+    r[:, 0, 0] = 1 - 2 * (y * y + z * z)
+    r[:, 0, 1] = 2 * (x * y - z * w)
+    r[:, 0, 2] = 2 * (x * z + y * w)
+    r[:, 1, 0] = 2 * (x * y + z * w)
+    r[:, 1, 1] = 1 - 2 * (x * x + z * z)
+    r[:, 1, 2] = 2 * (y * z - x * w)
+    r[:, 2, 0] = 2 * (x * z - y * w)
+    r[:, 2, 1] = 2 * (y * z + x * w)
+    r[:, 2, 2] = 1 - 2 * (x * x + y * y)
+    return r
+
+
+def cone_rotations(n_dir: int, max_tilt_deg: float, seed: int) -> np.ndarray:
+    """Haar-random rotations (uniform unit quaternions, Shoemake 1992) kept when the beam
+    direction lies within ``max_tilt_deg`` of the volume z axis (a slab's normal)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    cos_max = math.cos(math.radians(max_tilt_deg))
+    while sum(len(o) for o in out) < n_dir:
+        u1, u2, u3 = rng.random((3, 4 * n_dir + 16))
+        q = np.stack([np.sqrt(1 - u1) * np.sin(2 * np.pi * u2), np.sqrt(1 - u1) * np.cos(2 * np.pi * u2),
+                      np.sqrt(u1) * np.sin(2 * np.pi * u3), np.sqrt(u1) * np.cos(2 * np.pi * u3)], axis=1)
+        r = _quat_to_rot(q)
+        out.append(r[np.abs(r[:, 2, 2]) >= cos_max])
+    return np.concatenate(out)[:n_dir].copy()
+
+
+# ----------------------------------------------------------------------------- phantoms
+@dataclass
+class Phantom:
+    """Sum of primitives. ``kind`` is ``"ball"`` (uniform ball, delta inside radius) or
+    ``"blob"`` (isotropic Gaussian, delta(r) = amp * exp(-|r-c|^2 / (2 s^2))).
+    Centres and sizes are in voxel units relative to the volume centre."""
+    kind: str
+    centre: np.ndarray   # (K, 3) voxel units, relative to the volume centre
+    size: np.ndarray     # (K,) radius (ball) or Gaussian s (blob), voxel units
+    amp: np.ndarray      # (K,) delta inside the ball, or the blob's peak delta
+
+
+def ball_phantom(grid, count: int, seed: int, r_range=(2.0, 8.0), delta_range=(1e-6, 1e-5)) -> Phantom:
+    """``count`` uniform balls with radii U[r_range] voxels and decrement U[delta_range],
+    centres inside the cylinder about y of radius n/2 - r (so every ball stays in the
+    field of view of a single-axis scan); overlaps add."""
+    nx, ny, nz = grid
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(r_range[0], r_range[1], count)
+    cen = np.zeros((count, 3))
+    rad_xz = 0.5 * min(nx, nz) - r
+    for n in range(count):
+        while True:
+            x, z = rng.uniform(-rad_xz[n], rad_xz[n], 2)
+            if x * x + z * z <= rad_xz[n] ** 2:
+                break
+        y = rng.uniform(-(0.5 * ny - r[n]), 0.5 * ny - r[n])
+        cen[n] = (x, y, z)
+    d = rng.uniform(delta_range[0], delta_range[1], count)
+    return Phantom("ball", cen, r, d)
+
+
+def blob_phantom(grid, count: int, seed: int, s_vox: float, w_range=(1.0, 8.0), amp_unit=1.0,
+                 margin: float = 3.0) -> Phantom:
+    """``count`` Gaussian pseudo-atoms of width ``s_vox`` voxels, weights U[w_range] times
+    ``amp_unit`` peak decrement, centres uniform inside the box shrunk by ``margin*s``
+    and inside the y-axis cylinder."""
+    nx, ny, nz = grid
+    rng = np.random.default_rng(seed)
+    m = margin * s_vox
+    rc = 0.5 * min(nx, nz) - m
+    cen = np.empty((0, 3))
+    while cen.shape[0] < count:
+        c = np.stack([rng.uniform(-rc, rc, 2 * count), rng.uniform(-(0.5 * ny - m), 0.5 * ny - m, 2 * count),
+                      rng.uniform(-rc, rc, 2 * count)], axis=1)
+        c = c[c[:, 0] ** 2 + c[:, 2] ** 2 <= rc * rc]
+        cen = np.concatenate([cen, c])
+    cen = cen[:count]
+    w = rng.uniform(w_range[0], w_range[1], count) * amp_unit
+    return Phantom("blob", cen, np.full(count, float(s_vox)), w)
+
+
+# ----------------------------------------------------------------------------- images
+def _pow2_at_least(x: int) -> int:
+    p = 1
+    while p < x:
+        p *= 2
+    return p
+
+
+def ball_projections(ph: Phantom, rot: np.ndarray, nu: int, nv: int) -> np.ndarray:
+    """Straight-ray line integrals of a ball phantom, in voxel-length units:
+    p(u, v) = sum over balls of 2 * delta * sqrt(r^2 - rho^2) (the Radon transform of a
+    uniform ball, sampled at pixel centres).  Returns float64 ``(D, nv, nu)``."""
+    assert ph.kind == "ball"
+    uu = np.arange(nu) - (nu - 1) / 2.0
+    vv = np.arange(nv) - (nv - 1) / 2.0
+    out = np.zeros((rot.shape[0], nv, nu))
+    for n in range(rot.shape[0]):
+        c = ph.centre @ rot[n].T  # beam-frame centres, voxel units
+        for b in range(ph.centre.shape[0]):
+            du = uu[None, :] - c[b, 0]
+            dv = vv[:, None] - c[b, 1]
+            rho2 = du * du + dv * dv
+            out[n] += 2.0 * ph.amp[b] * np.sqrt(np.maximum(ph.size[b] ** 2 - rho2, 0.0))
+    return out
+
+
+def _slab_projection(ph: Phantom, c_beam: np.ndarray, sel: np.ndarray, P: int, off: int, nu: int, nv: int,
+                     device) -> torch.Tensor:
+    """Projected decrement (voxel-length units) of the primitives ``sel`` on a P x P grid
+    whose pixel (off + u, off + v) is image pixel (u, v)."""
+    out = torch.zeros((P, P), dtype=torch.float64, device=device)
+    if sel.size == 0:
+        return out
+    cu = c_beam[sel, 0] + (nu - 1) / 2.0 + off
+    cv = c_beam[sel, 1] + (nv - 1) / 2.0 + off
+    size = ph.size[sel]
+    amp = ph.amp[sel]
+    if ph.kind == "ball":
+        rad = int(math.ceil(float(size.max()))) + 1
+    else:
+        rad = int(math.ceil(4.0 * float(size.max()))) + 1
+    offs = np.arange(-rad, rad + 1)
+    iu = np.floor(cu).astype(np.int64)[:, None, None] + offs[None, None, :]
+    iv = np.floor(cv).astype(np.int64)[:, None, None] + offs[None, :, None]
+    du = iu - cu[:, None, None]
+    dv = iv - cv[:, None, None]
+    rho2 = du * du + dv * dv
+    if ph.kind == "ball":
+        val = 2.0 * amp[:, None, None] * np.sqrt(np.maximum(size[:, None, None] ** 2 - rho2, 0.0))
+    else:
+        s = size[:, None, None]
+        val = amp[:, None, None] * math.sqrt(2.0 * math.pi) * s * np.exp(-rho2 / (2.0 * s * s))
+    iu_b = np.broadcast_to(iu, val.shape) % P
+    iv_b = np.broadcast_to(iv, val.shape) % P
+    flat = torch.as_tensor((iv_b * P + iu_b).reshape(-1), device=device)
+    out.view(-1).index_add_(0, flat, torch.as_tensor(val.reshape(-1), device=device))
+    return out
+
+
+def multislice_images(ph: Phantom, rot: np.ndarray, nu: int, nv: int, delta: float, lam: float,
+                      defocus: np.ndarray, sigma: float, *, cs: float = 0.0, n_slabs: int = 16,
+                      photons: float | None = None, seed: int = 0, device="cpu",
+                      dtype=torch.float32, thickness: float | None = None) -> torch.Tensor:
+    """Flat-fielded intensities I/I_in, shape ``(D, nv, nu)``, of ``ph`` under plane-wave
+    illumination along each ``rot[n]`` beam axis, by the multislice model described in
+    the module docstring.  The slabs tile ``[-thickness/2, thickness/2]`` (voxel units,
+    beam frame; default: the phantom's enclosing sphere) and a primitive belongs to the
+    slab holding its centre.  ``delta`` is the voxel and pixel pitch, ``lam`` the
+    wavelength, ``defocus[n]`` the image-plane distance R_n, ``sigma`` = beta/delta.
+    ``photons`` (per pixel) adds Poisson noise when given."""
+    D = rot.shape[0]
+    P = _pow2_at_least(2 * max(nu, nv))
+    off_u = (P - nu) // 2
+    off_v = (P - nv) // 2
+    f = torch.fft.fftfreq(P, d=delta, device=device, dtype=torch.float64)
+    q2 = f[None, :] ** 2 + f[:, None] ** 2
+    reach = ph.size * (1.0 if ph.kind == "ball" else 4.0)
+    thick = thickness if thickness is not None else \
+        2.0 * float(np.max(np.linalg.norm(ph.centre, axis=1) + reach)) + 1.0  # voxel units
+    dz = thick / n_slabs
+    zc = -thick / 2.0 + (np.arange(n_slabs) + 0.5) * dz
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    step = torch.exp(-1j * math.pi * lam * (dz * delta) * q2)
+    out = torch.empty((D, nv, nu), dtype=dtype, device=device)
+    for n in range(D):
+        c_beam = ph.centre @ rot[n].T
+        slab = np.clip(np.floor((c_beam[:, 2] + thick / 2.0) / dz), 0, n_slabs - 1).astype(np.int64)
+        U = torch.ones((P, P), dtype=torch.complex128, device=device)
+        for m in range(n_slabs):
+            sel = np.nonzero(slab == m)[0]
+            if sel.size:
+                proj = _slab_projection(ph, c_beam, sel, P, off_u, nu, nv, device) * delta  # length units
+                phi = (2.0 * math.pi / lam) * proj
+                U = U * torch.exp(torch.complex(-sigma * phi, phi))
+            if m + 1 < n_slabs:
+                U = torch.fft.ifft2(torch.fft.fft2(U) * step)
+            else:
+                chi = math.pi * lam * (float(defocus[n]) - zc[m] * delta) * q2
+                if cs != 0.0:
+                    chi = chi + 0.5 * math.pi * cs * lam ** 3 * q2 * q2
+                U = torch.fft.ifft2(torch.fft.fft2(U) * torch.exp(-1j * chi))
+        I = (U.real ** 2 + U.imag ** 2)[off_v:off_v + nv, off_u:off_u + nu]
+        if photons is not None:
+            I = torch.poisson(I * photons, generator=gen) / photons
+        out[n] = I.to(dtype)
+    return out
+
+
+# ----------------------------------------------------------------------------- workloads
+def config_workload(name: str, *, scale_dirs: int | None = None):
+    """Parameters of the named synthetic workloads (all seeded).
+
+    ``"small"``: 64^3 voxels of 1 nm, 90 single-axis directions over 180 deg, 64x64
+    images, lambda = 0.1 nm, Nz = 8, 20 uniform balls (radii U[2,8] voxels, delta
+    U[1e-6,1e-5], sigma = beta/delta = 0.01), R_n ~ U[100,120] nm, 1e4 photons/pixel.
+
+    ``"mid"``: 256^3 voxels of 0.1 nm, 360 single-axis directions over 180 deg,
+    256x256 images, lambda = 1.97 pm (300 keV electrons), Nz = 32, defocus 1 um,
+    Cs = 2.7 mm, 2e4 Gaussian pseudo-atoms (s = 0.1 nm, weights U[1,8], peak phase
+    0.01 rad per unit weight), sigma = 0.07, 100 electrons/pixel.
+    """
+    if name == "small":
+        n, D = 64, 90
+        cfg = dict(grid=(n, n, n), nu=n, nv=n, n_dir=D, delta=1e-9, lam=1e-10, nz_layers=8, sigma=0.01,
+                   eps=1e-2, cs=0.0, photons=1e4, seed=1001, phantom="balls", count=20)
+        rng = np.random.default_rng(cfg["seed"] + 7)
+        cfg["defocus"] = rng.uniform(100e-9, 120e-9, D)
+    elif name == "mid":
+        n, D = 256, 360
+        cfg = dict(grid=(n, n, n), nu=n, nv=n, n_dir=D, delta=1e-10, lam=1.97e-12, nz_layers=32, sigma=0.07,
+                   eps=0.1, cs=2.7e-3, photons=100.0, seed=2001, phantom="blobs", count=20000)
+        cfg["defocus"] = np.full(D, 1e-6)
+    else:
+        raise ValueError(name)
+    if scale_dirs is not None:
+        cfg["n_dir"] = scale_dirs
+        cfg["defocus"] = cfg["defocus"][:scale_dirs]
+    cfg["rot"] = single_axis_rotations(cfg["n_dir"])
+    return cfg
+
+
+def make_phantom(cfg) -> Phantom:
+    """The phantom that ``cfg`` (from :func:`config_workload`) names."""
+    if cfg["phantom"] == "balls":
+        return ball_phantom(cfg["grid"], cfg["count"], cfg["seed"])
+    # peak phase per unit weight 0.01 rad: (2 pi / lam) * amp * sqrt(2 pi) * s * delta = 0.01
+    s = 1e-10 / cfg["delta"]
+    amp = 0.01 * cfg["lam"] / (2 * math.pi * math.sqrt(2 * math.pi) * s * cfg["delta"])
+    return blob_phantom(cfg["grid"], cfg["count"], cfg["seed"], s, amp_unit=amp)
