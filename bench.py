@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of the layered UTR reconstruction on synthetic seeded workloads.
+
+A step is one ``recon_run`` over the whole workload: every direction through the
+FFT / per-layer CTF filter / inverse FFT stage and the layered backprojection, with
+the images already resident in HBM.  The metric is voxel x direction updates per
+second (U = V * D per step).  One JSON line is printed by rank 0.
+
+``--impl reference`` times the FP64 CPU oracle instead (a bounded sample of the
+same workload per step, on the host cores).
+
+Multi-GPU: the reconstruction has no exchange step on one GPU's worth of work, so
+``--gpus N`` (under torchrun) runs N independent replicas, one seeded tomogram per
+rank, and reports the aggregate (weak scaling)."""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel×direction updates/s at stated rel-L2 vs FP64 oracle; % HBM roofline"
+UNIT = "updates/s"
+
+WORKLOAD_TEXT = {
+    "mid": ("mid-size plain method: 256^3 grid (0.1 nm voxels), 360 single-axis directions over 180 deg, "
+            "256x256 float32 images, 300 keV electrons (lambda 1.97 pm), Nz=32 depth layers, defocus 1 um, "
+            "Cs 2.7 mm, sigma 0.07, eps 0.1; 2e4 Gaussian pseudo-atoms (s 0.1 nm, weights U[1,8]); "
+            "multislice images with 100 e/px Poisson noise"),
+    "small": ("small plain method: 64^3 grid (1 nm voxels), 90 single-axis directions over 180 deg, 64x64 "
+              "float32 images, lambda 0.1 nm, Nz=8 depth layers, R_n ~ U[100,120] nm, sigma 0.01, eps 0.01; "
+              "20 uniform balls (r U[2,8] vox, delta U[1e-6,1e-5]); multislice images, 1e4 photons/px"),
+}
+
+# DRAM traffic per launch (bytes) from ncu captures, keyed by kernel and workload and
+# valid only for the kernel source they were taken on (sha256 of the .cu file).
+NCU_TRAFFIC: dict = {}
+
+
+def _src_hash(name: str) -> str:
+    p = os.path.join(ROOT, "paper_2206_09151_gb300", "csrc", name)
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def load_peaks() -> tuple[dict, str]:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d["hbm_gbs"], "bf16_tflops": d["bf16_tflops"]}, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def gpu_index(local_rank: int) -> int:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [x.strip() for x in vis.split(",") if x.strip()]
+        if local_rank < len(ids) and ids[local_rank].isdigit():
+            return int(ids[local_rank])
+    return local_rank
+
+
+# ----------------------------------------------------------------------------- workload
+def workload(name: str, rank: int = 0):
+    from paper_2206_09151_gb300 import phantoms as ph
+    cfg = ph.config_workload(name)
+    cfg["seed"] = cfg["seed"] + 100 * rank
+    return cfg
+
+
+def make_images(cfg, device):
+    import torch
+
+    from paper_2206_09151_gb300 import phantoms as ph
+    phan = ph.make_phantom(cfg)
+    return ph.multislice_images(phan, cfg["rot"], cfg["nu"], cfg["nv"], cfg["delta"], cfg["lam"], cfg["defocus"],
+                                cfg["sigma"], cs=cfg["cs"], photons=cfg["photons"], seed=cfg["seed"], device=device,
+                                dtype=torch.float32)
+
+
+def oracle_sample(cfg, images_np, dirs):
+    """FP64 oracle on the directions ``dirs`` alone (a D = len(dirs) scan), full volume."""
+    import oracle as O
+    return O.recon(images_np[dirs], cfg["rot"][dirs], lam=cfg["lam"], delta=cfg["delta"],
+                   defocus=cfg["defocus"][dirs], nz_layers=cfg["nz_layers"], grid=cfg["grid"], sigma=cfg["sigma"],
+                   eps=cfg["eps"], cs=cfg["cs"])
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import torch
+    cfg = workload(args.workload)
+    V = int(np.prod(cfg["grid"]))
+    D = cfg["n_dir"]
+    per_step = max(1, args.ref_dirs)
+    plan = [[((s * per_step + q) * 97) % D for q in range(per_step)] for s in range(args.warmup + args.steps)]
+    need = sorted({d for ds in plan for d in ds})
+    sub = dict(cfg, rot=cfg["rot"][need], defocus=cfg["defocus"][need])
+    images = np.zeros((D, cfg["nv"], cfg["nu"]), np.float32)
+    images[need] = make_images(sub, "cpu").numpy()  # only the sampled views are simulated
+    times = []
+    for s, dirs in enumerate(plan):
+        t0 = time.perf_counter()
+        oracle_sample(cfg, images, dirs)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            times.append(dt)
+    t = sum(times) / len(times)
+    value = V * per_step / t
+    sample = f"{per_step} direction(s) per step over the full {cfg['grid'][0]}^3 volume, FP64 numpy, 1 thread"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload], "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    del torch
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+KERNELS = ["k_rows_fwd", "k_cols", "k_rows_inv", "k_backproject"]
+
+
+def algorithmic_bytes(cfg, r, stack_bytes: int, dir_counts: list[int]) -> list[float]:
+    """Bytes each kernel must move per run (inputs read once, outputs written once)."""
+    nu, nv, nzl = cfg["nu"], cfg["nv"], cfg["nz_layers"]
+    half = r.padded // 2 + 1
+    V = int(np.prod(cfg["grid"]))
+    out = [0.0, 0.0, 0.0, 0.0]
+    for b, nb in enumerate(dir_counts):
+        spec = nb * nv * half * 8
+        inter = nb * nzl * nv * half * 8
+        stack = nb * nzl * (nv + 2) * (nu + 2) * stack_bytes
+        out[0] += nb * nv * nu * 4 + spec
+        out[1] += spec + inter
+        out[2] += inter + stack
+        out[3] += stack + V * (4 if b == 0 else 8)
+    return out
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2206_09151_gb300 import _abi
+    from paper_2206_09151_gb300.build import build
+    from paper_2206_09151_gb300.recon import Reconstructor
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    cfg = workload(args.workload, rank)
+    images = make_images(cfg, dev)
+    torch.cuda.synchronize()
+    V = int(np.prod(cfg["grid"]))
+    D = cfg["n_dir"]
+    U = V * D
+    r = Reconstructor(cfg["rot"], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
+                      defocus=cfg["defocus"], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"], eps=cfg["eps"],
+                      cs=cfg["cs"], stack_dtype=args.stack, dir_block=args.dir_block, device=dev)
+    vol = r.new_volume()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    for _ in range(args.warmup):
+        r.run(images, vol)
+    torch.cuda.synchronize()
+
+    _abi.recon_profile_enable(r.plan, True)
+    kern_ms = [0.0] * 4
+    kern_n = [0] * 4
+    sampler = ClockSampler(gpu_index(local))
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush, outside the timed span
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r.run(images, vol, stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        ms, n = _abi.recon_profile_read(r.plan)
+        for q in range(4):
+            kern_ms[q] += ms[q]
+            kern_n[q] += n[q]
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    _abi.recon_profile_enable(r.plan, False)
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * U * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API: pinned host images in, volume out, every step
+    host_img = images.cpu().pin_memory()
+    host_vol = torch.empty(vol.shape, dtype=torch.float32).pin_memory()
+    dimg = torch.empty_like(images)
+    e2e_ms = []
+    for s in range(args.warmup + args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dimg.copy_(host_img, non_blocking=True)
+        r.run(dimg, vol, stream)
+        host_vol.copy_(vol, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if s >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_total = sum(e2e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * U * args.steps / (e2e_total / 1e3)
+
+    # roofline of the dominant kernel
+    peaks, peak_src = load_peaks()
+    db, nb = r.dir_block, r.n_blocks
+    counts = [min(db, D - b * db) for b in range(nb)]
+    algo = algorithmic_bytes(cfg, r, 2 if args.stack == "bf16" else 4, counts)
+    kernels = {}
+    for q, name in enumerate(KERNELS):
+        per_launch_ms = kern_ms[q] / max(kern_n[q], 1)
+        gbs = algo[q] / (kern_ms[q] / args.steps / 1e3) / 1e9 if kern_ms[q] > 0 else None
+        kernels[name] = {"launches": kern_n[q], "ms_per_launch": per_launch_ms,
+                         "share": kern_ms[q] / max(sum(kern_ms), 1e-12), "algorithmic_GBps": gbs}
+    dom = max(range(4), key=lambda q: kern_ms[q])
+    dom_name = KERNELS[dom]
+    achieved = algo[dom] / nb / (kern_ms[dom] / max(kern_n[dom], 1) / 1e3) / 1e9
+    src = "backproject.cu" if dom == 3 else "stage_a.cu"
+    key = (dom_name, args.workload, args.stack)
+    tr = NCU_TRAFFIC.get(key)
+    traffic = tr["bytes_per_launch"] if tr and tr["src"] == _src_hash(src) else None
+    roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else
+                "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": algo[dom] / nb,
+                "units_per_launch": V * db if dom == 3 else db}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.stack, "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload], "stack": args.stack, "dir_block": db,
+                       "blocks": nb, "padded_fft": r.padded, "updates_per_step": U,
+                       "l2": "flushed between timed steps (256 MiB write outside the timed span)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": images.numel() * 4,
+                    "d2h_bytes_per_step": vol.numel() * 4},
+            "gpu_launches": sum(kern_n), "roofline": roofline, "kernels": kernels, "clocks": clocks}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # the oracle on a bounded sample (a few directions, full volume), beside the same
+        # sample reconstructed on the GPU: the stated accuracy and the CPU rate
+        sel = [int(x) for x in np.linspace(0, D - 1, args.cpu_dirs).round()]
+        img_np = images.cpu().numpy()
+        t0 = time.perf_counter()
+        ref = oracle_sample(cfg, img_np, sel)
+        dt = time.perf_counter() - t0
+        rs = Reconstructor(cfg["rot"][sel], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
+                           defocus=cfg["defocus"][sel], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"],
+                           eps=cfg["eps"], cs=cfg["cs"], stack_dtype=args.stack, device=dev)
+        got = rs.run(images[sel].contiguous()).cpu().numpy()
+        rs.close()
+        rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        sample = f"{len(sel)} of {D} directions over the full volume ({len(sel) * V:.3e} updates), FP64 numpy"
+        line["cpu_baseline"] = {"value": len(sel) * V / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": sample, "seconds": dt}
+        line["accuracy"] = {"rel_l2_vs_fp64_oracle": rel, "sample": sample,
+                            "target": 1e-5 if args.stack == "f32" else 3e-3}
+    if rank == 0:
+        print(json.dumps(line))
+    r.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=list(WORKLOAD_TEXT), default="mid")
+    ap.add_argument("--stack", choices=["f32", "bf16"], default="f32")
+    ap.add_argument("--dir-block", type=int, default=0)
+    ap.add_argument("--cpu-dirs", type=int, default=3)
+    ap.add_argument("--ref-dirs", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

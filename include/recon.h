@@ -1,0 +1,173 @@
+/*
+ * recon.h -- C-ABI of the GB300 layered unified tomographic reconstruction (UTR).
+ *
+ * Gureyev, Brown, Quiney, Allen, "Fast unified reconstruction algorithm for
+ * conventional, phase-contrast and diffraction tomography" (arXiv 2206.09151).
+ *
+ * The operator, per plane-wave illumination direction n (any scan geometry, Sec. 2):
+ *   g_n      = ln(I_n / I_in)                                  (left side of Eq. 4)
+ *   G_n      = 2D DFT of g_n zero-padded to P x P, kernel exp(-i 2 pi r.q)      (Eq. 3)
+ *   chi_k(q) = pi lambda (R_n - z_k) q^2 + (pi/2) Cs lambda^3 q^4 - omega,
+ *              omega = atan(sigma)                                 (Eq. 5, Eq. 7)
+ *   H_k(q)   = lambda / (4 pi sqrt(1+sigma^2)) * sin chi_k / (sin^2 chi_k + eps)
+ *              (the real part of the bracket of Eq. 11 at layer k's own defocus;
+ *               Eq. 13 when Nz = 1 and eps = 0)
+ *   W(q)     = (pi / D) * ramp |q_u| as the band-limited Ram-Lak kernel (Sec. 2:
+ *               the sampling-matrix inverse of a single-axis scan)
+ *   Y_{n,k}  = crop_N( Re IDFT[ G_n H_k W ] )                     -- the layer stack
+ *   vol(r)  += bilinear( Y_{n, k(r)}, u_n(r), v_n(r) )  over all n -- layered backprojection
+ * with k(r) the depth layer containing voxel r along direction n.  Nz = 1 with the
+ * filter off is conventional filtered backprojection (Eq. 15).
+ *
+ * Conventions: volume vol[z][y][x] float32, voxel (i,j,k) centred at
+ * ((i-(nx-1)/2) delta, (j-(ny-1)/2) delta, (k-(nz-1)/2) delta).  rot[n] is a row-major
+ * 3x3 rotation volume frame -> beam frame; its rows are the detector u axis, the
+ * detector v axis and the beam direction.  Images img[n][v][u] float32, pixel (u, v) at
+ * ((u-(nu-1)/2) delta, (v-(nv-1)/2) delta) in the beam frame.  Defocus R_n is measured
+ * from the plane through the rotation centre, positive downstream.  Depth layers are
+ * Nz equal slabs over the volume's bounding-box extent along the beam; the layer of a
+ * voxel is floor of a 2^-24 fixed-point depth coordinate (exact integer arithmetic).
+ *
+ * Errors: every entry point returns RECON_OK (0) or a negative code; no exception
+ * crosses the ABI.  recon_last_error() gives a message for the calling thread's last
+ * failure.  Kernels run asynchronously on the caller's stream: an error inside a
+ * kernel surfaces at the next call that synchronises (recon_sync) or in a later
+ * launch check.
+ *
+ * Threading: a plan is immutable after recon_plan and may be used from several host
+ * threads, but two runs that share one workspace must not overlap on the GPU.
+ */
+#ifndef RECON_H_
+#define RECON_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define RECON_OK 0
+#define RECON_E_INVALID_ARG (-1)      /* null pointer, bad size, bad enum, bad geometry */
+#define RECON_E_UNSUPPORTED_SIZE (-2) /* a size beyond the library's limits            */
+#define RECON_E_CUDA (-3)             /* a CUDA runtime call or a launch failed        */
+#define RECON_E_WORKSPACE (-4)        /* workspace too small or not 256-byte aligned    */
+#define RECON_E_NO_MEMORY (-5)        /* host allocation failed                         */
+
+/* ---------------------------------------------------------------- option values */
+#define RECON_FILTER_OFF 0       /* H = 1: ramp-filtered backprojection of g (Eq. 15)   */
+#define RECON_FILTER_TIKHONOV 1  /* H_k above (real part of Eq. 11, per layer)         */
+
+#define RECON_INPUT_INTENSITY 0  /* images are I/I_in; g = ln(max(I/I_in, 1e-6))       */
+#define RECON_INPUT_CONTRAST 1   /* images already are g (a contrast or a projection)  */
+
+#define RECON_STACK_F32 0        /* layer stack stored in float32                       */
+#define RECON_STACK_BF16 1       /* layer stack stored in bfloat16 (FP32 FFT/accumulate) */
+
+#define RECON_RAMP_SINGLE_AXIS 0 /* ramp along u; every rot[n] must keep v = volume y   */
+
+/* Limits (RECON_E_UNSUPPORTED_SIZE beyond them). */
+#define RECON_MAX_IMAGE 1024     /* nu, nv <= 1024, so P <= 2048                        */
+#define RECON_MAX_LAYERS 96      /* 1 <= nz_layers <= 96                                */
+#define RECON_MAX_GRID 4096      /* nx, ny, nz <= 4096                                  */
+
+/* ---------------------------------------------------------------- types */
+typedef struct recon_plan_s* recon_plan_t;
+
+typedef struct {
+  int nx, ny, nz; /* voxels along x, y, z; pitch = delta */
+} recon_grid;
+
+typedef struct {
+  int n_dir;         /* D >= 0 directions (D = 0: run writes zeros, or leaves vol)   */
+  int nu, nv;        /* image width (u, fastest) and height (v), pixels of pitch delta */
+  const double* rot; /* host, [n_dir][3][3] row-major, volume -> beam frame; copied  */
+} recon_geometry;
+
+typedef struct {
+  double sigma;    /* beta/delta of the monomorphous object (Eq. 7); omega = atan(sigma) */
+  double eps;      /* Tikhonov parameter of Eq. 11, > 0 when filter = TIKHONOV         */
+  double cs;       /* spherical aberration Cs (metres), 0 = none                        */
+  int filter;      /* RECON_FILTER_*                                                    */
+  int input_mode;  /* RECON_INPUT_*                                                     */
+  int stack_dtype; /* RECON_STACK_*                                                     */
+  int ramp_mode;   /* RECON_RAMP_*                                                      */
+  int accumulate;  /* 0: run overwrites vol; 1: run adds into vol                       */
+  int dir_block;   /* directions per block (stack held in workspace), 0 = automatic    */
+} recon_options;
+
+/* Fills *opts with defaults: sigma 0, eps 0.1 (the value of Sec. 3), cs 0, Tikhonov
+ * filter, intensity input, float32 stack, single-axis ramp, overwrite, automatic
+ * block.  No error (opts NULL is ignored). */
+void recon_default_options(recon_options* opts);
+
+/* Builds a plan (host memory only; no CUDA call, no device allocation).
+ *   geom      geometry, rot copied                    lambda  wavelength (m), > 0
+ *   delta     voxel and pixel pitch (m), > 0           defocus host [n_dir] R_n (m), copied
+ *   nz_layers Nz depth layers                          grid    output volume size
+ *   opts      NULL = recon_default_options
+ * The per-direction FP64 tables are computed here: layer depths z_k and defocus
+ * R_n - z_k (Eq. 5), the CTF phase constants (Eq. 7, Eq. 11), the ramp (Sec. 2).
+ * Returns INVALID_ARG / UNSUPPORTED_SIZE / NO_MEMORY on failure, *out untouched. */
+int recon_plan(const recon_geometry* geom, double lambda, double delta, const double* defocus, int nz_layers,
+               const recon_grid* grid, const recon_options* opts, recon_plan_t* out);
+
+/* Device workspace bytes that recon_run needs for this plan (tables, spectra, one
+ * block of layer stacks).  The caller allocates it (256-byte aligned). */
+int recon_workspace_size(recon_plan_t plan, size_t* bytes);
+
+/* Runs the whole operator on `stream` (a cudaStream_t, NULL = legacy default stream).
+ *   images    device, float32 [n_dir][nv][nu], caller-owned, read only
+ *   volume    device, float32 [nz][ny][nx], caller-owned, written (or added to)
+ *   workspace device, >= recon_workspace_size bytes, 256-byte aligned, scratch
+ * Asynchronous: returns once every kernel is queued.  Uses the current CUDA device. */
+int recon_run(recon_plan_t plan, const float* images, float* volume, void* workspace, size_t ws_bytes,
+              void* stream);
+
+/* Stage A alone (Sec. 2, Eq. 4-11 per layer): the layer stacks of directions
+ * [dir_begin, dir_begin + dir_count), dir_count <= the plan's block size, into the
+ * workspace.  *stack_out receives a device pointer into the workspace, laid out
+ * [dir_count][Nz][nv + 2][nu + 2] of float32 or bfloat16 (per stack_dtype) with a
+ * one-pixel zero border: Y_{n,k}(u, v) sits at [n][k][v + 1][u + 1]. */
+int recon_filter_stage(recon_plan_t plan, const float* images, int dir_begin, int dir_count, void* workspace,
+                       size_t ws_bytes, void* stream, const void** stack_out);
+
+/* Stage B alone: layered backprojection of the stacks of directions
+ * [dir_begin, dir_begin + dir_count) held at `stack` (layout of recon_filter_stage)
+ * into `volume` (added when accumulate != 0, else overwritten).  The workspace holds
+ * the direction tables, so it must be the one recon_filter_stage used, or any
+ * workspace of recon_workspace_size bytes. */
+int recon_backproject(recon_plan_t plan, const void* stack, int dir_begin, int dir_count, float* volume,
+                      int accumulate, void* workspace, size_t ws_bytes, void* stream);
+
+/* Plan facts: padded FFT size P, directions per block, number of blocks. */
+int recon_plan_info(recon_plan_t plan, int* padded, int* dir_block, int* n_blocks);
+
+/* Optional kernel timing.  While enabled, recon_run records CUDA events on its
+ * stream around each kernel of each direction block (row FFTs, column filter/iFFTs,
+ * row iFFTs, backprojection).  recon_profile_read waits for the last run's events
+ * and returns the summed milliseconds of each kernel over that run (ms[4], in the
+ * order above) and the number of launches of each (launches[4]).  The events live
+ * in the plan (created on enable, destroyed with the plan); a plan being profiled
+ * must not run on two streams at once. */
+int recon_profile_enable(recon_plan_t plan, int enable);
+int recon_profile_read(recon_plan_t plan, double* ms, int* launches);
+
+/* Waits for `stream` and reports a CUDA error raised by earlier kernels. */
+int recon_sync(void* stream);
+
+/* Frees the plan.  NULL is a no-op. */
+int recon_destroy(recon_plan_t plan);
+
+/* Static text for a status code. */
+const char* recon_error_string(int code);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* recon_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RECON_H_ */

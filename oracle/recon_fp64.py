@@ -213,29 +213,55 @@ def backproject_direction(stack: np.ndarray, A: np.ndarray, B: np.ndarray, T: np
     return out
 
 
+def _partial_recon(args):
+    """Sum over directions ``dirs`` of their contributions to voxels (i, j, k)."""
+    (images, rot, dirs, lam, delta, defocus, nz_layers, grid, sigma, eps, cs, filt, input_mode, i, j, k,
+     n_dir) = args
+    nu, nv = images.shape[2], images.shape[1]
+    A, B = pixel_coefficients(rot, grid, nu, nv)
+    T = layer_constants(rot, grid, nz_layers)
+    zc = layer_centres(rot, grid, nz_layers, delta)
+    acc = np.zeros(i.shape)
+    chunk = 1 << 21
+    for n in dirs:
+        st = layer_stack(images[n], delta=delta, lam=lam, r_n=float(defocus[n]), z_layers=zc[n], n_dir=n_dir,
+                         sigma=sigma, eps=eps, cs=cs, filt=filt, input_mode=input_mode)
+        for s0 in range(0, i.size, chunk):
+            sl = slice(s0, s0 + chunk)
+            acc[sl] += backproject_direction(st, A[n], B[n], T[n], i[sl], j[sl], k[sl])
+    return acc
+
+
 def recon(images, rot, *, lam: float, delta: float, defocus, nz_layers: int, grid, sigma: float = 0.0,
           eps: float = 0.1, cs: float = 0.0, filt: int = FILTER_TIKHONOV, input_mode: int = INPUT_INTENSITY,
-          voxels=None) -> np.ndarray:
+          voxels=None, dirs=None, workers: int = 1) -> np.ndarray:
     """The whole operator, FP64.  ``images`` (D, nv, nu); ``rot`` (D, 3, 3);
     ``defocus`` (D,).  Returns vol[z][y][x] float64, or, when ``voxels = (i, j, k)``
-    index arrays are given, the values at those voxels only."""
+    index arrays are given, the values at those voxels only.  ``dirs`` restricts the
+    sum to a subset of the directions (the ramp keeps its pi/D for all D);
+    ``workers`` > 1 splits the directions over a spawned process pool (the same
+    arithmetic, summed in a different order)."""
     images = np.asarray(images)
     rot = np.asarray(rot, dtype=np.float64)
-    D, nv, nu = images.shape
+    D = images.shape[0]
     nx, ny, nz = grid
     if voxels is None:
         kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
         i, j, k = ii.ravel(), jj.ravel(), kk.ravel()
     else:
         i, j, k = (np.asarray(x, np.int64) for x in voxels)
-    A, B = pixel_coefficients(rot, grid, nu, nv)
-    T = layer_constants(rot, grid, nz_layers)
-    zc = layer_centres(rot, grid, nz_layers, delta)
-    acc = np.zeros(i.shape)
-    for n in range(D):
-        st = layer_stack(images[n], delta=delta, lam=lam, r_n=float(defocus[n]), z_layers=zc[n], n_dir=D,
-                         sigma=sigma, eps=eps, cs=cs, filt=filt, input_mode=input_mode)
-        acc += backproject_direction(st, A[n], B[n], T[n], i, j, k)
+    dirs = list(range(D)) if dirs is None else list(dirs)
+    common = (lam, delta, np.asarray(defocus, np.float64), nz_layers, tuple(grid), sigma, eps, cs, filt,
+              input_mode, i, j, k, D)
+    if workers <= 1 or len(dirs) < 2:
+        acc = _partial_recon((images, rot, dirs) + common)
+    else:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        groups = [dirs[w::workers] for w in range(workers) if dirs[w::workers]]
+        with ProcessPoolExecutor(max_workers=len(groups), mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_partial_recon, [(images, rot, g) + common for g in groups]))
+        acc = np.sum(parts, axis=0)
     if voxels is None:
         return acc.reshape(nz, ny, nx)
     return acc

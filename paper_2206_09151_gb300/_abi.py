@@ -1,0 +1,181 @@
+"""ctypes binding of ``include/recon.h``: the same entry points, argument marshalling
+only.  Every step of the reconstruction runs in ``librecon.so``'s CUDA kernels;
+there is no Python or CPU fallback -- a missing library raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "librecon.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "recon.h")
+
+RECON_OK = 0
+RECON_E_INVALID_ARG = -1
+RECON_E_UNSUPPORTED_SIZE = -2
+RECON_E_CUDA = -3
+RECON_E_WORKSPACE = -4
+RECON_E_NO_MEMORY = -5
+
+RECON_FILTER_OFF = 0
+RECON_FILTER_TIKHONOV = 1
+RECON_INPUT_INTENSITY = 0
+RECON_INPUT_CONTRAST = 1
+RECON_STACK_F32 = 0
+RECON_STACK_BF16 = 1
+RECON_RAMP_SINGLE_AXIS = 0
+
+
+class ReconGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int)]
+
+
+class ReconGeometry(ctypes.Structure):
+    _fields_ = [("n_dir", ctypes.c_int), ("nu", ctypes.c_int), ("nv", ctypes.c_int),
+                ("rot", ctypes.POINTER(ctypes.c_double))]
+
+
+class ReconOptions(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("eps", ctypes.c_double), ("cs", ctypes.c_double),
+                ("filter", ctypes.c_int), ("input_mode", ctypes.c_int), ("stack_dtype", ctypes.c_int),
+                ("ramp_mode", ctypes.c_int), ("accumulate", ctypes.c_int), ("dir_block", ctypes.c_int)]
+
+
+class ReconError(RuntimeError):
+    def __init__(self, code: int, where: str, message: str):
+        super().__init__(f"{where}: {message} [{code}]")
+        self.code = code
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Loads ``librecon.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2206_09151_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp, sz, ip = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int
+    L.recon_default_options.argtypes = [ctypes.POINTER(ReconOptions)]
+    L.recon_default_options.restype = None
+    L.recon_plan.argtypes = [ctypes.POINTER(ReconGeometry), ctypes.c_double, ctypes.c_double,
+                             ctypes.POINTER(ctypes.c_double), ip, ctypes.POINTER(ReconGrid),
+                             ctypes.POINTER(ReconOptions), ctypes.POINTER(vp)]
+    L.recon_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
+    L.recon_run.argtypes = [vp, vp, vp, vp, sz, vp]
+    L.recon_filter_stage.argtypes = [vp, vp, ip, ip, vp, sz, vp, ctypes.POINTER(vp)]
+    L.recon_backproject.argtypes = [vp, vp, ip, ip, vp, ip, vp, sz, vp]
+    L.recon_plan_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]
+    L.recon_profile_enable.argtypes = [vp, ip]
+    L.recon_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ip)]
+    L.recon_sync.argtypes = [vp]
+    L.recon_destroy.argtypes = [vp]
+    L.recon_error_string.argtypes = [ip]
+    L.recon_error_string.restype = ctypes.c_char_p
+    L.recon_last_error.argtypes = []
+    L.recon_last_error.restype = ctypes.c_char_p
+    for name in ("recon_plan", "recon_workspace_size", "recon_run", "recon_filter_stage", "recon_backproject",
+                 "recon_plan_info", "recon_sync", "recon_destroy", "recon_profile_enable", "recon_profile_read"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def header_entry_points(path: str = HEADER) -> list[str]:
+    """Names of the functions ``include/recon.h`` declares."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(recon_[a-z_0-9]+)\s*\(", text)))
+
+
+def _check(rc: int, where: str):
+    if rc != RECON_OK:
+        L = load_library()
+        raise ReconError(rc, where, L.recon_last_error().decode() or L.recon_error_string(rc).decode())
+
+
+def recon_default_options() -> ReconOptions:
+    o = ReconOptions()
+    load_library().recon_default_options(ctypes.byref(o))
+    return o
+
+
+def recon_plan(rot: np.ndarray, nu: int, nv: int, lam: float, delta: float, defocus, nz_layers: int, grid,
+               opts: ReconOptions | None = None) -> ctypes.c_void_p:
+    """Marshals the arguments of ``recon_plan``; returns the plan handle."""
+    L = load_library()
+    rot = np.ascontiguousarray(rot, dtype=np.float64).reshape(-1, 3, 3)
+    defocus = np.ascontiguousarray(defocus, dtype=np.float64).reshape(-1)
+    geom = ReconGeometry(rot.shape[0], nu, nv, rot.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    g = ReconGrid(*grid)
+    out = ctypes.c_void_p()
+    rc = L.recon_plan(ctypes.byref(geom), lam, delta, defocus.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                      nz_layers, ctypes.byref(g), ctypes.byref(opts) if opts is not None else None, ctypes.byref(out))
+    _check(rc, "recon_plan")
+    return out
+
+
+def recon_workspace_size(plan) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().recon_workspace_size(plan, ctypes.byref(n)), "recon_workspace_size")
+    return n.value
+
+
+def recon_plan_info(plan) -> tuple[int, int, int]:
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load_library().recon_plan_info(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "recon_plan_info")
+    return a.value, b.value, c.value
+
+
+def recon_run(plan, images_ptr: int, volume_ptr: int, ws_ptr: int, ws_bytes: int, stream: int):
+    _check(load_library().recon_run(plan, images_ptr, volume_ptr, ws_ptr, ws_bytes, stream), "recon_run")
+
+
+def recon_filter_stage(plan, images_ptr: int, dir_begin: int, dir_count: int, ws_ptr: int, ws_bytes: int,
+                       stream: int) -> int:
+    out = ctypes.c_void_p()
+    _check(load_library().recon_filter_stage(plan, images_ptr, dir_begin, dir_count, ws_ptr, ws_bytes, stream,
+                                             ctypes.byref(out)), "recon_filter_stage")
+    return out.value
+
+
+def recon_backproject(plan, stack_ptr: int, dir_begin: int, dir_count: int, volume_ptr: int, accumulate: int,
+                      ws_ptr: int, ws_bytes: int, stream: int):
+    _check(load_library().recon_backproject(plan, stack_ptr, dir_begin, dir_count, volume_ptr, accumulate, ws_ptr,
+                                            ws_bytes, stream), "recon_backproject")
+
+
+def recon_profile_enable(plan, enable: bool):
+    _check(load_library().recon_profile_enable(plan, int(bool(enable))), "recon_profile_enable")
+
+
+def recon_profile_read(plan) -> tuple[list[float], list[int]]:
+    """Summed milliseconds and launch counts of (row FFT, column filter/iFFT, row iFFT,
+    backprojection) over the plan's last profiled run."""
+    ms = (ctypes.c_double * 4)()
+    n = (ctypes.c_int * 4)()
+    _check(load_library().recon_profile_read(plan, ms, n), "recon_profile_read")
+    return list(ms), list(n)
+
+
+def recon_sync(stream: int):
+    _check(load_library().recon_sync(stream), "recon_sync")
+
+
+def recon_destroy(plan):
+    load_library().recon_destroy(plan)
+
+
+def recon_error_string(code: int) -> str:
+    return load_library().recon_error_string(code).decode()
+
+
+def recon_last_error() -> str:
+    return load_library().recon_last_error().decode()

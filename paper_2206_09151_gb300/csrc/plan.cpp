@@ -1,0 +1,483 @@
+// C-ABI of the layered UTR reconstruction: plan building (host, FP64), workspace
+// layout, and the run loop over direction blocks.  See include/recon.h.
+//
+// Compiled with -ffp-contract=off: the layer constants below must be the exact FP64
+// results of the written operation order (they define the layer decision).
+#include "recon.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "recon_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(RECON_E_CUDA, std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// frac(x / 2) as a 64-bit fixed-point fraction: the phase x*pi taken modulo 2*pi.
+uint64_t half_turns_fixed(double x) {
+  const double h = 0.5 * x;
+  double f = h - std::floor(h);
+  if (!(f < 1.0)) f = 0.0;  // h slightly negative may round to exactly 1
+  const double scaled = std::ldexp(f, 64);
+  if (scaled >= 18446744073709551616.0) return 0;
+  return (uint64_t)scaled;
+}
+
+}  // namespace
+
+struct recon_plan_s {
+  int D, nu, nv, nx, ny, nz, nzl, P, logP, half, db, n_blocks;
+  double lambda, delta;
+  recon_options opt;
+  std::vector<recon::DirParams> dirs;
+  std::vector<uint64_t> uA;
+  std::vector<float> ramp;
+  std::vector<float2> tw;
+  recon::StageAConst ca;
+  recon::BackprojConst cb;
+  // workspace layout (byte offsets)
+  size_t off_dirs, off_uA, off_ramp, off_tw, off_S, off_T, off_stack, ws_bytes, table_bytes;
+  size_t stack_dir_bytes;
+  // optional profiling: 4 events per block plus one at the start of the run
+  bool profile = false;
+  std::vector<cudaEvent_t> events;
+  int profiled_blocks = 0;
+  ~recon_plan_s() {
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+  }
+};
+
+extern "C" {
+
+void recon_default_options(recon_options* o) {
+  if (!o) return;
+  o->sigma = 0.0;
+  o->eps = 0.1;
+  o->cs = 0.0;
+  o->filter = RECON_FILTER_TIKHONOV;
+  o->input_mode = RECON_INPUT_INTENSITY;
+  o->stack_dtype = RECON_STACK_F32;
+  o->ramp_mode = RECON_RAMP_SINGLE_AXIS;
+  o->accumulate = 0;
+  o->dir_block = 0;
+}
+
+const char* recon_error_string(int code) {
+  switch (code) {
+    case RECON_OK: return "ok";
+    case RECON_E_INVALID_ARG: return "invalid argument";
+    case RECON_E_UNSUPPORTED_SIZE: return "unsupported size";
+    case RECON_E_CUDA: return "CUDA error";
+    case RECON_E_WORKSPACE: return "workspace too small or misaligned";
+    case RECON_E_NO_MEMORY: return "host allocation failed";
+    default: return "unknown status";
+  }
+}
+
+const char* recon_last_error(void) { return g_last_error.c_str(); }
+
+int recon_plan(const recon_geometry* geom, double lambda, double delta, const double* defocus, int nz_layers,
+               const recon_grid* grid, const recon_options* opts, recon_plan_t* out) {
+  if (!geom || !grid || !out) return fail(RECON_E_INVALID_ARG, "recon_plan: null geometry, grid or out");
+  const int D = geom->n_dir;
+  if (D < 0) return fail(RECON_E_INVALID_ARG, "recon_plan: n_dir < 0");
+  if (D > 0 && (!geom->rot || !defocus)) return fail(RECON_E_INVALID_ARG, "recon_plan: null rot or defocus");
+  if (geom->nu < 1 || geom->nv < 1) return fail(RECON_E_INVALID_ARG, "recon_plan: image size < 1");
+  if (geom->nu > RECON_MAX_IMAGE || geom->nv > RECON_MAX_IMAGE)
+    return fail(RECON_E_UNSUPPORTED_SIZE, "recon_plan: image side > RECON_MAX_IMAGE");
+  if (grid->nx < 0 || grid->ny < 0 || grid->nz < 0) return fail(RECON_E_INVALID_ARG, "recon_plan: grid < 0");
+  if (grid->nx > RECON_MAX_GRID || grid->ny > RECON_MAX_GRID || grid->nz > RECON_MAX_GRID)
+    return fail(RECON_E_UNSUPPORTED_SIZE, "recon_plan: grid side > RECON_MAX_GRID");
+  if (nz_layers < 1) return fail(RECON_E_INVALID_ARG, "recon_plan: nz_layers < 1");
+  if (nz_layers > RECON_MAX_LAYERS) return fail(RECON_E_UNSUPPORTED_SIZE, "recon_plan: nz_layers > RECON_MAX_LAYERS");
+  if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(RECON_E_INVALID_ARG, "recon_plan: lambda must be > 0");
+  if (!(delta > 0.0) || !std::isfinite(delta)) return fail(RECON_E_INVALID_ARG, "recon_plan: delta must be > 0");
+  recon_options o;
+  recon_default_options(&o);
+  if (opts) o = *opts;
+  if (o.filter != RECON_FILTER_OFF && o.filter != RECON_FILTER_TIKHONOV)
+    return fail(RECON_E_INVALID_ARG, "recon_plan: unknown filter");
+  if (o.input_mode != RECON_INPUT_INTENSITY && o.input_mode != RECON_INPUT_CONTRAST)
+    return fail(RECON_E_INVALID_ARG, "recon_plan: unknown input_mode");
+  if (o.stack_dtype != RECON_STACK_F32 && o.stack_dtype != RECON_STACK_BF16)
+    return fail(RECON_E_INVALID_ARG, "recon_plan: unknown stack_dtype");
+  if (o.ramp_mode != RECON_RAMP_SINGLE_AXIS) return fail(RECON_E_INVALID_ARG, "recon_plan: unknown ramp_mode");
+  if (o.filter == RECON_FILTER_TIKHONOV && !(o.eps > 0.0))
+    return fail(RECON_E_INVALID_ARG, "recon_plan: eps must be > 0 with the Tikhonov filter");
+  if (!std::isfinite(o.sigma) || !std::isfinite(o.eps) || !std::isfinite(o.cs))
+    return fail(RECON_E_INVALID_ARG, "recon_plan: non-finite sigma, eps or cs");
+  if (o.dir_block < 0) return fail(RECON_E_INVALID_ARG, "recon_plan: dir_block < 0");
+
+  recon_plan_s* p = new (std::nothrow) recon_plan_s();
+  if (!p) return fail(RECON_E_NO_MEMORY, "recon_plan: out of host memory");
+  p->D = D;
+  p->nu = geom->nu;
+  p->nv = geom->nv;
+  p->nx = grid->nx;
+  p->ny = grid->ny;
+  p->nz = grid->nz;
+  p->nzl = nz_layers;
+  p->lambda = lambda;
+  p->delta = delta;
+  p->opt = o;
+  int P = 1, logP = 0;
+  while (P < 2 * (p->nu > p->nv ? p->nu : p->nv)) {
+    P *= 2;
+    ++logP;
+  }
+  p->P = P;
+  p->logP = logP;
+  p->half = P / 2 + 1;
+
+  try {
+    p->dirs.resize(D);
+    p->uA.resize((size_t)D * nz_layers);
+    const double cx = 0.5 * (p->nx - 1), cy = 0.5 * (p->ny - 1), cz = 0.5 * (p->nz - 1);
+    const double PD = (double)P * delta;
+    for (int n = 0; n < D; ++n) {
+      const double* R = geom->rot + 9 * (size_t)n;
+      for (int q = 0; q < 9; ++q)
+        if (!std::isfinite(R[q])) {
+          delete p;
+          return fail(RECON_E_INVALID_ARG, "recon_plan: non-finite rotation");
+        }
+      for (int r = 0; r < 3; ++r)
+        for (int s = 0; s < 3; ++s) {
+          const double dot = R[3 * r] * R[3 * s] + R[3 * r + 1] * R[3 * s + 1] + R[3 * r + 2] * R[3 * s + 2];
+          if (std::fabs(dot - (r == s ? 1.0 : 0.0)) > 1e-6) {
+            delete p;
+            return fail(RECON_E_INVALID_ARG, "recon_plan: rot[" + std::to_string(n) + "] is not orthonormal");
+          }
+        }
+      if (o.ramp_mode == RECON_RAMP_SINGLE_AXIS &&
+          (std::fabs(R[3]) > 1e-9 || std::fabs(R[5]) > 1e-9 || std::fabs(R[4] - 1.0) > 1e-9)) {
+        delete p;
+        return fail(RECON_E_INVALID_ARG, "recon_plan: single-axis ramp needs rot[n] row 1 = (0, 1, 0) (n = " +
+                                             std::to_string(n) + ")");
+      }
+      if (!std::isfinite(defocus[n])) {
+        delete p;
+        return fail(RECON_E_INVALID_ARG, "recon_plan: non-finite defocus");
+      }
+      recon::DirParams& d = p->dirs[n];
+      std::memset(&d, 0, sizeof(d));
+      for (int q = 0; q < 3; ++q) {
+        d.a[q] = R[q];
+        d.b[q] = R[3 + q];
+        d.af[q] = (float)R[q];
+        d.bf[q] = (float)R[3 + q];
+      }
+      d.a[3] = 0.5 * (p->nu - 1) - ((R[0] * cx + R[1] * cy) + R[2] * cz);
+      d.b[3] = 0.5 * (p->nv - 1) - ((R[3] * cx + R[4] * cy) + R[5] * cz);
+      // Depth layers: Nz equal slabs over the bounding-box extent along the beam.
+      // Exact operation order (defines the fixed-point layer decision):
+      const double ext = (std::fabs(R[6]) * (double)p->nx + std::fabs(R[7]) * (double)p->ny) +
+                         std::fabs(R[8]) * (double)p->nz;
+      const double scale = (double)nz_layers / ext;
+      const double ti = R[6] * scale, tj = R[7] * scale, tk = R[8] * scale;
+      const double t0 = 0.5 * (double)nz_layers -
+                        ((ti * (0.5 * (p->nx - 1)) + tj * (0.5 * (p->ny - 1))) + tk * (0.5 * (p->nz - 1)));
+      const double one = 16777216.0;  // 2^24
+      d.t[0] = (int32_t)std::rint(t0 * one);
+      d.t[1] = (int32_t)std::rint(ti * one);
+      d.t[2] = (int32_t)std::rint(tj * one);
+      d.t[3] = (int32_t)std::rint(tk * one);
+      // Per-layer CTF phase constant: chi = pi * [lambda (R_n - z_k) / (P delta)^2] * m^2 + ...
+      const double extm = ext * delta;
+      for (int k = 0; k < nz_layers; ++k) {
+        const double zk = -0.5 * extm + (k + 0.5) * (extm / nz_layers);
+        const double Ak = lambda * (defocus[n] - zk) / (PD * PD);
+        p->uA[(size_t)n * nz_layers + k] = half_turns_fixed(Ak);
+      }
+    }
+    // Ramp: (pi/D) delta DFT_P[Ram-Lak](m), m = 0..P/2, with the 1/P^2 of the inverse DFT.
+    p->ramp.assign(p->half, 0.0f);
+    if (D > 0) {
+      for (int m = 0; m < p->half; ++m) {
+        double s = 1.0 / (4.0 * delta * delta);
+        for (int nn = 1; nn < P / 2; nn += 2) {
+          const long long ph = ((long long)m * nn) % P;
+          s += 2.0 * (-1.0 / ((double)nn * nn * M_PI * M_PI * delta * delta)) * std::cos(2.0 * M_PI * ph / P);
+        }
+        p->ramp[m] = (float)((M_PI / D) * delta * s / ((double)P * P));
+      }
+    }
+    p->tw.resize(P / 2);
+    for (int j = 0; j < P / 2; ++j) {
+      p->tw[j].x = (float)std::cos(2.0 * M_PI * j / P);
+      p->tw[j].y = (float)-std::sin(2.0 * M_PI * j / P);
+    }
+  } catch (const std::bad_alloc&) {
+    delete p;
+    return fail(RECON_E_NO_MEMORY, "recon_plan: out of host memory");
+  }
+
+  recon::StageAConst& ca = p->ca;
+  ca.P = P;
+  ca.logP = logP;
+  ca.nu = p->nu;
+  ca.nv = p->nv;
+  ca.nz_layers = nz_layers;
+  ca.filter = o.filter;
+  ca.input_mode = o.input_mode;
+  ca.stack_bf16 = o.stack_dtype == RECON_STACK_BF16;
+  const double PD = (double)P * delta;
+  ca.uC = half_turns_fixed(o.cs * lambda * lambda * lambda / (2.0 * PD * PD * PD * PD));
+  ca.uW = half_turns_fixed(std::atan(o.sigma) / M_PI);
+  ca.eps = (float)o.eps;
+  ca.pref = (float)(lambda / (4.0 * M_PI * std::sqrt(1.0 + o.sigma * o.sigma)));
+  ca.half = p->half;
+  ca.su = p->nu + 2;
+  ca.layer_elems = (size_t)(p->nv + 2) * (p->nu + 2);
+
+  recon::BackprojConst& cb = p->cb;
+  cb.nx = p->nx;
+  cb.ny = p->ny;
+  cb.nz = p->nz;
+  cb.nu = p->nu;
+  cb.nv = p->nv;
+  cb.nz_layers = nz_layers;
+  cb.su = ca.su;
+  cb.layer_elems = ca.layer_elems;
+  cb.stack_bf16 = ca.stack_bf16;
+
+  const size_t elem = ca.stack_bf16 ? 2 : 4;
+  p->stack_dir_bytes = (size_t)nz_layers * ca.layer_elems * elem;
+  const size_t per_dir = (size_t)p->nv * p->half * 8 * (1 + (size_t)nz_layers) + p->stack_dir_bytes;
+  int db = o.dir_block;
+  if (db == 0) {
+    const size_t budget = (size_t)1 << 30;
+    db = (int)(budget / per_dir);
+    if (db < 1) db = 1;
+  }
+  if (db > 1024) db = 1024;
+  if (D > 0 && db > D) db = D;
+  if (db < 1) db = 1;
+  p->db = db;
+  p->n_blocks = D > 0 ? (D + db - 1) / db : 0;
+
+  size_t off = 0;
+  p->off_dirs = off;
+  off = align256(off + sizeof(recon::DirParams) * (size_t)(D > 0 ? D : 1));
+  p->off_uA = off;
+  off = align256(off + sizeof(uint64_t) * (size_t)(D > 0 ? D : 1) * nz_layers);
+  p->off_ramp = off;
+  off = align256(off + sizeof(float) * p->half);
+  p->off_tw = off;
+  off = align256(off + sizeof(float2) * (P / 2));
+  p->table_bytes = off;
+  p->off_S = off;
+  off = align256(off + (size_t)db * p->nv * p->half * 8);
+  p->off_T = off;
+  off = align256(off + (size_t)db * nz_layers * p->nv * p->half * 8);
+  p->off_stack = off;
+  off = align256(off + (size_t)db * p->stack_dir_bytes);
+  p->ws_bytes = off;
+  *out = p;
+  return RECON_OK;
+}
+
+int recon_workspace_size(recon_plan_t p, size_t* bytes) {
+  if (!p || !bytes) return fail(RECON_E_INVALID_ARG, "recon_workspace_size: null argument");
+  *bytes = p->ws_bytes;
+  return RECON_OK;
+}
+
+int recon_plan_info(recon_plan_t p, int* padded, int* dir_block, int* n_blocks) {
+  if (!p) return fail(RECON_E_INVALID_ARG, "recon_plan_info: null plan");
+  if (padded) *padded = p->P;
+  if (dir_block) *dir_block = p->db;
+  if (n_blocks) *n_blocks = p->n_blocks;
+  return RECON_OK;
+}
+
+int recon_destroy(recon_plan_t p) {
+  delete p;
+  return RECON_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int check_ws(recon_plan_t p, void* ws, size_t ws_bytes, const char* who) {
+  if (!ws) return fail(RECON_E_WORKSPACE, std::string(who) + ": null workspace");
+  if (((uintptr_t)ws & 255) != 0) return fail(RECON_E_WORKSPACE, std::string(who) + ": workspace not 256-byte aligned");
+  if (ws_bytes < p->ws_bytes)
+    return fail(RECON_E_WORKSPACE, std::string(who) + ": workspace has " + std::to_string(ws_bytes) + " bytes, needs " +
+                                       std::to_string(p->ws_bytes));
+  return RECON_OK;
+}
+
+recon::Workspace carve(recon_plan_t p, void* ws) {
+  char* b = (char*)ws;
+  recon::Workspace w;
+  w.dirs = (recon::DirParams*)(b + p->off_dirs);
+  w.uA = (uint64_t*)(b + p->off_uA);
+  w.ramp = (float*)(b + p->off_ramp);
+  w.tw = (float2*)(b + p->off_tw);
+  w.S = (float2*)(b + p->off_S);
+  w.T = (float2*)(b + p->off_T);
+  w.stack = (void*)(b + p->off_stack);
+  return w;
+}
+
+int upload_tables(recon_plan_t p, const recon::Workspace& w, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (p->D > 0) {
+    e = cudaMemcpyAsync(w.dirs, p->dirs.data(), sizeof(recon::DirParams) * p->D, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(w.uA, p->uA.data(), sizeof(uint64_t) * p->uA.size(), cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w.ramp, p->ramp.data(), sizeof(float) * p->ramp.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w.tw, p->tw.data(), sizeof(float2) * p->tw.size(), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "upload of plan tables");
+  return RECON_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int recon_run(recon_plan_t p, const float* images, float* volume, void* workspace, size_t ws_bytes, void* stream) {
+  if (!p) return fail(RECON_E_INVALID_ARG, "recon_run: null plan");
+  const size_t nvox = (size_t)p->nx * p->ny * p->nz;
+  if (nvox > 0 && !volume) return fail(RECON_E_INVALID_ARG, "recon_run: null volume");
+  if (p->D > 0 && !images) return fail(RECON_E_INVALID_ARG, "recon_run: null images");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->D == 0 || nvox == 0) {
+    if (nvox > 0 && !p->opt.accumulate) {
+      cudaError_t e = cudaMemsetAsync(volume, 0, nvox * sizeof(float), s);
+      if (e != cudaSuccess) return cuda_fail(e, "recon_run: clearing the volume");
+    }
+    return RECON_OK;
+  }
+  int rc = check_ws(p, workspace, ws_bytes, "recon_run");
+  if (rc) return rc;
+  const recon::Workspace w = carve(p, workspace);
+  rc = upload_tables(p, w, s);
+  if (rc) return rc;
+  cudaEvent_t* ev = p->profile ? p->events.data() : nullptr;
+  if (ev) cudaEventRecord(ev[0], s);
+  for (int b = 0; b < p->n_blocks; ++b) {
+    const int d0 = b * p->db;
+    const int cnt = (p->D - d0) < p->db ? (p->D - d0) : p->db;
+    cudaError_t e = recon::launch_stage_a(p->ca, w, images, d0, cnt, s, ev ? ev + 1 + 4 * b : nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "recon_run: stage A launch");
+    if (ev) cudaEventRecord(ev[3 + 4 * b], s);
+    e = recon::launch_backproject(p->cb, w.dirs, w.stack, d0, cnt, volume, p->opt.accumulate || b > 0, s);
+    if (e != cudaSuccess) return cuda_fail(e, "recon_run: backprojection launch");
+    if (ev) cudaEventRecord(ev[4 + 4 * b], s);
+  }
+  if (ev) p->profiled_blocks = p->n_blocks;
+  return RECON_OK;
+}
+
+int recon_filter_stage(recon_plan_t p, const float* images, int dir_begin, int dir_count, void* workspace,
+                       size_t ws_bytes, void* stream, const void** stack_out) {
+  if (!p || !stack_out) return fail(RECON_E_INVALID_ARG, "recon_filter_stage: null plan or stack_out");
+  if (dir_begin < 0 || dir_count < 0 || dir_begin + dir_count > p->D || dir_count > p->db)
+    return fail(RECON_E_INVALID_ARG, "recon_filter_stage: direction range outside the plan or above its block size");
+  if (dir_count > 0 && !images) return fail(RECON_E_INVALID_ARG, "recon_filter_stage: null images");
+  int rc = check_ws(p, workspace, ws_bytes, "recon_filter_stage");
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const recon::Workspace w = carve(p, workspace);
+  rc = upload_tables(p, w, s);
+  if (rc) return rc;
+  cudaError_t e = recon::launch_stage_a(p->ca, w, images, dir_begin, dir_count, s);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_filter_stage: launch");
+  *stack_out = w.stack;
+  return RECON_OK;
+}
+
+int recon_backproject(recon_plan_t p, const void* stack, int dir_begin, int dir_count, float* volume, int accumulate,
+                      void* workspace, size_t ws_bytes, void* stream) {
+  if (!p) return fail(RECON_E_INVALID_ARG, "recon_backproject: null plan");
+  if (dir_begin < 0 || dir_count < 0 || dir_begin + dir_count > p->D || dir_count > 1024)
+    return fail(RECON_E_INVALID_ARG, "recon_backproject: direction range outside the plan (or > 1024 directions)");
+  const size_t nvox = (size_t)p->nx * p->ny * p->nz;
+  if (nvox > 0 && !volume) return fail(RECON_E_INVALID_ARG, "recon_backproject: null volume");
+  if (dir_count > 0 && !stack) return fail(RECON_E_INVALID_ARG, "recon_backproject: null stack");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (dir_count == 0 || nvox == 0) {
+    if (nvox > 0 && !accumulate) {
+      cudaError_t e = cudaMemsetAsync(volume, 0, nvox * sizeof(float), s);
+      if (e != cudaSuccess) return cuda_fail(e, "recon_backproject: clearing the volume");
+    }
+    return RECON_OK;
+  }
+  int rc = check_ws(p, workspace, ws_bytes, "recon_backproject");
+  if (rc) return rc;
+  const recon::Workspace w = carve(p, workspace);
+  rc = upload_tables(p, w, s);
+  if (rc) return rc;
+  cudaError_t e = recon::launch_backproject(p->cb, w.dirs, stack, dir_begin, dir_count, volume, accumulate, s);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_backproject: launch");
+  return RECON_OK;
+}
+
+int recon_profile_enable(recon_plan_t p, int enable) {
+  if (!p) return fail(RECON_E_INVALID_ARG, "recon_profile_enable: null plan");
+  if (enable && p->events.empty()) {
+    p->events.resize(1 + 4 * (size_t)p->n_blocks);
+    for (size_t i = 0; i < p->events.size(); ++i) {
+      cudaError_t e = cudaEventCreate(&p->events[i]);
+      if (e != cudaSuccess) {
+        p->events.resize(i);
+        return cuda_fail(e, "recon_profile_enable: cudaEventCreate");
+      }
+    }
+  }
+  p->profile = enable != 0;
+  p->profiled_blocks = 0;
+  return RECON_OK;
+}
+
+int recon_profile_read(recon_plan_t p, double* ms, int* launches) {
+  if (!p || !ms || !launches) return fail(RECON_E_INVALID_ARG, "recon_profile_read: null argument");
+  for (int q = 0; q < 4; ++q) {
+    ms[q] = 0.0;
+    launches[q] = 0;
+  }
+  if (p->profiled_blocks == 0) return RECON_OK;
+  cudaError_t e = cudaEventSynchronize(p->events[4 * (size_t)p->profiled_blocks]);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_profile_read: cudaEventSynchronize");
+  for (int b = 0; b < p->profiled_blocks; ++b)
+    for (int q = 0; q < 4; ++q) {
+      float t = 0.f;
+      e = cudaEventElapsedTime(&t, p->events[4 * (size_t)b + q], p->events[4 * (size_t)b + q + 1]);
+      if (e != cudaSuccess) return cuda_fail(e, "recon_profile_read: cudaEventElapsedTime");
+      ms[q] += t;
+      launches[q] += 1;
+    }
+  return RECON_OK;
+}
+
+int recon_sync(void* stream) {
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_sync");
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "recon_sync");
+  return RECON_OK;
+}
+
+}  // extern "C"

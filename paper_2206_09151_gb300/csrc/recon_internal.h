@@ -1,0 +1,67 @@
+// Internal types shared by the host plan and the CUDA kernels of the layered UTR path.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace recon {
+
+// Per-direction constants, built by the plan in FP64 (one 128-byte record per direction).
+struct DirParams {
+  double a[4];      // detector u pixel: a(i,j,k) = a[0] i + a[1] j + a[2] k + a[3]
+  double b[4];      // detector v pixel, same form
+  float af[3];      // FP32 copies of the steps a[0..2]
+  float bf[3];      // FP32 copies of the steps b[0..2]
+  int32_t t[4];     // depth in 2^-24 layer units: T0, Ti, Tj, Tk (exact integer sum)
+  int32_t pad[6];
+};
+static_assert(sizeof(DirParams) == 128, "DirParams must stay 128 bytes");
+
+// Constants of stage A (FFT -> per-layer filter -> inverse FFT -> stack).
+struct StageAConst {
+  int P, logP;          // padded FFT size and its log2
+  int nu, nv;           // image size
+  int nz_layers;        // Nz
+  int filter;           // RECON_FILTER_*
+  int input_mode;       // RECON_INPUT_*
+  int stack_bf16;       // 0: float32 stack, 1: bfloat16 stack
+  uint64_t uC;          // Cs phase per m^2 as a fraction of 2 pi, 2^-64 units
+  uint64_t uW;          // omega as a fraction of 2 pi, 2^-64 units
+  float eps;            // Tikhonov eps
+  float pref;           // lambda / (4 pi sqrt(1 + sigma^2))
+  int half;             // P/2 + 1 (columns of the half spectrum)
+  int su;               // stack row pitch, nu + 2
+  size_t layer_elems;   // (nv + 2) * (nu + 2)
+};
+
+// Device pointers into the workspace.
+struct Workspace {
+  DirParams* dirs;      // [D]
+  uint64_t* uA;         // [D][Nz]: pi lambda (R_n - z_k)/(P delta)^2 per unit m, fraction of 2 pi
+  float* ramp;          // [P/2+1]: ramp weight, includes pi/D and 1/P^2
+  float2* tw;           // [P/2]: exp(-2 pi i j / P)
+  float2* S;            // [DB][nv][P/2+1]: row transforms
+  float2* T;            // [DB][Nz][nv][P/2+1]: per-layer column inverse transforms
+  void* stack;          // [DB][Nz][nv+2][nu+2]
+};
+
+// Kernel launchers (stage_a.cu, backproject.cu).  They return cudaGetLastError().
+// `ev`, when not null, holds two events recorded after the row FFTs and after the
+// column kernel (the caller records the ones before and after the whole stage).
+cudaError_t launch_stage_a(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin,
+                           int dir_count, cudaStream_t stream, cudaEvent_t* ev = nullptr);
+
+struct BackprojConst {
+  int nx, ny, nz;
+  int nu, nv, nz_layers;
+  int su;
+  size_t layer_elems;
+  int stack_bf16;
+};
+
+cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
+                               int dir_count, float* volume, int accumulate, cudaStream_t stream);
+
+}  // namespace recon

@@ -1,0 +1,103 @@
+"""PyTorch-facing wrapper of the C-ABI: device memory and streams come from PyTorch;
+the computation is ``librecon.so``'s kernels (``recon_run`` and the stage entry points)."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _abi
+
+_FILTERS = {"off": _abi.RECON_FILTER_OFF, "tikhonov": _abi.RECON_FILTER_TIKHONOV}
+_INPUTS = {"intensity": _abi.RECON_INPUT_INTENSITY, "contrast": _abi.RECON_INPUT_CONTRAST}
+_STACKS = {"f32": _abi.RECON_STACK_F32, "bf16": _abi.RECON_STACK_BF16}
+
+
+class Reconstructor:
+    """One plan plus its workspace on the current CUDA device.
+
+    ``rot`` (D, 3, 3) volume->beam rotations, ``nu``/``nv`` image size, ``grid`` =
+    (nx, ny, nz), ``lam`` wavelength, ``delta`` pitch, ``defocus`` (D,) R_n,
+    ``nz_layers`` depth layers; options as in ``recon_options``."""
+
+    def __init__(self, rot, nu: int, nv: int, grid, *, lam: float, delta: float, defocus, nz_layers: int,
+                 sigma: float = 0.0, eps: float = 0.1, cs: float = 0.0, filter: str = "tikhonov",
+                 input_mode: str = "intensity", stack_dtype: str = "f32", accumulate: bool = False,
+                 dir_block: int = 0, device=None, allocate: bool = True):
+        o = _abi.recon_default_options()
+        o.sigma, o.eps, o.cs = float(sigma), float(eps), float(cs)
+        o.filter, o.input_mode, o.stack_dtype = _FILTERS[filter], _INPUTS[input_mode], _STACKS[stack_dtype]
+        o.accumulate, o.dir_block = int(bool(accumulate)), int(dir_block)
+        self.rot = np.ascontiguousarray(rot, np.float64).reshape(-1, 3, 3)
+        self.D = self.rot.shape[0]
+        self.nu, self.nv, self.grid, self.nz_layers = nu, nv, tuple(grid), nz_layers
+        self.stack_dtype = torch.bfloat16 if stack_dtype == "bf16" else torch.float32
+        self.plan = _abi.recon_plan(self.rot, nu, nv, lam, delta, defocus, nz_layers, self.grid, o)
+        self.ws_bytes = _abi.recon_workspace_size(self.plan)
+        self.padded, self.dir_block, self.n_blocks = _abi.recon_plan_info(self.plan)
+        self.device = torch.device(device) if device is not None else (
+            torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else None)
+        self.workspace = None
+        if allocate:
+            self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=self.device)
+
+    # -------------------------------------------------------------- helpers
+    @staticmethod
+    def _stream(stream) -> int:
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return int(s.cuda_stream)
+
+    def _check_images(self, images: torch.Tensor):
+        if images.dtype != torch.float32 or not images.is_cuda or not images.is_contiguous():
+            raise ValueError("images must be a contiguous float32 CUDA tensor")
+        if tuple(images.shape) != (self.D, self.nv, self.nu):
+            raise ValueError(f"images shape {tuple(images.shape)} != {(self.D, self.nv, self.nu)}")
+
+    def new_volume(self) -> torch.Tensor:
+        nx, ny, nz = self.grid
+        return torch.empty((nz, ny, nx), dtype=torch.float32, device=self.device)
+
+    # -------------------------------------------------------------- entry points
+    def run(self, images: torch.Tensor, volume: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """``recon_run``: the whole operator into ``volume`` (allocated if None)."""
+        self._check_images(images)
+        if volume is None:
+            volume = self.new_volume()
+        nx, ny, nz = self.grid
+        if volume.dtype != torch.float32 or not volume.is_contiguous() or tuple(volume.shape) != (nz, ny, nx):
+            raise ValueError("volume must be a contiguous float32 tensor of shape (nz, ny, nx)")
+        _abi.recon_run(self.plan, images.data_ptr(), volume.data_ptr(), self.workspace.data_ptr(), self.ws_bytes,
+                       self._stream(stream))
+        return volume
+
+    def filter_stage(self, images: torch.Tensor, dir_begin: int, dir_count: int, stream=None) -> torch.Tensor:
+        """``recon_filter_stage``: a view of the workspace holding the layer stacks,
+        shape (dir_count, Nz, nv + 2, nu + 2), zero border included."""
+        self._check_images(images)
+        ptr = _abi.recon_filter_stage(self.plan, images.data_ptr(), dir_begin, dir_count,
+                                      self.workspace.data_ptr(), self.ws_bytes, self._stream(stream))
+        off = ptr - self.workspace.data_ptr()
+        esz = 2 if self.stack_dtype == torch.bfloat16 else 4
+        n = dir_count * self.nz_layers * (self.nv + 2) * (self.nu + 2)
+        return self.workspace[off:off + n * esz].view(self.stack_dtype).view(
+            dir_count, self.nz_layers, self.nv + 2, self.nu + 2)
+
+    def backproject(self, stack: torch.Tensor, dir_begin: int, dir_count: int, volume: torch.Tensor,
+                    accumulate: bool, stream=None) -> torch.Tensor:
+        """``recon_backproject``: layered backprojection of ``stack`` (layout of
+        :meth:`filter_stage`) into ``volume``."""
+        if stack.dtype != self.stack_dtype or not stack.is_contiguous():
+            raise ValueError("stack dtype/layout does not match the plan")
+        _abi.recon_backproject(self.plan, stack.data_ptr(), dir_begin, dir_count, volume.data_ptr(),
+                               int(bool(accumulate)), self.workspace.data_ptr(), self.ws_bytes, self._stream(stream))
+        return volume
+
+    def close(self):
+        if getattr(self, "plan", None) is not None:
+            _abi.recon_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,107 @@
+"""The C-ABI library loads and exports every entry point include/recon.h declares,
+and its host-side plan validation works without a GPU (recon_plan makes no CUDA
+call).  CPU only: no compute call here."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from paper_2206_09151_gb300 import _abi, phantoms as ph
+from paper_2206_09151_gb300.build import build
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build()
+    return _abi.load_library()
+
+
+def test_every_declared_entry_point_is_exported(lib):
+    names = _abi.header_entry_points()
+    assert {"recon_plan", "recon_run", "recon_destroy", "recon_workspace_size", "recon_error_string"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _plan(**kw):
+    args = dict(rot=ph.single_axis_rotations(12), nu=40, nv=33, lam=1e-10, delta=1e-9,
+                defocus=np.full(12, 1e-7), nz_layers=4, grid=(30, 20, 10))
+    args.update(kw)
+    opts = args.pop("opts", None)
+    return _abi.recon_plan(args["rot"], args["nu"], args["nv"], args["lam"], args["delta"], args["defocus"],
+                           args["nz_layers"], args["grid"], opts)
+
+
+def test_plan_builds_on_the_host_and_reports_its_layout(lib):
+    p = _plan()
+    P, db, nb = _abi.recon_plan_info(p)
+    assert P == 128 and 1 <= db <= 12 and nb == -(-12 // db)
+    ws = _abi.recon_workspace_size(p)
+    assert ws > 0 and ws % 256 == 0
+    _abi.recon_destroy(p)
+    assert lib.recon_destroy(None) == 0
+
+
+def test_workspace_grows_with_the_direction_block(lib):
+    o1 = _abi.recon_default_options()
+    o1.dir_block = 1
+    o4 = _abi.recon_default_options()
+    o4.dir_block = 4
+    p1, p4 = _plan(opts=o1), _plan(opts=o4)
+    assert _abi.recon_plan_info(p1)[1:] == (1, 12) and _abi.recon_plan_info(p4)[1:] == (4, 3)
+    assert _abi.recon_workspace_size(p4) > _abi.recon_workspace_size(p1)
+    _abi.recon_destroy(p1)
+    _abi.recon_destroy(p4)
+
+
+def test_default_options(lib):
+    o = _abi.recon_default_options()
+    assert (o.sigma, o.eps, o.cs, o.filter, o.input_mode, o.stack_dtype, o.accumulate, o.dir_block) == \
+        (0.0, 0.1, 0.0, 1, 0, 0, 0, 0)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(nu=0), _abi.RECON_E_INVALID_ARG),
+    (dict(nu=1025), _abi.RECON_E_UNSUPPORTED_SIZE),
+    (dict(nz_layers=0), _abi.RECON_E_INVALID_ARG),
+    (dict(nz_layers=97), _abi.RECON_E_UNSUPPORTED_SIZE),
+    (dict(lam=0.0), _abi.RECON_E_INVALID_ARG),
+    (dict(delta=-1.0), _abi.RECON_E_INVALID_ARG),
+    (dict(grid=(5000, 2, 2)), _abi.RECON_E_UNSUPPORTED_SIZE),
+    (dict(rot=ph.single_axis_rotations(12) * 1.01), _abi.RECON_E_INVALID_ARG),
+    (dict(rot=ph.cone_rotations(12, 40.0, seed=1)), _abi.RECON_E_INVALID_ARG),
+    (dict(defocus=np.full(12, np.nan)), _abi.RECON_E_INVALID_ARG),
+])
+def test_plan_rejects_bad_arguments(lib, kw, code):
+    with pytest.raises(_abi.ReconError) as e:
+        _plan(**kw)
+    assert e.value.code == code
+    assert _abi.recon_last_error() != ""
+
+
+def test_plan_rejects_bad_options(lib):
+    o = _abi.recon_default_options()
+    o.eps = 0.0
+    with pytest.raises(_abi.ReconError):
+        _plan(opts=o)
+    o = _abi.recon_default_options()
+    o.filter = 7
+    with pytest.raises(_abi.ReconError):
+        _plan(opts=o)
+
+
+def test_null_arguments_are_errors_not_crashes(lib):
+    out = ctypes.c_void_p()
+    assert lib.recon_plan(None, 1.0, 1.0, None, 1, None, None, ctypes.byref(out)) == _abi.RECON_E_INVALID_ARG
+    assert lib.recon_workspace_size(None, None) == _abi.RECON_E_INVALID_ARG
+    assert lib.recon_run(None, None, None, None, 0, None) == _abi.RECON_E_INVALID_ARG
+    p = _plan()
+    # a misaligned or short workspace is refused before any CUDA call
+    assert lib.recon_run(p, 16, 16, 8, 1 << 40, None) == _abi.RECON_E_WORKSPACE
+    assert lib.recon_run(p, 16, 16, 256, 1, None) == _abi.RECON_E_WORKSPACE
+    _abi.recon_destroy(p)
+
+
+def test_error_strings(lib):
+    for c in (0, -1, -2, -3, -4, -5):
+        assert _abi.recon_error_string(c)
