@@ -215,6 +215,10 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
           const long long ph = ((long long)m * nn) % P;
           s += 2.0 * (-1.0 / ((double)nn * nn * M_PI * M_PI * delta * delta)) * std::cos(2.0 * M_PI * ph / P);
         }
+        if ((P / 2) % 2 == 1) {  // the unpaired tap n = -P/2 (odd only when P = 2)
+          const double hn = (double)(P / 2);
+          s += (-1.0 / (hn * hn * M_PI * M_PI * delta * delta)) * ((m % 2) ? -1.0 : 1.0);
+        }
         p->ramp[m] = (float)((M_PI / D) * delta * s / ((double)P * P));
       }
     }
