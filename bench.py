@@ -129,9 +129,9 @@ def gpu_index(local_rank: int) -> int:
 
 
 # ----------------------------------------------------------------------------- workload
-def workload(name: str, rank: int = 0):
+def workload(name: str, rank: int = 0, dirs: int | None = None):
     from paper_2206_09151_gb300 import phantoms as ph
-    cfg = ph.config_workload(name)
+    cfg = ph.config_workload(name, scale_dirs=dirs)
     cfg["seed"] = cfg["seed"] + 100 * rank
     return cfg
 
@@ -232,7 +232,7 @@ def run_ours(args):
         build()
     if world > 1:
         dist.barrier()
-    cfg = workload(args.workload, rank)
+    cfg = workload(args.workload, rank, args.dirs)
     images = make_images(cfg, dev)
     torch.cuda.synchronize()
     V = int(np.prod(cfg["grid"]))
@@ -336,7 +336,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.stack, "data": "synthetic",
-            "config": {"workload": WORKLOAD_TEXT[args.workload], "stack": args.stack, "dir_block": db,
+            "config": {"workload": WORKLOAD_TEXT[args.workload] + (f" [first {D} directions only]" if args.dirs else ""),
+                       "stack": args.stack, "dir_block": db,
                        "blocks": nb, "padded_fft": r.padded, "updates_per_step": U,
                        "l2": "flushed between timed steps (256 MiB write outside the timed span)",
                        "parallelism": f"replicas x{world}"},
@@ -380,6 +381,7 @@ def main():
     ap.add_argument("--workload", choices=list(WORKLOAD_TEXT), default="mid")
     ap.add_argument("--stack", choices=["f32", "bf16"], default="f32")
     ap.add_argument("--dir-block", type=int, default=0)
+    ap.add_argument("--dirs", type=int, default=None, help="first N directions only (small profiling cases)")
     ap.add_argument("--cpu-dirs", type=int, default=3)
     ap.add_argument("--ref-dirs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")

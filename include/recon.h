@@ -154,6 +154,31 @@ int recon_plan_info(recon_plan_t plan, int* padded, int* dir_block, int* n_block
 int recon_profile_enable(recon_plan_t plan, int enable);
 int recon_profile_read(recon_plan_t plan, double* ms, int* launches);
 
+/* Size of the static device scratch that recon_run_noalloc works in (32 MiB). */
+#define RECON_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* recon_run without any device allocation.  The paper has no counterpart: this is a
+ * service for callers that may not allocate GPU memory themselves -- a component that
+ * lives inside a host application which has already divided the device memory among
+ * its parts, a real-time acquisition loop in which cudaMalloc/cudaFree are banned
+ * because they can synchronise the device and stall the frame stream, or a plugin in a
+ * process whose allocator owns every byte.  The caller still passes the device images
+ * and volume (same layout and meaning as recon_run); the plan tables, spectra,
+ * intermediates and layer stacks live in one static 32 MiB device array compiled into
+ * the library, which every GPU that loads the library keeps until the process exits.
+ * Directions are processed in the largest block that fits that array.
+ *   Limit: a plan whose table head plus one direction's scratch exceeds
+ *   RECON_NOALLOC_SCRATCH_BYTES is refused with RECON_E_UNSUPPORTED_SIZE and a message
+ *   giving both sizes.
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before any
+ *   stream capture.
+ *   Sharing: all calls share the one array and it keeps the last call's contents;
+ *   nothing in it needs to start at zero (every kernel writes what it later reads), but
+ *   two calls that overlap on the GPU (other streams, other threads) race on it.
+ * Calls no cudaMalloc, cudaFree or allocating library routine. */
+int recon_run_noalloc(recon_plan_t plan, const float* images, float* volume, void* stream);
+
 /* Waits for `stream` and reports a CUDA error raised by earlier kernels. */
 int recon_sync(void* stream);
 

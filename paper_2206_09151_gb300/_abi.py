@@ -27,6 +27,7 @@ RECON_INPUT_CONTRAST = 1
 RECON_STACK_F32 = 0
 RECON_STACK_BF16 = 1
 RECON_RAMP_SINGLE_AXIS = 0
+RECON_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 class ReconGrid(ctypes.Structure):
@@ -72,6 +73,7 @@ def load_library(path: str = LIB_PATH):
     L.recon_filter_stage.argtypes = [vp, vp, ip, ip, vp, sz, vp, ctypes.POINTER(vp)]
     L.recon_backproject.argtypes = [vp, vp, ip, ip, vp, ip, vp, sz, vp]
     L.recon_plan_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]
+    L.recon_run_noalloc.argtypes = [vp, vp, vp, vp]
     L.recon_profile_enable.argtypes = [vp, ip]
     L.recon_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ip)]
     L.recon_sync.argtypes = [vp]
@@ -81,7 +83,8 @@ def load_library(path: str = LIB_PATH):
     L.recon_last_error.argtypes = []
     L.recon_last_error.restype = ctypes.c_char_p
     for name in ("recon_plan", "recon_workspace_size", "recon_run", "recon_filter_stage", "recon_backproject",
-                 "recon_plan_info", "recon_sync", "recon_destroy", "recon_profile_enable", "recon_profile_read"):
+                 "recon_plan_info", "recon_sync", "recon_destroy", "recon_profile_enable", "recon_profile_read",
+                 "recon_run_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -136,6 +139,11 @@ def recon_plan_info(plan) -> tuple[int, int, int]:
 
 def recon_run(plan, images_ptr: int, volume_ptr: int, ws_ptr: int, ws_bytes: int, stream: int):
     _check(load_library().recon_run(plan, images_ptr, volume_ptr, ws_ptr, ws_bytes, stream), "recon_run")
+
+
+def recon_run_noalloc(plan, images_ptr: int, volume_ptr: int, stream: int):
+    """``recon_run`` in the library's static device scratch (no allocation anywhere)."""
+    _check(load_library().recon_run_noalloc(plan, images_ptr, volume_ptr, stream), "recon_run_noalloc")
 
 
 def recon_filter_stage(plan, images_ptr: int, dir_begin: int, dir_count: int, ws_ptr: int, ws_bytes: int,

@@ -485,3 +485,60 @@ int recon_sync(void* stream) {
 }
 
 }  // extern "C"
+
+namespace recon {
+
+void set_last_error(const char* msg) { g_last_error = msg; }
+
+int run_in_scratch(recon_plan_t p, const float* images, float* volume, char* scratch, size_t scratch_bytes,
+                   cudaStream_t s) {
+  if (!p) return fail(RECON_E_INVALID_ARG, "recon_run_noalloc: null plan");
+  const size_t nvox = (size_t)p->nx * p->ny * p->nz;
+  if (nvox > 0 && !volume) return fail(RECON_E_INVALID_ARG, "recon_run_noalloc: null volume");
+  if (p->D > 0 && !images) return fail(RECON_E_INVALID_ARG, "recon_run_noalloc: null images");
+  // Same table head as the caller-owned workspace, then the largest direction block
+  // whose spectra, intermediates and stacks still fit the scratch.
+  const size_t spec = (size_t)p->nv * p->half * 8;
+  const size_t inter = spec * p->nzl;
+  auto need = [&](size_t db) {
+    return p->table_bytes + align256(db * spec) + align256(db * inter) + align256(db * p->stack_dir_bytes);
+  };
+  if (need(1) > scratch_bytes)
+    return fail(RECON_E_UNSUPPORTED_SIZE, "recon_run_noalloc: this plan needs " + std::to_string(need(1)) +
+                                              " bytes of scratch for one direction; the static scratch holds " +
+                                              std::to_string(scratch_bytes));
+  if (p->D == 0 || nvox == 0) {
+    if (nvox > 0 && !p->opt.accumulate) {
+      cudaError_t e = cudaMemsetAsync(volume, 0, nvox * sizeof(float), s);
+      if (e != cudaSuccess) return cuda_fail(e, "recon_run_noalloc: clearing the volume");
+    }
+    return RECON_OK;
+  }
+  size_t db = 1;
+  while ((int)db < p->db && need(db + 1) <= scratch_bytes) ++db;
+  recon::Workspace w;
+  w.dirs = (recon::DirParams*)(scratch + p->off_dirs);
+  w.uA = (uint64_t*)(scratch + p->off_uA);
+  w.ramp = (float*)(scratch + p->off_ramp);
+  w.tw = (float2*)(scratch + p->off_tw);
+  size_t off = p->table_bytes;
+  w.S = (float2*)(scratch + off);
+  off += align256(db * spec);
+  w.T = (float2*)(scratch + off);
+  off += align256(db * inter);
+  w.stack = (void*)(scratch + off);
+  int rc = upload_tables(p, w, s);
+  if (rc) return rc;
+  const int n_blocks = (int)((p->D + db - 1) / db);
+  for (int b = 0; b < n_blocks; ++b) {
+    const int d0 = b * (int)db;
+    const int cnt = (p->D - d0) < (int)db ? (p->D - d0) : (int)db;
+    cudaError_t e = recon::launch_stage_a(p->ca, w, images, d0, cnt, s);
+    if (e != cudaSuccess) return cuda_fail(e, "recon_run_noalloc: stage A launch");
+    e = recon::launch_backproject(p->cb, w.dirs, w.stack, d0, cnt, volume, p->opt.accumulate || b > 0, s);
+    if (e != cudaSuccess) return cuda_fail(e, "recon_run_noalloc: backprojection launch");
+  }
+  return RECON_OK;
+}
+
+}  // namespace recon

@@ -6,6 +6,8 @@
 
 #include <cuda_runtime.h>
 
+struct recon_plan_s;
+
 namespace recon {
 
 // Per-direction constants, built by the plan in FP64 (one 128-byte record per direction).
@@ -63,5 +65,11 @@ struct BackprojConst {
 
 cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
                                int dir_count, float* volume, int accumulate, cudaStream_t stream);
+
+// Whole-operator run with its workspace carved from `scratch` (tables first, then
+// the largest direction block that fits); used by recon_run_noalloc.
+int run_in_scratch(struct ::recon_plan_s* plan, const float* images, float* volume, char* scratch,
+                   size_t scratch_bytes, cudaStream_t stream);
+void set_last_error(const char* msg);
 
 }  // namespace recon
