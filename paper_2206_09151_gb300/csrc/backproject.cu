@@ -118,11 +118,142 @@ __global__ void __launch_bounds__(kTX* kTY) k_backproject(const DirParams* __res
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Single-axis scans about the volume y axis (rot row 1 = (0,1,0) for every view): the
+// detector row is v = j + b_off for every direction, and the u coordinate and the depth
+// layer do not depend on j.  A thread owns an (i, k) voxel column segment of kJ voxels
+// along y: per direction it forms u and the layer once, then walks kJ detector rows with
+// two taps each (four when b_off is a half-integer), accumulating in registers.
+constexpr int kAX = 32, kAZ = 8, kJ = 16;
+
+struct AxisDir {  // per (tile, direction), 32 bytes in shared memory
+  float fa;       // fractional tile-origin u coordinate minus 0.5
+  int ia;         // integer tile-origin u coordinate
+  uint32_t t;     // depth at the tile origin, 2^-24 layer units
+  float af0, af2; // du/di, du/dk
+  uint32_t ti, tk;
+  int pad;
+};
+static_assert(sizeof(AxisDir) == 32, "AxisDir layout");
+
+template <typename ST>
+__device__ __forceinline__ float lerp_row(const ST* p, float fa) {
+  const float v0 = stack_val(p), v1 = stack_val(p + 1);
+  return fmaf(fa, v1 - v0, v0);
+}
+
+template <typename ST, bool TWO_ROWS>
+__global__ void __launch_bounds__(kAX* kAZ) k_backproject_axis(const DirParams* __restrict__ dirs,
+                                                                const ST* __restrict__ stack, BackprojConst c,
+                                                                int dir_begin, int dir_count,
+                                                                float* __restrict__ vol, int accumulate) {
+  extern __shared__ AxisDir s_ax[];
+  const int i0 = blockIdx.x * kAX, k0 = blockIdx.y * kAZ, j0 = blockIdx.z * kJ;
+  const int tx = threadIdx.x % kAX, tz = threadIdx.x / kAX;
+  for (int d = threadIdx.x; d < dir_count; d += blockDim.x) {
+    const DirParams& p = dirs[dir_begin + d];
+    const double a = fma(p.a[0], (double)i0, fma(p.a[2], (double)k0, p.a[3]));  // p.a[1] = 0
+    const double fla = floor(a);
+    AxisDir ad;
+    ad.fa = (float)(a - fla) - 0.5f;
+    ad.ia = (int)fla;
+    ad.t = (uint32_t)p.t[0] + (uint32_t)p.t[1] * (uint32_t)i0 + (uint32_t)p.t[3] * (uint32_t)k0;  // Tj = 0
+    ad.af0 = p.af[0];
+    ad.af2 = p.af[2];
+    ad.ti = (uint32_t)p.t[1];
+    ad.tk = (uint32_t)p.t[3];
+    ad.pad = 0;
+    s_ax[d] = ad;
+  }
+  __syncthreads();
+
+  float acc[kJ];
+#pragma unroll
+  for (int q = 0; q < kJ; ++q) acc[q] = 0.f;
+  // detector row of this thread's first voxel, and whether every row it reads lies in
+  // the stack (rows -1 and nv are the zero border)
+  const int row0 = j0 + c.b_int;
+  const bool rows_inside = row0 >= -1 && row0 + kJ - 1 + (TWO_ROWS ? 1 : 0) <= c.nv;
+  const float ftx = (float)tx, ftz = (float)tz;
+  const int last_layer = c.nz_layers - 1;
+  const float fb = c.b_frac;
+  for (int d = 0; d < dir_count; ++d) {
+    const AxisDir ad = s_ax[d];
+    const float ap = fmaf(ad.af0, ftx, fmaf(ad.af2, ftz, ad.fa));
+    const int layer = min(max((int32_t)(ad.t + ad.ti * (uint32_t)tx + ad.tk * (uint32_t)tz) >> 24, 0), last_layer);
+    const float ta = fminf(fmaxf(ap, (float)(-1 - ad.ia)), (float)(c.nu - 1 - ad.ia)) + kMagic;
+    const int ra = __float_as_int(ta) - kMagicBits;
+    const float fa = __saturatef(ap - (ta - kMagic) + 0.5f);
+    const ST* p = stack + ((size_t)d * c.nz_layers + layer) * c.layer_elems + (ptrdiff_t)(row0 + 1) * c.su +
+                  (ra + ad.ia + 1);
+    if (rows_inside) {
+      if (TWO_ROWS) {
+        float prev = lerp_row(p, fa);
+#pragma unroll
+        for (int q = 0; q < kJ; ++q) {
+          const float next = lerp_row(p + (q + 1) * c.su, fa);
+          acc[q] += fmaf(fb, next - prev, prev);
+          prev = next;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < kJ; ++q) acc[q] += lerp_row(p + q * c.su, fa);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < kJ; ++q) {
+        const int r = row0 + q;
+        const float lo = (r >= -1 && r <= c.nv) ? lerp_row(p + q * c.su, fa) : 0.f;
+        if (TWO_ROWS) {
+          const float hi = (r + 1 >= -1 && r + 1 <= c.nv) ? lerp_row(p + (q + 1) * c.su, fa) : 0.f;
+          acc[q] += fmaf(fb, hi - lo, lo);
+        } else {
+          acc[q] += lo;
+        }
+      }
+    }
+  }
+
+  const int i = i0 + tx, k = k0 + tz;
+  if (i >= c.nx || k >= c.nz) return;
+#pragma unroll
+  for (int q = 0; q < kJ; ++q) {
+    const int j = j0 + q;
+    if (j < c.ny) {
+      float* v = vol + ((size_t)k * c.ny + j) * c.nx + i;
+      *v = accumulate ? *v + acc[q] : acc[q];
+    }
+  }
+}
+
+template <typename ST, bool TWO_ROWS>
+cudaError_t launch_axis(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
+                        int dir_count, float* volume, int accumulate, cudaStream_t stream) {
+  dim3 grid((c.nx + kAX - 1) / kAX, (c.nz + kAZ - 1) / kAZ, (c.ny + kJ - 1) / kJ);
+  const size_t smem = (size_t)dir_count * sizeof(AxisDir);
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_backproject_axis<ST, TWO_ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_backproject_axis<ST, TWO_ROWS><<<grid, kAX * kAZ, smem, stream>>>(dirs, (const ST*)stack, c, dir_begin,
+                                                                      dir_count, volume, accumulate);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
                                int dir_count, float* volume, int accumulate, cudaStream_t stream) {
   if (dir_count <= 0 || c.nx <= 0 || c.ny <= 0 || c.nz <= 0) return cudaSuccess;
+  if (c.axis_y) {
+    const bool two = c.b_frac != 0.f;
+    if (c.stack_bf16)
+      return two ? launch_axis<__nv_bfloat16, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream)
+                 : launch_axis<__nv_bfloat16, false>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream);
+    return two ? launch_axis<float, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream)
+               : launch_axis<float, false>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream);
+  }
   dim3 grid((c.nx + kTX - 1) / kTX, (c.ny + kTY - 1) / kTY, (c.nz + kTZ - 1) / kTZ);
   const size_t smem = (size_t)dir_count * sizeof(TileDir);
   if (c.stack_bf16) {

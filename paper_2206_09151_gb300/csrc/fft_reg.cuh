@@ -1,0 +1,144 @@
+// Register-resident mixed-radix Stockham FFT for one CTA-level group of P/8 threads.
+//
+// Each of the T = P/8 threads of a group holds 8 complex values, element s of thread j
+// being position j + s*T of the sequence, both on input and on output (natural order).
+// The passes use radix 8 while the remaining length allows, then one radix-2 or
+// radix-4 pass; between passes the values go through a padded shared-memory buffer
+// (index i stored at i + i/16, which keeps the 64-bit accesses of a half-warp on
+// distinct banks for these patterns).  Twiddles come from a shared table
+// tw[k] = exp(-2 pi i k / P), k < P.  INV selects the inverse (conjugate) transform,
+// unscaled.  Every thread of the CTA must call it (it uses __syncthreads).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace recon {
+namespace fft {
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// multiply by -i (forward) or +i (inverse)
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+__host__ __device__ constexpr int padded(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int buffer_len(int P) { return P + P / 16 + 1; }
+
+template <bool INV>
+__device__ __forceinline__ void dft2(float2* v) {
+  const float2 a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& a, float2& b, float2& c, float2& d) {
+  const float2 t0 = cadd(a, c), t1 = csub(a, c), t2 = cadd(b, d), t3 = mul_mi<INV>(csub(b, d));
+  a = cadd(t0, t2);
+  c = csub(t0, t2);
+  b = cadd(t1, t3);
+  d = csub(t1, t3);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2* v) {
+  dft4<INV>(v[0], v[1], v[2], v[3]);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2* v) {
+  constexpr float h = 0.70710678118654752f;  // 1/sqrt(2)
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  // o_k *= W8^k, W8 = exp(-+ i pi / 4)
+  o1 = INV ? make_float2(h * (o1.x - o1.y), h * (o1.x + o1.y)) : make_float2(h * (o1.x + o1.y), h * (o1.y - o1.x));
+  o2 = mul_mi<INV>(o2);
+  o3 = INV ? make_float2(-h * (o3.x + o3.y), h * (o3.x - o3.y)) : make_float2(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, o1);
+  v[5] = csub(e1, o1);
+  v[2] = cadd(e2, o2);
+  v[6] = csub(e2, o2);
+  v[3] = cadd(e3, o3);
+  v[7] = csub(e3, o3);
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void dftR(float2* v) {
+  if constexpr (R == 8) dft8<INV>(v);
+  else if constexpr (R == 4) dft4<INV>(v);
+  else dft2<INV>(v);
+}
+
+// One Stockham pass of radix R at sub-length Ns (product of the radices before it).
+template <int P, int R, int Ns, bool INV>
+__device__ __forceinline__ void pass(float2 (&x)[8], float2* buf, const float2* tw, int j) {
+  constexpr int T = P / 8, NB = 8 / R, STRIDE = P / R;
+  constexpr bool FIRST = Ns == 1, LAST = Ns * R == P;
+  float2 v[8];
+  if constexpr (FIRST) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q * R + r] = x[q + r * NB];
+  } else {
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[q * R + r] = buf[padded(j + q * T + r * STRIDE)];
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int kb = (j + q * T) & (Ns - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = tw[kb * r * (P / (Ns * R))];
+        if (INV) w.y = -w.y;
+        v[q * R + r] = cmul(v[q * R + r], w);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NB; ++q) dftR<R, INV>(v + q * R);
+  if constexpr (LAST) {
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+#pragma unroll
+      for (int r = 0; r < R; ++r) x[q + r * NB] = v[q * R + r];
+  } else {
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int b = j + q * T;
+      const int base = (b / Ns) * Ns * R + (b & (Ns - 1));
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[padded(base + r * Ns)] = v[q * R + r];
+    }
+  }
+}
+
+template <int P, int Ns, bool INV>
+__device__ __forceinline__ void stockham(float2 (&x)[8], float2* buf, const float2* tw, int j) {
+  constexpr int rem = P / Ns;
+  constexpr int R = (rem % 8 == 0) ? 8 : rem;
+  pass<P, R, Ns, INV>(x, buf, tw, j);
+  if constexpr (Ns * R < P) stockham<P, Ns * R, INV>(x, buf, tw, j);
+}
+
+// Length-P FFT of the 8 values a thread holds (positions j + s*P/8), P >= 16.
+template <int P, bool INV>
+__device__ __forceinline__ void block_fft(float2 (&x)[8], float2* buf, const float2* tw, int j) {
+  static_assert(P >= 16 && (P & (P - 1)) == 0, "P must be a power of two >= 16");
+  stockham<P, 1, INV>(x, buf, tw, j);
+}
+
+}  // namespace fft
+}  // namespace recon

@@ -166,10 +166,12 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
           }
         }
       if (o.ramp_mode == RECON_RAMP_SINGLE_AXIS &&
-          (std::fabs(R[3]) > 1e-9 || std::fabs(R[5]) > 1e-9 || std::fabs(R[4] - 1.0) > 1e-9)) {
+          (std::fabs(R[3] - geom->rot[3]) > 1e-9 || std::fabs(R[4] - geom->rot[4]) > 1e-9 ||
+           std::fabs(R[5] - geom->rot[5]) > 1e-9)) {
         delete p;
-        return fail(RECON_E_INVALID_ARG, "recon_plan: single-axis ramp needs rot[n] row 1 = (0, 1, 0) (n = " +
-                                             std::to_string(n) + ")");
+        return fail(RECON_E_INVALID_ARG,
+                    "recon_plan: single-axis ramp needs one rotation axis: rot[n] row 1 must equal rot[0] row 1 (n = " +
+                        std::to_string(n) + ")");
       }
       if (!std::isfinite(defocus[n])) {
         delete p;
@@ -260,6 +262,17 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
   cb.su = ca.su;
   cb.layer_elems = ca.layer_elems;
   cb.stack_bf16 = ca.stack_bf16;
+  cb.axis_y = D > 0;
+  for (int n = 0; n < D; ++n) {
+    const double* R = geom->rot + 9 * (size_t)n;
+    if (!(R[3] == 0.0 && R[4] == 1.0 && R[5] == 0.0 && R[1] == 0.0 && R[7] == 0.0)) cb.axis_y = 0;
+  }
+  {
+    const double boff = 0.5 * (p->nv - 1) - 0.5 * (p->ny - 1);  // v = j + boff when row 1 = (0,1,0)
+    const double fl = std::floor(boff);
+    cb.b_int = (int)fl;
+    cb.b_frac = (float)(boff - fl);
+  }
 
   const size_t elem = ca.stack_bf16 ? 2 : 4;
   p->stack_dir_bytes = (size_t)nz_layers * ca.layer_elems * elem;

@@ -61,6 +61,12 @@ struct BackprojConst {
   int su;
   size_t layer_elems;
   int stack_bf16;
+  // Every view keeps the detector v axis on the volume y axis (rot row 1 = (0,1,0)
+  // exactly): then v = j + b_off for every direction and the layer and u coordinate
+  // are constant along a voxel column in y (the single-axis kernel).
+  int axis_y;
+  int b_int;      // floor(b_off)
+  float b_frac;   // b_off - floor(b_off), 0 or 1/2
 };
 
 cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,

@@ -47,11 +47,12 @@ __all__ = [
 
 
 # ----------------------------------------------------------------------------- geometry
-def single_axis_rotations(n_dir: int, span: float = math.pi, start: float = 0.0) -> np.ndarray:
-    """Rotations for ``n_dir`` tilts about the volume y axis, evenly over ``[start, start+span)``.
+def single_axis_rotations(n_dir: int, span: float = math.pi, start: float = 0.0, axis=None) -> np.ndarray:
+    """Rotations for ``n_dir`` tilts about one fixed axis, evenly over ``[start, start+span)``.
 
-    The detector v axis stays the volume y axis, so this is the single-axis scan of
-    Sec. 2 for which the sampling density reduces to the ramp |q_x|.
+    The axis is the volume y axis by default, else the unit vector along ``axis``; it
+    stays the detector v axis for every view (row 1 of every rotation), which is the
+    single-axis scan of Sec. 2 whose sampling density reduces to the ramp |q_x|.
     """
     th = start + span * np.arange(n_dir, dtype=np.float64) / max(n_dir, 1)
     c, s = np.cos(th), np.sin(th)
@@ -61,6 +62,15 @@ def single_axis_rotations(n_dir: int, span: float = math.pi, start: float = 0.0)
     rot[:, 1, 1] = 1.0
     rot[:, 2, 0] = -s
     rot[:, 2, 2] = c
+    if axis is not None:
+        v = np.asarray(axis, np.float64) / np.linalg.norm(axis)
+        # Q: a rotation taking e_y to v (Rodrigues about e_y x v); rot_n Q^T has row 1 = v
+        ey = np.array([0.0, 1.0, 0.0])
+        w = np.cross(ey, v)
+        sn, cs = np.linalg.norm(w), float(ey @ v)
+        K = np.array([[0, -w[2], w[1]], [w[2], 0, -w[0]], [-w[1], w[0], 0]]) / (sn if sn > 0 else 1.0)
+        Q = np.eye(3) + sn * K + (1 - cs) * (K @ K)
+        rot = rot @ Q.T
     return rot
 
 

@@ -81,9 +81,9 @@ def test_stage_a_layer_stack_matches_oracle(case):
 
 
 # ---------------------------------------------------------------- stage B
-def _stage_b_case(grid, nu, nv, nzl, D, seed, start=0.1, span=math.pi):
+def _stage_b_case(grid, nu, nv, nzl, D, seed, start=0.1, span=math.pi, axis=None):
     rng = np.random.default_rng(seed)
-    rot = ph.single_axis_rotations(D, span=span, start=start)
+    rot = ph.single_axis_rotations(D, span=span, start=start, axis=axis)
     r = make(rot, nu, nv, grid, lam=1e-10, delta=1e-9, defocus=np.zeros(D), nz_layers=nzl, dir_block=D)
     stacks = rng.standard_normal((D, nzl, nv, nu)).astype(np.float32)
     padded = np.zeros((D, nzl, nv + 2, nu + 2), np.float32)
@@ -102,14 +102,18 @@ def _stage_b_case(grid, nu, nv, nzl, D, seed, start=0.1, span=math.pi):
     return got.ravel(), ref
 
 
-@pytest.mark.parametrize("grid,nu,nv,nzl,D", [
-    ((37, 20, 9), 41, 23, 5, 7),
-    ((64, 64, 64), 64, 64, 8, 90),
-    ((33, 70, 130), 160, 72, 16, 11),
-    ((1, 1, 1), 1, 1, 1, 2),
-])
-def test_stage_b_backprojection_matches_oracle(grid, nu, nv, nzl, D):
-    got, ref = _stage_b_case(grid, nu, nv, nzl, D, seed=sum(grid) + D)
+@pytest.mark.parametrize("grid,nu,nv,nzl,D,axis", [
+    ((37, 20, 9), 41, 23, 5, 7, None),          # half-integer row offset (two detector rows)
+    ((64, 64, 64), 64, 64, 8, 90, None),
+    ((33, 70, 130), 160, 72, 16, 11, None),
+    ((20, 50, 10), 30, 24, 3, 5, None),         # volume taller than the detector
+    ((20, 51, 10), 30, 24, 3, 5, None),         # ... with a half-integer offset
+    ((1, 1, 1), 1, 1, 1, 2, None),
+    ((37, 20, 9), 41, 23, 5, 7, (0.3, 1.0, -0.2)),   # tilted axis: general kernel
+    ((48, 40, 56), 64, 64, 6, 30, (0.0, 1.0, 0.5)),
+], ids=["y-half", "y-64", "y-tall", "y-rows-outside", "y-rows-outside-half", "y-1", "tilted", "tilted-2"])
+def test_stage_b_backprojection_matches_oracle(grid, nu, nv, nzl, D, axis):
+    got, ref = _stage_b_case(grid, nu, nv, nzl, D, seed=sum(grid) + D, axis=axis)
     assert rel_l2(got, ref) <= TOL_F32
     # any layer or tap decided differently would show as an O(1) error at that voxel
     assert np.max(np.abs(got - ref)) <= 1e-4 * max(np.max(np.abs(ref)), 1.0)
