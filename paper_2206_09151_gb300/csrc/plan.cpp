@@ -224,8 +224,8 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
         p->ramp[m] = (float)((M_PI / D) * delta * s / ((double)P * P));
       }
     }
-    p->tw.resize(P / 2);
-    for (int j = 0; j < P / 2; ++j) {
+    p->tw.resize(P);
+    for (int j = 0; j < P; ++j) {
       p->tw[j].x = (float)std::cos(2.0 * M_PI * j / P);
       p->tw[j].y = (float)-std::sin(2.0 * M_PI * j / P);
     }
@@ -297,7 +297,7 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
   p->off_ramp = off;
   off = align256(off + sizeof(float) * p->half);
   p->off_tw = off;
-  off = align256(off + sizeof(float2) * (P / 2));
+  off = align256(off + sizeof(float2) * P);
   p->table_bytes = off;
   p->off_S = off;
   off = align256(off + (size_t)db * p->nv * p->half * 8);

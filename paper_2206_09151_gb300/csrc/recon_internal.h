@@ -43,9 +43,9 @@ struct Workspace {
   DirParams* dirs;      // [D]
   uint64_t* uA;         // [D][Nz]: pi lambda (R_n - z_k)/(P delta)^2 per unit m, fraction of 2 pi
   float* ramp;          // [P/2+1]: ramp weight, includes pi/D and 1/P^2
-  float2* tw;           // [P/2]: exp(-2 pi i j / P)
+  float2* tw;           // [P]: exp(-2 pi i j / P)
   float2* S;            // [DB][nv][P/2+1]: row transforms
-  float2* T;            // [DB][Nz][nv][P/2+1]: per-layer column inverse transforms
+  float2* T;            // [DB][Nz][P/2+1][nv]: per-layer column inverse transforms (column-major)
   void* stack;          // [DB][Nz][nv+2][nu+2]
 };
 

@@ -1,58 +1,35 @@
 // Stage A of the layered UTR path: contrast -> 2D DFT -> per-layer CTF inverse and
 // ramp -> inverse 2D DFT -> cropped layer stack (Sec. 2, Eq. 4, 7, 11; ramp of Sec. 2).
 //
-// Three kernels per block of directions, all shared-memory radix-2 FFTs of length P:
-//   k_rows_fwd  two image rows per CTA packed as one complex row (real + i real),
-//               forward FFT, split into the two half spectra      -> S[n][v][0..P/2]
-//   k_cols      CB adjacent spectrum columns per CTA: forward FFT along v (rows >= nv
-//               are the zero padding), kept in shared memory; then for every layer k:
-//               multiply by H_k(q) W(q_u), inverse FFT along v, keep v < nv
-//                                                                 -> T[n][k][v][0..P/2]
-//   k_rows_inv  two rows of one layer per CTA: Hermitian-extend both half spectra,
-//               pack as real + i real, inverse FFT, crop u < nu   -> stack (zero border)
+// Three kernels per block of directions:
+//   k_rows_fwd  two image rows packed as one complex row (real + i real), forward FFT,
+//               split into the two half spectra                    -> S[n][v][0..P/2]
+//   k_cols      one spectrum column per group of P/8 threads: forward FFT along v (rows
+//               >= nv are the zero padding), kept in registers; then for every layer
+//               k: multiply by H_k(q) W(q_u), inverse FFT along v, store v < nv
+//                                                                   -> T[n][k][col][v]
+//   k_rows_inv  two rows of one layer per group: Hermitian-extend both half spectra,
+//               pack as real + i real, inverse FFT, crop u < nu     -> stack (zero border)
+// For P >= 16 the FFTs are register-resident mixed-radix Stockham transforms
+// (fft_reg.cuh); tiny images (P <= 8) use a shared-memory radix-2 transform.
 // The image sits at offset 0 of the P x P frame; by the shift invariance of the
 // circular filters this equals any other placement with the same crop.
 #include <cuda_bf16.h>
 
+#include "fft_reg.cuh"
 #include "recon_internal.h"
 
 namespace recon {
 namespace {
 
-constexpr int kColsPerCta = 4;
+using fft::cmul;
+using fft::padded;
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
+constexpr int kThreads = 256;
 
-__device__ __forceinline__ int bitrev(int i, int logP) { return (int)(__brev((unsigned)i) >> (32 - logP)); }
-
-// In-place radix-2 decimation-in-time FFT of `ntr` transforms of length P held at
-// data + t * ld, input in bit-reversed order, output in natural order.  tw[j] =
-// exp(-2 pi i j / P); INV uses the conjugate twiddles (no 1/P scaling).
-template <bool INV>
-__device__ void fft_radix2(float2* data, int ld, int ntr, int P, int logP, const float2* tw) {
-  const int halfP = P >> 1;
-  const int total = ntr * halfP;
-  for (int s = 0; s < logP; ++s) {
-    const int half = 1 << s;
-    const int tw_shift = logP - 1 - s;
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int t = idx >> (logP - 1);
-      const int j = idx & (halfP - 1);
-      const int pos = j & (half - 1);
-      const int i1 = ((j - pos) << 1) + pos;
-      float2* d = data + t * ld;
-      float2 w = tw[pos << tw_shift];
-      if (INV) w.y = -w.y;
-      const float2 a = d[i1];
-      const float2 wb = cmul(w, d[i1 + half]);
-      d[i1] = make_float2(a.x + wb.x, a.y + wb.y);
-      d[i1 + half] = make_float2(a.x - wb.x, a.y - wb.y);
-    }
-  }
-  __syncthreads();
+template <int P>
+__host__ __device__ constexpr int groups_per_cta() {
+  return kThreads / (P / 8) > 0 ? kThreads / (P / 8) : 1;
 }
 
 __device__ __forceinline__ float contrast_of(float x, int input_mode) {
@@ -60,92 +37,13 @@ __device__ __forceinline__ float contrast_of(float x, int input_mode) {
   return input_mode == 0 ? logf(fmaxf(x, 1e-6f)) : x;
 }
 
-__global__ void k_rows_fwd(const float* __restrict__ images, float2* __restrict__ S, const float2* __restrict__ twg,
-                           StageAConst c, int dir_begin) {
-  extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* z = sm + (c.P >> 1);
-  const int n = blockIdx.y;
-  const int v0 = blockIdx.x * 2;
-  const bool two = v0 + 1 < c.nv;
-  const float* im = images + (size_t)(dir_begin + n) * c.nu * c.nv;
-  for (int i = threadIdx.x; i < (c.P >> 1); i += blockDim.x) tw[i] = twg[i];
-  for (int i = threadIdx.x; i < c.P; i += blockDim.x) {
-    float x1 = 0.f, x2 = 0.f;
-    if (i < c.nu) {
-      x1 = contrast_of(im[(size_t)v0 * c.nu + i], c.input_mode);
-      if (two) x2 = contrast_of(im[(size_t)(v0 + 1) * c.nu + i], c.input_mode);
-    }
-    z[bitrev(i, c.logP)] = make_float2(x1, x2);
-  }
-  fft_radix2<false>(z, c.P, 1, c.P, c.logP, tw);
-  float2* s1 = S + ((size_t)n * c.nv + v0) * c.half;
-  for (int m = threadIdx.x; m < c.half; m += blockDim.x) {
-    const float2 zm = z[m & (c.P - 1)];
-    const float2 zc = z[(c.P - m) & (c.P - 1)];
-    // X1 = (Z[m] + conj Z[P-m]) / 2,  X2 = (Z[m] - conj Z[P-m]) / (2i)
-    s1[m] = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
-    if (two) s1[c.half + m] = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
-  }
-}
-
-// sin(chi_k) for the integer squared frequency msq = m_u^2 + m_v^2.  chi/(2 pi) is
-// accumulated modulo 1 in 64-bit fixed point (exact modular products), so the range
-// reduction of chi (hundreds of radians at the band edge) loses nothing; the top 32
-// bits give chi in (-pi, pi] to 2^-31 turns before the FP32 sine.
-__device__ __forceinline__ float sin_chi(uint64_t uA, uint64_t uC, uint64_t uW, uint32_t msq) {
-  const uint64_t m = msq;
-  const uint64_t x = uA * m + uC * (m * m) - uW;
+// sin(chi_k) from x = chi/(2 pi) modulo 1 in 64-bit fixed point.  The constants are
+// fractions of a turn, so the products with the integer squared frequency m are exact
+// modulo 2 pi: the range reduction of chi (hundreds of radians at the band edge) loses
+// nothing, and the top 32 bits give chi in [-pi, pi) to 2^-31 turns.
+__device__ __forceinline__ float sin_from_turns(uint64_t x) {
   const int32_t hi = (int32_t)(x >> 32);
   return sinpif((float)hi * 4.656612873077393e-10f);  // hi * 2^-31 = chi / pi in [-1, 1)
-}
-
-__global__ void k_cols(const float2* __restrict__ S, float2* __restrict__ T, const float2* __restrict__ twg,
-                       const uint64_t* __restrict__ uA, const float* __restrict__ ramp, StageAConst c,
-                       int dir_begin) {
-  extern __shared__ float2 sm[];
-  const int ld = c.P + 1;  // one-element skew between the columns' transforms
-  float2* tw = sm;
-  float2* G = tw + (c.P >> 1);
-  float2* Wk = G + kColsPerCta * ld;
-  const int n = blockIdx.y;
-  const int c0 = blockIdx.x * kColsPerCta;
-  for (int i = threadIdx.x; i < (c.P >> 1); i += blockDim.x) tw[i] = twg[i];
-  const float2* Sn = S + (size_t)n * c.nv * c.half;
-  for (int idx = threadIdx.x; idx < kColsPerCta * c.P; idx += blockDim.x) {
-    const int t = idx % kColsPerCta;
-    const int v = idx / kColsPerCta;
-    const int col = c0 + t;
-    float2 val = make_float2(0.f, 0.f);
-    if (v < c.nv && col < c.half) val = Sn[(size_t)v * c.half + col];
-    G[t * ld + bitrev(v, c.logP)] = val;
-  }
-  fft_radix2<false>(G, ld, kColsPerCta, c.P, c.logP, tw);
-  const uint64_t* uAn = uA + (size_t)(dir_begin + n) * c.nz_layers;
-  for (int k = 0; k < c.nz_layers; ++k) {
-    const uint64_t uAk = uAn[k];
-    for (int idx = threadIdx.x; idx < kColsPerCta * c.P; idx += blockDim.x) {
-      const int t = idx / c.P;
-      const int m = idx - t * c.P;
-      const int col = min(c0 + t, c.half - 1);
-      const int mv = m < (c.P >> 1) ? m : m - c.P;
-      float f = ramp[col];
-      if (c.filter) {
-        const float s = sin_chi(uAk, c.uC, c.uW, (uint32_t)(col * col + mv * mv));
-        f *= c.pref * s / fmaf(s, s, c.eps);  // real part of the Eq. 11 bracket
-      }
-      const float2 g = G[t * ld + m];
-      Wk[t * ld + bitrev(m, c.logP)] = make_float2(g.x * f, g.y * f);
-    }
-    fft_radix2<true>(Wk, ld, kColsPerCta, c.P, c.logP, tw);
-    float2* Tk = T + ((size_t)n * c.nz_layers + k) * c.nv * c.half;
-    for (int idx = threadIdx.x; idx < kColsPerCta * c.nv; idx += blockDim.x) {
-      const int t = idx % kColsPerCta;
-      const int v = idx / kColsPerCta;
-      if (c0 + t < c.half) Tk[(size_t)v * c.half + c0 + t] = Wk[t * ld + v];
-    }
-    __syncthreads();
-  }
 }
 
 template <typename OutT>
@@ -155,38 +53,297 @@ __device__ __forceinline__ float to_stack<float>(float x) { return x; }
 template <>
 __device__ __forceinline__ __nv_bfloat16 to_stack<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
 
-template <typename OutT>
-__global__ void k_rows_inv(const float2* __restrict__ T, OutT* __restrict__ stack, const float2* __restrict__ twg,
-                           StageAConst c) {
-  extern __shared__ float2 sm[];
-  float2* tw = sm;
-  float2* z = sm + (c.P >> 1);
-  const int n = blockIdx.z;
-  const int k = blockIdx.y;
-  const int v0 = blockIdx.x * 2;
-  const bool two = v0 + 1 < c.nv;
-  for (int i = threadIdx.x; i < (c.P >> 1); i += blockDim.x) tw[i] = twg[i];
-  const float2* X1 = T + (((size_t)n * c.nz_layers + k) * c.nv + v0) * c.half;
-  const float2* X2 = X1 + c.half;
-  const int hP = c.P >> 1;
-  for (int m = threadIdx.x; m < c.P; m += blockDim.x) {
+// ------------------------------------------------------------------ register FFT kernels
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_rows_fwd(const float* __restrict__ images, float2* __restrict__ S,
+                                                        const float2* __restrict__ twg, StageAConst c,
+                                                        int dir_begin) {
+  constexpr int TT = P / 8, G = groups_per_cta<P>(), L = fft::buffer_len(P);
+  __shared__ float2 tw[P];
+  __shared__ float2 buf_all[G * L];
+  const int g = threadIdx.x / TT, j = threadIdx.x % TT;
+  float2* buf = buf_all + g * L;
+  for (int i = threadIdx.x; i < P; i += kThreads) tw[i] = twg[i];
+  const int n = blockIdx.y;
+  const int v0 = 2 * (blockIdx.x * G + g);
+  const bool row1 = v0 < c.nv, row2 = v0 + 1 < c.nv;
+  const float* im = images + (size_t)(dir_begin + n) * c.nu * c.nv;
+  float2 x[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int u = j + s * TT;
+    const bool in = u < c.nu;
+    const float x1 = (row1 && in) ? contrast_of(im[(size_t)v0 * c.nu + u], c.input_mode) : 0.f;
+    const float x2 = (row2 && in) ? contrast_of(im[(size_t)(v0 + 1) * c.nu + u], c.input_mode) : 0.f;
+    x[s] = make_float2(x1, x2);
+  }
+  __syncthreads();
+  fft::block_fft<P, false>(x, buf, tw, j);
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 8; ++s) buf[padded(j + s * TT)] = x[s];
+  __syncthreads();
+  if (!row1) return;
+  float2* s1 = S + ((size_t)n * c.nv + v0) * c.half;
+  for (int m = j; m < c.half; m += TT) {
+    const float2 zm = buf[padded(m & (P - 1))];
+    const float2 zc = buf[padded((P - m) & (P - 1))];
+    // X1 = (Z[m] + conj Z[P-m]) / 2,  X2 = (Z[m] - conj Z[P-m]) / (2i)
+    s1[m] = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
+    if (row2) s1[c.half + m] = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_cols(const float2* __restrict__ S, float2* __restrict__ T,
+                                                    const float2* __restrict__ twg, const uint64_t* __restrict__ uA,
+                                                    const float* __restrict__ ramp, StageAConst c, int dir_begin) {
+  constexpr int TT = P / 8, CB = groups_per_cta<P>(), L = fft::buffer_len(P);
+  __shared__ float2 tw[P];
+  __shared__ float2 buf_all[CB * L];
+  const int g = threadIdx.x / TT, j = threadIdx.x % TT;
+  float2* buf = buf_all + g * L;
+  for (int i = threadIdx.x; i < P; i += kThreads) tw[i] = twg[i];
+  const int n = blockIdx.y;
+  const int c0 = blockIdx.x * CB;
+  const int col = c0 + g;
+  const float2* Sn = S + (size_t)n * c.nv * c.half;
+  // coalesced fill of rows v < nv of the CTA's CB columns
+  for (int idx = threadIdx.x; idx < c.nv * CB; idx += kThreads) {
+    const int t = idx % CB, v = idx / CB;
+    buf_all[t * L + padded(v)] = (c0 + t < c.half) ? Sn[(size_t)v * c.half + c0 + t] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  float2 xg[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int v = j + s * TT;
+    xg[s] = v < c.nv ? buf[padded(v)] : make_float2(0.f, 0.f);
+  }
+  fft::block_fft<P, false>(xg, buf, tw, j);  // G(col, m_v) at m_v = j + s*TT, kept for all layers
+
+  const bool ok = col < c.half;
+  const int colc = ok ? col : c.half - 1;
+  const float w = ramp[colc];
+  uint32_t msq[8];
+  uint64_t base[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int m = j + s * TT;
+    const int mv = m < P / 2 ? m : m - P;
+    msq[s] = (uint32_t)(colc * colc + mv * mv);
+    const uint64_t m64 = msq[s];
+    base[s] = c.uC * (m64 * m64) - c.uW;
+  }
+  const uint64_t* uAn = uA + (size_t)(dir_begin + n) * c.nz_layers;
+  float2* Tn = T + (size_t)n * c.nz_layers * c.half * c.nv;
+  for (int k = 0; k < c.nz_layers; ++k) {
+    const uint64_t uAk = uAn[k];
+    float2 x[8];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      float f = w;
+      if (c.filter) {
+        const float sn = sin_from_turns(uAk * (uint64_t)msq[s] + base[s]);
+        f *= c.pref * __fdividef(sn, fmaf(sn, sn, c.eps));  // real part of the Eq. 11 bracket
+      }
+      x[s] = make_float2(xg[s].x * f, xg[s].y * f);
+    }
+    fft::block_fft<P, true>(x, buf, tw, j);
+    if (ok) {
+      float2* out = Tn + ((size_t)k * c.half + col) * c.nv;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {
+        const int v = j + s * TT;
+        if (v < c.nv) out[v] = x[s];
+      }
+    }
+  }
+}
+
+template <int P, typename OutT>
+__global__ void __launch_bounds__(kThreads) k_rows_inv(const float2* __restrict__ T, OutT* __restrict__ stack,
+                                                        const float2* __restrict__ twg, StageAConst c) {
+  constexpr int TT = P / 8, G = groups_per_cta<P>(), L = fft::buffer_len(P), H = P / 2 + 1;
+  constexpr int TILE = 2 * G * H, BUF = G * L;
+  __shared__ float2 tw[P];
+  // the half-spectrum tile is read once, before the FFT's first exchange: the
+  // exchange buffer reuses its memory
+  __shared__ float2 shared_mem[TILE > BUF ? TILE : BUF];
+  float2* tile = shared_mem;
+  const int g = threadIdx.x / TT, j = threadIdx.x % TT;
+  float2* buf = shared_mem + g * L;
+  for (int i = threadIdx.x; i < P; i += kThreads) tw[i] = twg[i];
+  const int n = blockIdx.z, k = blockIdx.y;
+  const int vbase = blockIdx.x * 2 * G;
+  const float2* Tk = T + ((size_t)n * c.nz_layers + k) * H * c.nv;
+  for (int idx = threadIdx.x; idx < TILE; idx += kThreads) {
+    const int vv = idx % (2 * G), cc = idx / (2 * G);
+    const int v = vbase + vv;
+    tile[vv * H + cc] = v < c.nv ? Tk[(size_t)cc * c.nv + v] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const int v0 = vbase + 2 * g;
+  const float2* X1 = tile + (2 * g) * H;
+  const float2* X2 = X1 + H;
+  float2 x[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int m = j + s * TT;
     float2 a, b;
-    if (m <= hP) {
+    if (m <= P / 2) {
       a = X1[m];
-      b = two ? X2[m] : make_float2(0.f, 0.f);
-      if (m == 0 || m == hP) {  // C2R: DC and Nyquist bins are real
+      b = X2[m];
+      if (m == 0 || m == P / 2) {  // C2R: DC and Nyquist bins are real
         a.y = 0.f;
         b.y = 0.f;
       }
     } else {  // Hermitian extension X[m] = conj X[P - m]
-      a = X1[c.P - m];
+      a = X1[P - m];
+      b = X2[P - m];
       a.y = -a.y;
-      b = two ? X2[c.P - m] : make_float2(0.f, 0.f);
       b.y = -b.y;
     }
-    z[bitrev(m, c.logP)] = make_float2(a.x - b.y, a.y + b.x);  // a + i b
+    x[s] = make_float2(a.x - b.y, a.y + b.x);  // a + i b
   }
-  fft_radix2<true>(z, c.P, 1, c.P, c.logP, tw);
+  fft::block_fft<P, true>(x, buf, tw, j);
+  OutT* Lk = stack + ((size_t)n * c.nz_layers + k) * c.layer_elems;
+  const int su = c.su;
+  if (v0 < c.nv) {
+    const bool two = v0 + 1 < c.nv;
+    OutT* r1 = Lk + (size_t)(v0 + 1) * su + 1;
+    OutT* r2 = r1 + su;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int u = j + s * TT;
+      if (u < c.nu) {
+        r1[u] = to_stack<OutT>(x[s].x);
+        if (two) r2[u] = to_stack<OutT>(x[s].y);
+      }
+    }
+    if (j == 0) {  // left and right border columns
+      r1[-1] = to_stack<OutT>(0.f);
+      r1[c.nu] = to_stack<OutT>(0.f);
+      if (two) {
+        r2[-1] = to_stack<OutT>(0.f);
+        r2[c.nu] = to_stack<OutT>(0.f);
+      }
+    }
+  }
+  if (blockIdx.x == 0)  // top border row
+    for (int i = threadIdx.x; i < su; i += kThreads) Lk[i] = to_stack<OutT>(0.f);
+  if (vbase + 2 * G >= c.nv)  // bottom border row
+    for (int i = threadIdx.x; i < su; i += kThreads) Lk[(size_t)(c.nv + 1) * su + i] = to_stack<OutT>(0.f);
+}
+
+// ------------------------------------------------------------------ radix-2 fallback (P <= 8)
+__device__ __forceinline__ int bitrev(int i, int logP) { return (int)(__brev((unsigned)i) >> (32 - logP)); }
+
+template <bool INV>
+__device__ void fft_radix2(float2* data, int P, int logP, const float2* tw) {
+  const int halfP = P >> 1;
+  for (int s = 0; s < logP; ++s) {
+    const int half = 1 << s;
+    const int tw_shift = logP - 1 - s;
+    __syncthreads();
+    for (int jj = threadIdx.x; jj < halfP; jj += blockDim.x) {
+      const int pos = jj & (half - 1);
+      const int i1 = ((jj - pos) << 1) + pos;
+      float2 w = tw[pos << tw_shift];
+      if (INV) w.y = -w.y;
+      const float2 a = data[i1];
+      const float2 wb = cmul(w, data[i1 + half]);
+      data[i1] = make_float2(a.x + wb.x, a.y + wb.y);
+      data[i1 + half] = make_float2(a.x - wb.x, a.y - wb.y);
+    }
+  }
+  __syncthreads();
+}
+
+__global__ void k_small_rows_fwd(const float* __restrict__ images, float2* __restrict__ S,
+                                 const float2* __restrict__ twg, StageAConst c, int dir_begin) {
+  __shared__ float2 tw[8];
+  __shared__ float2 z[8];
+  const int n = blockIdx.y;
+  const int v0 = blockIdx.x * 2;
+  const bool two = v0 + 1 < c.nv;
+  const float* im = images + (size_t)(dir_begin + n) * c.nu * c.nv;
+  for (int i = threadIdx.x; i < c.P; i += blockDim.x) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < c.P; i += blockDim.x) {
+    float x1 = 0.f, x2 = 0.f;
+    if (i < c.nu) {
+      x1 = contrast_of(im[(size_t)v0 * c.nu + i], c.input_mode);
+      if (two) x2 = contrast_of(im[(size_t)(v0 + 1) * c.nu + i], c.input_mode);
+    }
+    z[bitrev(i, c.logP)] = make_float2(x1, x2);
+  }
+  fft_radix2<false>(z, c.P, c.logP, tw);
+  float2* s1 = S + ((size_t)n * c.nv + v0) * c.half;
+  for (int m = threadIdx.x; m < c.half; m += blockDim.x) {
+    const float2 zm = z[m & (c.P - 1)];
+    const float2 zc = z[(c.P - m) & (c.P - 1)];
+    s1[m] = make_float2(0.5f * (zm.x + zc.x), 0.5f * (zm.y - zc.y));
+    if (two) s1[c.half + m] = make_float2(0.5f * (zm.y + zc.y), -0.5f * (zm.x - zc.x));
+  }
+}
+
+__global__ void k_small_cols(const float2* __restrict__ S, float2* __restrict__ T, const float2* __restrict__ twg,
+                             const uint64_t* __restrict__ uA, const float* __restrict__ ramp, StageAConst c,
+                             int dir_begin) {
+  __shared__ float2 tw[8];
+  __shared__ float2 G[8];
+  __shared__ float2 Wk[8];
+  const int n = blockIdx.y;
+  const int col = blockIdx.x;  // one column per CTA
+  for (int i = threadIdx.x; i < c.P; i += blockDim.x) tw[i] = twg[i];
+  const float2* Sn = S + (size_t)n * c.nv * c.half;
+  for (int v = threadIdx.x; v < c.P; v += blockDim.x)
+    G[bitrev(v, c.logP)] = v < c.nv ? Sn[(size_t)v * c.half + col] : make_float2(0.f, 0.f);
+  fft_radix2<false>(G, c.P, c.logP, tw);
+  const uint64_t* uAn = uA + (size_t)(dir_begin + n) * c.nz_layers;
+  for (int k = 0; k < c.nz_layers; ++k) {
+    for (int m = threadIdx.x; m < c.P; m += blockDim.x) {
+      const int mv = m < (c.P >> 1) ? m : m - c.P;
+      const uint64_t msq = (uint64_t)(col * col + mv * mv);
+      float f = ramp[col];
+      if (c.filter) {
+        const float sn = sin_from_turns(uAn[k] * msq + c.uC * (msq * msq) - c.uW);
+        f *= c.pref * __fdividef(sn, fmaf(sn, sn, c.eps));
+      }
+      Wk[bitrev(m, c.logP)] = make_float2(G[m].x * f, G[m].y * f);
+    }
+    fft_radix2<true>(Wk, c.P, c.logP, tw);
+    float2* out = T + (((size_t)n * c.nz_layers + k) * c.half + col) * c.nv;
+    for (int v = threadIdx.x; v < c.nv; v += blockDim.x) out[v] = Wk[v];
+    __syncthreads();
+  }
+}
+
+template <typename OutT>
+__global__ void k_small_rows_inv(const float2* __restrict__ T, OutT* __restrict__ stack,
+                                 const float2* __restrict__ twg, StageAConst c) {
+  __shared__ float2 tw[8];
+  __shared__ float2 z[8];
+  const int n = blockIdx.z, k = blockIdx.y;
+  const int v0 = blockIdx.x * 2;
+  const bool two = v0 + 1 < c.nv;
+  for (int i = threadIdx.x; i < c.P; i += blockDim.x) tw[i] = twg[i];
+  const float2* Tk = T + ((size_t)n * c.nz_layers + k) * c.half * c.nv;
+  const int hP = c.P >> 1;
+  for (int m = threadIdx.x; m < c.P; m += blockDim.x) {
+    const int mm = m <= hP ? m : c.P - m;
+    float2 a = Tk[(size_t)mm * c.nv + v0];
+    float2 b = two ? Tk[(size_t)mm * c.nv + v0 + 1] : make_float2(0.f, 0.f);
+    if (m == 0 || m == hP) {
+      a.y = 0.f;
+      b.y = 0.f;
+    } else if (m > hP) {
+      a.y = -a.y;
+      b.y = -b.y;
+    }
+    z[bitrev(m, c.logP)] = make_float2(a.x - b.y, a.y + b.x);
+  }
+  fft_radix2<true>(z, c.P, c.logP, tw);
   OutT* L = stack + ((size_t)n * c.nz_layers + k) * c.layer_elems;
   const int su = c.su;
   for (int u = (int)threadIdx.x - 1; u <= c.nu; u += blockDim.x) {
@@ -194,16 +351,42 @@ __global__ void k_rows_inv(const float2* __restrict__ T, OutT* __restrict__ stac
     const float2 zu = in ? z[u] : make_float2(0.f, 0.f);
     L[(size_t)(v0 + 1) * su + (u + 1)] = to_stack<OutT>(zu.x);
     if (two) L[(size_t)(v0 + 2) * su + (u + 1)] = to_stack<OutT>(zu.y);
-    if (v0 == 0) L[u + 1] = to_stack<OutT>(0.f);                                    // top border row
-    if (v0 + 2 >= c.nv) L[(size_t)(c.nv + 1) * su + (u + 1)] = to_stack<OutT>(0.f);  // bottom border row
+    if (v0 == 0) L[u + 1] = to_stack<OutT>(0.f);
+    if (v0 + 2 >= c.nv) L[(size_t)(c.nv + 1) * su + (u + 1)] = to_stack<OutT>(0.f);
   }
 }
 
-int threads_for(int P) {
-  int t = P >> 1;
-  if (t < 64) t = 64;
-  if (t > 512) t = 512;
-  return t;
+// ------------------------------------------------------------------ launch
+template <int P>
+cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin, int dir_count,
+                       cudaStream_t stream, cudaEvent_t* ev) {
+  constexpr int G = groups_per_cta<P>();
+  k_rows_fwd<P><<<dim3((c.nv + 2 * G - 1) / (2 * G), dir_count), kThreads, 0, stream>>>(images, ws.S, ws.tw, c,
+                                                                                         dir_begin);
+  if (ev) cudaEventRecord(ev[0], stream);
+  k_cols<P><<<dim3((c.half + G - 1) / G, dir_count), kThreads, 0, stream>>>(ws.S, ws.T, ws.tw, ws.uA, ws.ramp, c,
+                                                                             dir_begin);
+  if (ev) cudaEventRecord(ev[1], stream);
+  const dim3 gi((c.nv + 2 * G - 1) / (2 * G), c.nz_layers, dir_count);
+  if (c.stack_bf16)
+    k_rows_inv<P, __nv_bfloat16><<<gi, kThreads, 0, stream>>>(ws.T, (__nv_bfloat16*)ws.stack, ws.tw, c);
+  else
+    k_rows_inv<P, float><<<gi, kThreads, 0, stream>>>(ws.T, (float*)ws.stack, ws.tw, c);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin,
+                         int dir_count, cudaStream_t stream, cudaEvent_t* ev) {
+  k_small_rows_fwd<<<dim3((c.nv + 1) / 2, dir_count), 32, 0, stream>>>(images, ws.S, ws.tw, c, dir_begin);
+  if (ev) cudaEventRecord(ev[0], stream);
+  k_small_cols<<<dim3(c.half, dir_count), 32, 0, stream>>>(ws.S, ws.T, ws.tw, ws.uA, ws.ramp, c, dir_begin);
+  if (ev) cudaEventRecord(ev[1], stream);
+  const dim3 gi((c.nv + 1) / 2, c.nz_layers, dir_count);
+  if (c.stack_bf16)
+    k_small_rows_inv<__nv_bfloat16><<<gi, 32, 0, stream>>>(ws.T, (__nv_bfloat16*)ws.stack, ws.tw, c);
+  else
+    k_small_rows_inv<float><<<gi, 32, 0, stream>>>(ws.T, (float*)ws.stack, ws.tw, c);
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -211,32 +394,17 @@ int threads_for(int P) {
 cudaError_t launch_stage_a(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin,
                            int dir_count, cudaStream_t stream, cudaEvent_t* ev) {
   if (dir_count <= 0) return cudaSuccess;
-  const int thr = threads_for(c.P);
-  {
-    dim3 grid((c.nv + 1) / 2, dir_count);
-    size_t smem = (size_t)(c.P / 2 + c.P) * sizeof(float2);
-    k_rows_fwd<<<grid, thr, smem, stream>>>(images, ws.S, ws.tw, c, dir_begin);
-    if (ev) cudaEventRecord(ev[0], stream);
+  switch (c.P) {
+    case 16: return launch_reg<16>(c, ws, images, dir_begin, dir_count, stream, ev);
+    case 32: return launch_reg<32>(c, ws, images, dir_begin, dir_count, stream, ev);
+    case 64: return launch_reg<64>(c, ws, images, dir_begin, dir_count, stream, ev);
+    case 128: return launch_reg<128>(c, ws, images, dir_begin, dir_count, stream, ev);
+    case 256: return launch_reg<256>(c, ws, images, dir_begin, dir_count, stream, ev);
+    case 512: return launch_reg<512>(c, ws, images, dir_begin, dir_count, stream, ev);
+    case 1024: return launch_reg<1024>(c, ws, images, dir_begin, dir_count, stream, ev);
+    case 2048: return launch_reg<2048>(c, ws, images, dir_begin, dir_count, stream, ev);
+    default: return launch_small(c, ws, images, dir_begin, dir_count, stream, ev);
   }
-  {
-    dim3 grid((c.half + kColsPerCta - 1) / kColsPerCta, dir_count);
-    size_t smem = (size_t)(c.P / 2 + 2 * kColsPerCta * (c.P + 1)) * sizeof(float2);
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    k_cols<<<grid, 256, smem, stream>>>(ws.S, ws.T, ws.tw, ws.uA, ws.ramp, c, dir_begin);
-    if (ev) cudaEventRecord(ev[1], stream);
-  }
-  {
-    dim3 grid((c.nv + 1) / 2, c.nz_layers, dir_count);
-    size_t smem = (size_t)(c.P / 2 + c.P) * sizeof(float2);
-    if (c.stack_bf16)
-      k_rows_inv<__nv_bfloat16><<<grid, thr, smem, stream>>>(ws.T, (__nv_bfloat16*)ws.stack, ws.tw, c);
-    else
-      k_rows_inv<float><<<grid, thr, smem, stream>>>(ws.T, (float*)ws.stack, ws.tw, c);
-  }
-  return cudaGetLastError();
 }
 
 }  // namespace recon
