@@ -5,9 +5,12 @@
 // The passes use radix 8 while the remaining length allows, then one radix-2 or
 // radix-4 pass; between passes the values go through a padded shared-memory buffer
 // (index i stored at i + i/16, which keeps the 64-bit accesses of a half-warp on
-// distinct banks for these patterns).  Twiddles come from a shared table
-// tw[k] = exp(-2 pi i k / P), k < P.  INV selects the inverse (conjugate) transform,
-// unscaled.  Every thread of the CTA must call it (it uses __syncthreads).
+// distinct banks for these patterns).  Twiddles come from a per-pass table in shared
+// memory: the pass at sub-length Ns (radix R) stores exp(-2 pi i kb r / (Ns R)) at
+// offset (Ns - 8) + kb (R - 1) + (r - 1) for kb < Ns, 1 <= r < R, so the lanes of a
+// warp read addresses R - 1 apart (no bank conflicts); the table has P - 8 entries.
+// INV selects the inverse (conjugate) transform, unscaled.  Every thread of the CTA
+// must call it (it uses __syncthreads).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -28,6 +31,8 @@ __device__ __forceinline__ float2 mul_mi(float2 a) {
 
 __host__ __device__ constexpr int padded(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int buffer_len(int P) { return P + P / 16 + 1; }
+// entries of the per-pass twiddle table for length P (P >= 16)
+__host__ __device__ constexpr int pass_table_len(int P) { return P - 8; }
 
 template <bool INV>
 __device__ __forceinline__ void dft2(float2* v) {
@@ -97,10 +102,10 @@ __device__ __forceinline__ void pass(float2 (&x)[8], float2* buf, const float2* 
       for (int r = 0; r < R; ++r) v[q * R + r] = buf[padded(j + q * T + r * STRIDE)];
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
-      const int kb = (j + q * T) & (Ns - 1);
+      const float2* twk = tw + (Ns - 8) + ((j + q * T) & (Ns - 1)) * (R - 1) - 1;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        float2 w = tw[kb * r * (P / (Ns * R))];
+        float2 w = twk[r];
         if (INV) w.y = -w.y;
         v[q * R + r] = cmul(v[q * R + r], w);
       }

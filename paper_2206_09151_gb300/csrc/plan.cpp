@@ -49,10 +49,11 @@ struct recon_plan_s {
   std::vector<uint64_t> uA;
   std::vector<float> ramp;
   std::vector<float2> tw;
+  std::vector<float2> twp;
   recon::StageAConst ca;
   recon::BackprojConst cb;
   // workspace layout (byte offsets)
-  size_t off_dirs, off_uA, off_ramp, off_tw, off_S, off_T, off_stack, ws_bytes, table_bytes;
+  size_t off_dirs, off_uA, off_ramp, off_tw, off_twp, off_S, off_T, off_stack, ws_bytes, table_bytes;
   size_t stack_dir_bytes;
   // optional profiling: 4 events per block plus one at the start of the run
   bool profile = false;
@@ -229,6 +230,22 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
       p->tw[j].x = (float)std::cos(2.0 * M_PI * j / P);
       p->tw[j].y = (float)-std::sin(2.0 * M_PI * j / P);
     }
+    // per-pass twiddles of the register FFT: pass at sub-length Ns (radix R) holds
+    // exp(-2 pi i kb r / (Ns R)) at (Ns - 8) + kb (R - 1) + (r - 1)
+    p->twp.assign(P >= 16 ? P - 8 : 1, float2{0.f, 0.f});
+    if (P >= 16) {
+      for (int Ns = 1; Ns < P;) {
+        const int rem = P / Ns;
+        const int R = (rem % 8 == 0) ? 8 : rem;
+        if (Ns > 1)
+          for (int kb = 0; kb < Ns; ++kb)
+            for (int r = 1; r < R; ++r) {
+              const double ang = -2.0 * M_PI * (double)kb * r / ((double)Ns * R);
+              p->twp[(Ns - 8) + kb * (R - 1) + (r - 1)] = float2{(float)std::cos(ang), (float)std::sin(ang)};
+            }
+        Ns *= R;
+      }
+    }
   } catch (const std::bad_alloc&) {
     delete p;
     return fail(RECON_E_NO_MEMORY, "recon_plan: out of host memory");
@@ -298,6 +315,8 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
   off = align256(off + sizeof(float) * p->half);
   p->off_tw = off;
   off = align256(off + sizeof(float2) * P);
+  p->off_twp = off;
+  off = align256(off + sizeof(float2) * p->twp.size());
   p->table_bytes = off;
   p->off_S = off;
   off = align256(off + (size_t)db * p->nv * p->half * 8);
@@ -349,6 +368,7 @@ recon::Workspace carve(recon_plan_t p, void* ws) {
   w.uA = (uint64_t*)(b + p->off_uA);
   w.ramp = (float*)(b + p->off_ramp);
   w.tw = (float2*)(b + p->off_tw);
+  w.twp = (float2*)(b + p->off_twp);
   w.S = (float2*)(b + p->off_S);
   w.T = (float2*)(b + p->off_T);
   w.stack = (void*)(b + p->off_stack);
@@ -366,6 +386,8 @@ int upload_tables(recon_plan_t p, const recon::Workspace& w, cudaStream_t s) {
     e = cudaMemcpyAsync(w.ramp, p->ramp.data(), sizeof(float) * p->ramp.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(w.tw, p->tw.data(), sizeof(float2) * p->tw.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(w.twp, p->twp.data(), sizeof(float2) * p->twp.size(), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e, "upload of plan tables");
   return RECON_OK;
 }
@@ -534,6 +556,7 @@ int run_in_scratch(recon_plan_t p, const float* images, float* volume, char* scr
   w.uA = (uint64_t*)(scratch + p->off_uA);
   w.ramp = (float*)(scratch + p->off_ramp);
   w.tw = (float2*)(scratch + p->off_tw);
+  w.twp = (float2*)(scratch + p->off_twp);
   size_t off = p->table_bytes;
   w.S = (float2*)(scratch + off);
   off += align256(db * spec);

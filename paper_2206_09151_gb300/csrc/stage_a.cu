@@ -18,6 +18,7 @@
 
 #include "fft_reg.cuh"
 #include "recon_internal.h"
+#include "sinpi_poly.h"
 
 namespace recon {
 namespace {
@@ -46,6 +47,24 @@ __device__ __forceinline__ float sin_from_turns(uint64_t x) {
   return sinpif((float)hi * 4.656612873077393e-10f);  // hi * 2^-31 = chi / pi in [-1, 1)
 }
 
+// sin(pi t) for t = hi * 2^-31 in [-1, 1) (hi: the top 32 bits of chi / (2 pi) in
+// fixed point).  The fold sin(pi t) = sin(pi (+-1 - t)) is exact integer arithmetic and
+// brings t into [-1/2, 1/2]; then z = 2t in [-1, 1] goes through the odd polynomial
+// z * p(z^2) ~ sin(pi z / 2) of sinpi_poly.h (least-squares fit, max error 1.7e-7).
+__device__ __forceinline__ float sin_half_turns(int32_t hi) {
+  const bool fold = (uint32_t)hi + 0x40000000u > 0x80000000u;  // |t| > 1/2
+  const int32_t u = fold ? (int32_t)(0x80000000u - (uint32_t)hi) : hi;
+  const float z = (float)u * 9.313225746154785e-10f;  // u * 2^-30
+  const float z2 = z * z;
+  float p = RECON_SINPI_C5;
+  p = fmaf(p, z2, RECON_SINPI_C4);
+  p = fmaf(p, z2, RECON_SINPI_C3);
+  p = fmaf(p, z2, RECON_SINPI_C2);
+  p = fmaf(p, z2, RECON_SINPI_C1);
+  p = fmaf(p, z2, RECON_SINPI_C0);
+  return p * z;
+}
+
 template <typename OutT>
 __device__ __forceinline__ OutT to_stack(float x);
 template <>
@@ -58,12 +77,12 @@ template <int P>
 __global__ void __launch_bounds__(kThreads) k_rows_fwd(const float* __restrict__ images, float2* __restrict__ S,
                                                         const float2* __restrict__ twg, StageAConst c,
                                                         int dir_begin) {
-  constexpr int TT = P / 8, G = groups_per_cta<P>(), L = fft::buffer_len(P);
-  __shared__ float2 tw[P];
+  constexpr int TT = P / 8, G = groups_per_cta<P>(), L = fft::buffer_len(P), NT = fft::pass_table_len(P);
+  __shared__ float2 tw[NT];
   __shared__ float2 buf_all[G * L];
   const int g = threadIdx.x / TT, j = threadIdx.x % TT;
   float2* buf = buf_all + g * L;
-  for (int i = threadIdx.x; i < P; i += kThreads) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < NT; i += kThreads) tw[i] = twg[i];
   const int n = blockIdx.y;
   const int v0 = 2 * (blockIdx.x * G + g);
   const bool row1 = v0 < c.nv, row2 = v0 + 1 < c.nv;
@@ -95,15 +114,15 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(const float* __restrict__
 }
 
 template <int P>
-__global__ void __launch_bounds__(kThreads) k_cols(const float2* __restrict__ S, float2* __restrict__ T,
+__global__ void __launch_bounds__(kThreads, 4) k_cols(const float2* __restrict__ S, float2* __restrict__ T,
                                                     const float2* __restrict__ twg, const uint64_t* __restrict__ uA,
                                                     const float* __restrict__ ramp, StageAConst c, int dir_begin) {
-  constexpr int TT = P / 8, CB = groups_per_cta<P>(), L = fft::buffer_len(P);
-  __shared__ float2 tw[P];
+  constexpr int TT = P / 8, CB = groups_per_cta<P>(), L = fft::buffer_len(P), NT = fft::pass_table_len(P);
+  __shared__ float2 tw[NT];
   __shared__ float2 buf_all[CB * L];
   const int g = threadIdx.x / TT, j = threadIdx.x % TT;
   float2* buf = buf_all + g * L;
-  for (int i = threadIdx.x; i < P; i += kThreads) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < NT; i += kThreads) tw[i] = twg[i];
   const int n = blockIdx.y;
   const int c0 = blockIdx.x * CB;
   const int col = c0 + g;
@@ -125,26 +144,31 @@ __global__ void __launch_bounds__(kThreads) k_cols(const float2* __restrict__ S,
   const bool ok = col < c.half;
   const int colc = ok ? col : c.half - 1;
   const float w = ramp[colc];
-  uint32_t msq[8];
-  uint64_t base[8];
+  // chi/(2 pi) in 2^-32 turns needs only the top 32 bits of the 64-bit fixed-point
+  // sum: the per-layer product uA_k * m is formed as hi(uA) * m + umulhi(lo(uA), m), and
+  // the layer-independent part uC * m^2 - uW once per element (dropped low-word carries
+  // cost at most 2^-32 turns).
+  uint32_t msq[8], base_hi[8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int m = j + s * TT;
     const int mv = m < P / 2 ? m : m - P;
     msq[s] = (uint32_t)(colc * colc + mv * mv);
     const uint64_t m64 = msq[s];
-    base[s] = c.uC * (m64 * m64) - c.uW;
+    base_hi[s] = (uint32_t)((c.uC * (m64 * m64) - c.uW) >> 32);
   }
   const uint64_t* uAn = uA + (size_t)(dir_begin + n) * c.nz_layers;
   float2* Tn = T + (size_t)n * c.nz_layers * c.half * c.nv;
   for (int k = 0; k < c.nz_layers; ++k) {
     const uint64_t uAk = uAn[k];
+    const uint32_t a_hi = (uint32_t)(uAk >> 32), a_lo = (uint32_t)uAk;
     float2 x[8];
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       float f = w;
       if (c.filter) {
-        const float sn = sin_from_turns(uAk * (uint64_t)msq[s] + base[s]);
+        const uint32_t hi = a_hi * msq[s] + __umulhi(a_lo, msq[s]) + base_hi[s];
+        const float sn = sin_half_turns((int32_t)hi);
         f *= c.pref * __fdividef(sn, fmaf(sn, sn, c.eps));  // real part of the Eq. 11 bracket
       }
       x[s] = make_float2(xg[s].x * f, xg[s].y * f);
@@ -165,22 +189,33 @@ template <int P, typename OutT>
 __global__ void __launch_bounds__(kThreads) k_rows_inv(const float2* __restrict__ T, OutT* __restrict__ stack,
                                                         const float2* __restrict__ twg, StageAConst c) {
   constexpr int TT = P / 8, G = groups_per_cta<P>(), L = fft::buffer_len(P), H = P / 2 + 1;
-  constexpr int TILE = 2 * G * H, BUF = G * L;
-  __shared__ float2 tw[P];
+  constexpr int TILE = 2 * G * H, BUF = G * L, NT = fft::pass_table_len(P);
+  constexpr int FILL = (TILE + kThreads - 1) / kThreads;
+  __shared__ float2 tw[NT];
   // the half-spectrum tile is read once, before the FFT's first exchange: the
   // exchange buffer reuses its memory
   __shared__ float2 shared_mem[TILE > BUF ? TILE : BUF];
   float2* tile = shared_mem;
   const int g = threadIdx.x / TT, j = threadIdx.x % TT;
   float2* buf = shared_mem + g * L;
-  for (int i = threadIdx.x; i < P; i += kThreads) tw[i] = twg[i];
+  for (int i = threadIdx.x; i < NT; i += kThreads) tw[i] = twg[i];
   const int n = blockIdx.z, k = blockIdx.y;
   const int vbase = blockIdx.x * 2 * G;
   const float2* Tk = T + ((size_t)n * c.nz_layers + k) * H * c.nv;
-  for (int idx = threadIdx.x; idx < TILE; idx += kThreads) {
-    const int vv = idx % (2 * G), cc = idx / (2 * G);
-    const int v = vbase + vv;
-    tile[vv * H + cc] = v < c.nv ? Tk[(size_t)cc * c.nv + v] : make_float2(0.f, 0.f);
+  {  // all loads in flight before the shared stores
+    float2 tmp[FILL];
+#pragma unroll
+    for (int it = 0; it < FILL; ++it) {
+      const int idx = threadIdx.x + it * kThreads;
+      const int vv = idx % (2 * G), cc = idx / (2 * G);
+      const int v = vbase + vv;
+      tmp[it] = (idx < TILE && v < c.nv) ? Tk[(size_t)cc * c.nv + v] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int it = 0; it < FILL; ++it) {
+      const int idx = threadIdx.x + it * kThreads;
+      if (idx < TILE) tile[(idx % (2 * G)) * H + idx / (2 * G)] = tmp[it];
+    }
   }
   __syncthreads();
   const int v0 = vbase + 2 * g;
@@ -361,17 +396,17 @@ template <int P>
 cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin, int dir_count,
                        cudaStream_t stream, cudaEvent_t* ev) {
   constexpr int G = groups_per_cta<P>();
-  k_rows_fwd<P><<<dim3((c.nv + 2 * G - 1) / (2 * G), dir_count), kThreads, 0, stream>>>(images, ws.S, ws.tw, c,
+  k_rows_fwd<P><<<dim3((c.nv + 2 * G - 1) / (2 * G), dir_count), kThreads, 0, stream>>>(images, ws.S, ws.twp, c,
                                                                                          dir_begin);
   if (ev) cudaEventRecord(ev[0], stream);
-  k_cols<P><<<dim3((c.half + G - 1) / G, dir_count), kThreads, 0, stream>>>(ws.S, ws.T, ws.tw, ws.uA, ws.ramp, c,
+  k_cols<P><<<dim3((c.half + G - 1) / G, dir_count), kThreads, 0, stream>>>(ws.S, ws.T, ws.twp, ws.uA, ws.ramp, c,
                                                                              dir_begin);
   if (ev) cudaEventRecord(ev[1], stream);
   const dim3 gi((c.nv + 2 * G - 1) / (2 * G), c.nz_layers, dir_count);
   if (c.stack_bf16)
-    k_rows_inv<P, __nv_bfloat16><<<gi, kThreads, 0, stream>>>(ws.T, (__nv_bfloat16*)ws.stack, ws.tw, c);
+    k_rows_inv<P, __nv_bfloat16><<<gi, kThreads, 0, stream>>>(ws.T, (__nv_bfloat16*)ws.stack, ws.twp, c);
   else
-    k_rows_inv<P, float><<<gi, kThreads, 0, stream>>>(ws.T, (float*)ws.stack, ws.tw, c);
+    k_rows_inv<P, float><<<gi, kThreads, 0, stream>>>(ws.T, (float*)ws.stack, ws.twp, c);
   return cudaGetLastError();
 }
 
