@@ -128,8 +128,9 @@ int recon_run(recon_plan_t plan, const float* images, float* volume, void* works
 /* Stage A alone (Sec. 2, Eq. 4-11 per layer): the layer stacks of directions
  * [dir_begin, dir_begin + dir_count), dir_count <= the plan's block size, into the
  * workspace.  *stack_out receives a device pointer into the workspace, laid out
- * [dir_count][Nz][nv + 2][nu + 2] of float32 or bfloat16 (per stack_dtype) with a
- * one-pixel zero border: Y_{n,k}(u, v) sits at [n][k][v + 1][u + 1]. */
+ * [dir_count][Nz][nv + 2][nu + 1] of horizontal tap pairs (two float32, or two
+ * bfloat16, per stack_dtype): entry [n][k][v + 1][c] = (Y_{n,k}(c - 1, v), Y_{n,k}(c, v))
+ * for c in [0, nu], with Y = 0 outside the image; rows 0 and nv + 1 are zero. */
 int recon_filter_stage(recon_plan_t plan, const float* images, int dir_begin, int dir_count, void* workspace,
                        size_t ws_bytes, void* stream, const void** stack_out);
 

@@ -9,8 +9,10 @@
 // FP32 arithmetic inside the tile works on small numbers (error ~1e-6 pixel at any
 // detector size).  The depth coordinate is an exact 2^-24 fixed-point integer sum, so
 // the layer decision does not depend on the traversal order.  Out-of-detector taps
-// read the stack's one-pixel zero border: the integer tap is clamped to [-1, n-1] and
-// the weight saturated to [0, 1], which gives exactly bilinear-with-zero-outside.
+// read the stack's zero border (rows -1 and nv, pairs holding the columns -1 and nu):
+// the integer tap is clamped to [-1, n-1] and the weight saturated to [0, 1], which
+// gives exactly bilinear-with-zero-outside.  Each stack entry is the tap pair
+// (Y[u], Y[u+1]), so a bilinear row is one load.
 #include <cuda_bf16.h>
 
 #include "recon_internal.h"
@@ -30,8 +32,9 @@ struct TileDir {  // per (tile, direction), 64 bytes in shared memory
 };
 static_assert(sizeof(TileDir) == 64, "TileDir layout");
 
-__device__ __forceinline__ float stack_val(const float* p) { return __ldg(p); }
-__device__ __forceinline__ float stack_val(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+// A stack entry is the horizontal tap pair (Y[u], Y[u + 1]) (one 8-byte or 4-byte load).
+__device__ __forceinline__ float2 stack_pair(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 stack_pair(const __nv_bfloat162* p) { return __bfloat1622float2(__ldg(p)); }
 
 // Round-to-nearest integer of |x| < 2^22 through the FP32 adder: x + 1.5*2^23 holds
 // rint(x) in its low mantissa bits.
@@ -95,10 +98,9 @@ __global__ void __launch_bounds__(kTX* kTY) k_backproject(const DirParams* __res
       const float fa = __saturatef(ap - (ta - kMagic) + 0.5f);
       const float fb = __saturatef(bp - (tb - kMagic) + 0.5f);
       const ST* p = base + (size_t)layer * c.layer_elems + (ptrdiff_t)rb * c.su + ra;
-      const float v00 = stack_val(p), v01 = stack_val(p + 1);
-      const float v10 = stack_val(p + c.su), v11 = stack_val(p + c.su + 1);
-      const float top = fmaf(fa, v01 - v00, v00);
-      const float bot = fmaf(fa, v11 - v10, v10);
+      const float2 r0 = stack_pair(p), r1 = stack_pair(p + c.su);
+      const float top = fmaf(fa, r0.y - r0.x, r0.x);
+      const float bot = fmaf(fa, r1.y - r1.x, r1.x);
       acc[z] += fmaf(fb, bot - top, top);
       ap += td.af2;
       bp += td.bf2;
@@ -138,8 +140,8 @@ static_assert(sizeof(AxisDir) == 32, "AxisDir layout");
 
 template <typename ST>
 __device__ __forceinline__ float lerp_row(const ST* p, float fa) {
-  const float v0 = stack_val(p), v1 = stack_val(p + 1);
-  return fmaf(fa, v1 - v0, v0);
+  const float2 v = stack_pair(p);
+  return fmaf(fa, v.y - v.x, v.x);
 }
 
 template <typename ST, bool TWO_ROWS>
@@ -249,29 +251,29 @@ cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, co
   if (c.axis_y) {
     const bool two = c.b_frac != 0.f;
     if (c.stack_bf16)
-      return two ? launch_axis<__nv_bfloat16, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream)
-                 : launch_axis<__nv_bfloat16, false>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream);
-    return two ? launch_axis<float, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream)
-               : launch_axis<float, false>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream);
+      return two ? launch_axis<__nv_bfloat162, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream)
+                 : launch_axis<__nv_bfloat162, false>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream);
+    return two ? launch_axis<float2, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream)
+               : launch_axis<float2, false>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream);
   }
   dim3 grid((c.nx + kTX - 1) / kTX, (c.ny + kTY - 1) / kTY, (c.nz + kTZ - 1) / kTZ);
   const size_t smem = (size_t)dir_count * sizeof(TileDir);
   if (c.stack_bf16) {
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k_backproject<__nv_bfloat16>,
+      cudaError_t e = cudaFuncSetAttribute(k_backproject<__nv_bfloat162>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
-    k_backproject<__nv_bfloat16><<<grid, kTX * kTY, smem, stream>>>(
-        dirs, (const __nv_bfloat16*)stack, c, dir_begin, dir_count, volume, accumulate);
+    k_backproject<__nv_bfloat162><<<grid, kTX * kTY, smem, stream>>>(
+        dirs, (const __nv_bfloat162*)stack, c, dir_begin, dir_count, volume, accumulate);
   } else {
     if (smem > 48 * 1024) {
       cudaError_t e =
-          cudaFuncSetAttribute(k_backproject<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+          cudaFuncSetAttribute(k_backproject<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
     }
-    k_backproject<float><<<grid, kTX * kTY, smem, stream>>>(dirs, (const float*)stack, c, dir_begin, dir_count,
-                                                             volume, accumulate);
+    k_backproject<float2><<<grid, kTX * kTY, smem, stream>>>(dirs, (const float2*)stack, c, dir_begin, dir_count,
+                                                              volume, accumulate);
   }
   return cudaGetLastError();
 }

@@ -266,8 +266,8 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
   ca.eps = (float)o.eps;
   ca.pref = (float)(lambda / (4.0 * M_PI * std::sqrt(1.0 + o.sigma * o.sigma)));
   ca.half = p->half;
-  ca.su = p->nu + 2;
-  ca.layer_elems = (size_t)(p->nv + 2) * (p->nu + 2);
+  ca.su = p->nu + 1;
+  ca.layer_elems = (size_t)(p->nv + 2) * (p->nu + 1);
 
   recon::BackprojConst& cb = p->cb;
   cb.nx = p->nx;
@@ -291,14 +291,21 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
     cb.b_frac = (float)(boff - fl);
   }
 
-  const size_t elem = ca.stack_bf16 ? 2 : 4;
+  const size_t elem = ca.stack_bf16 ? 4 : 8;  // one tap pair
   p->stack_dir_bytes = (size_t)nz_layers * ca.layer_elems * elem;
   const size_t per_dir = (size_t)p->nv * p->half * 8 * (1 + (size_t)nz_layers) + p->stack_dir_bytes;
   int db = o.dir_block;
   if (db == 0) {
-    const size_t budget = (size_t)1 << 30;
+    // as many directions per block as a 4 GiB stage budget holds (fewer volume
+    // read-modify-writes), then balanced so that the blocks are of equal size
+    const size_t budget = (size_t)4 << 30;
     db = (int)(budget / per_dir);
     if (db < 1) db = 1;
+    if (db > 1024) db = 1024;
+    if (D > 0) {
+      const int nb = (D + db - 1) / db;
+      db = (D + nb - 1) / nb;
+    }
   }
   if (db > 1024) db = 1024;
   if (D > 0 && db > D) db = D;

@@ -34,8 +34,8 @@ struct StageAConst {
   float eps;            // Tikhonov eps
   float pref;           // lambda / (4 pi sqrt(1 + sigma^2))
   int half;             // P/2 + 1 (columns of the half spectrum)
-  int su;               // stack row pitch, nu + 2
-  size_t layer_elems;   // (nv + 2) * (nu + 2)
+  int su;               // stack row pitch in tap pairs, nu + 1
+  size_t layer_elems;   // pairs per layer, (nv + 2) * (nu + 1)
 };
 
 // Device pointers into the workspace.
@@ -47,7 +47,7 @@ struct Workspace {
   float2* twp;          // [P - 8]: per-pass twiddles of the register FFT (fft_reg.cuh), P >= 16
   float2* S;            // [DB][nv][P/2+1]: row transforms
   float2* T;            // [DB][Nz][P/2+1][nv]: per-layer column inverse transforms (column-major)
-  void* stack;          // [DB][Nz][nv+2][nu+2]
+  void* stack;          // [DB][Nz][nv+2][nu+1] tap pairs (Y[v][u-1], Y[v][u]), zero outside
 };
 
 // Kernel launchers (stage_a.cu, backproject.cu).  They return cudaGetLastError().

@@ -9,7 +9,7 @@
 //               k: multiply by H_k(q) W(q_u), inverse FFT along v, store v < nv
 //                                                                   -> T[n][k][col][v]
 //   k_rows_inv  two rows of one layer per group: Hermitian-extend both half spectra,
-//               pack as real + i real, inverse FFT, crop u < nu     -> stack (zero border)
+//               pack as real + i real, inverse FFT, crop u < nu    -> stack of tap pairs
 // For P >= 16 the FFTs are register-resident mixed-radix Stockham transforms
 // (fft_reg.cuh); tiny images (P <= 8) use a shared-memory radix-2 transform.
 // The image sits at offset 0 of the P x P frame; by the shift invariance of the
@@ -65,12 +65,17 @@ __device__ __forceinline__ float sin_half_turns(int32_t hi) {
   return p * z;
 }
 
-template <typename OutT>
-__device__ __forceinline__ OutT to_stack(float x);
+// The stack stores horizontal tap pairs: entry (row v + 1, column c) of a layer holds
+// (Y[v][c - 1], Y[v][c]) for c in [0, nu], zero outside the image, so a bilinear row is
+// one 8-byte (float32) or 4-byte (bfloat16) load.
+template <typename PairT>
+__device__ __forceinline__ PairT make_pair(float a, float b);
 template <>
-__device__ __forceinline__ float to_stack<float>(float x) { return x; }
+__device__ __forceinline__ float2 make_pair<float2>(float a, float b) { return make_float2(a, b); }
 template <>
-__device__ __forceinline__ __nv_bfloat16 to_stack<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+__device__ __forceinline__ __nv_bfloat162 make_pair<__nv_bfloat162>(float a, float b) {
+  return __floats2bfloat162_rn(a, b);
+}
 
 // ------------------------------------------------------------------ register FFT kernels
 template <int P>
@@ -185,8 +190,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_cols(const float2* __restrict__
   }
 }
 
-template <int P, typename OutT>
-__global__ void __launch_bounds__(kThreads) k_rows_inv(const float2* __restrict__ T, OutT* __restrict__ stack,
+template <int P, typename PairT>
+__global__ void __launch_bounds__(kThreads) k_rows_inv(const float2* __restrict__ T, PairT* __restrict__ stack,
                                                         const float2* __restrict__ twg, StageAConst c) {
   constexpr int TT = P / 8, G = groups_per_cta<P>(), L = fft::buffer_len(P), H = P / 2 + 1;
   constexpr int TILE = 2 * G * H, BUF = G * L, NT = fft::pass_table_len(P);
@@ -242,33 +247,33 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(const float2* __restrict_
     x[s] = make_float2(a.x - b.y, a.y + b.x);  // a + i b
   }
   fft::block_fft<P, true>(x, buf, tw, j);
-  OutT* Lk = stack + ((size_t)n * c.nz_layers + k) * c.layer_elems;
-  const int su = c.su;
+  // rows v0 (real part) and v0 + 1 (imaginary part) at u = j + s*TT; pair them with
+  // their right-hand neighbours through the (now free) exchange buffer
+  __syncthreads();
+#pragma unroll
+  for (int s = 0; s < 8; ++s) buf[padded(j + s * TT)] = x[s];
+  __syncthreads();
+  PairT* Lk = stack + ((size_t)n * c.nz_layers + k) * c.layer_elems;
+  const int sp = c.su;
   if (v0 < c.nv) {
     const bool two = v0 + 1 < c.nv;
-    OutT* r1 = Lk + (size_t)(v0 + 1) * su + 1;
-    OutT* r2 = r1 + su;
+    PairT* r1 = Lk + (size_t)(v0 + 1) * sp;
+    PairT* r2 = r1 + sp;
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-      const int u = j + s * TT;
-      if (u < c.nu) {
-        r1[u] = to_stack<OutT>(x[s].x);
-        if (two) r2[u] = to_stack<OutT>(x[s].y);
-      }
-    }
-    if (j == 0) {  // left and right border columns
-      r1[-1] = to_stack<OutT>(0.f);
-      r1[c.nu] = to_stack<OutT>(0.f);
-      if (two) {
-        r2[-1] = to_stack<OutT>(0.f);
-        r2[c.nu] = to_stack<OutT>(0.f);
+      const int cc = j + s * TT;  // pair column: (Y[cc - 1], Y[cc])
+      if (cc <= c.nu) {
+        const float2 left = cc >= 1 ? buf[padded(cc - 1)] : make_float2(0.f, 0.f);
+        const float2 right = cc < c.nu ? buf[padded(cc)] : make_float2(0.f, 0.f);
+        r1[cc] = make_pair<PairT>(left.x, right.x);
+        if (two) r2[cc] = make_pair<PairT>(left.y, right.y);
       }
     }
   }
   if (blockIdx.x == 0)  // top border row
-    for (int i = threadIdx.x; i < su; i += kThreads) Lk[i] = to_stack<OutT>(0.f);
+    for (int i = threadIdx.x; i < sp; i += kThreads) Lk[i] = make_pair<PairT>(0.f, 0.f);
   if (vbase + 2 * G >= c.nv)  // bottom border row
-    for (int i = threadIdx.x; i < su; i += kThreads) Lk[(size_t)(c.nv + 1) * su + i] = to_stack<OutT>(0.f);
+    for (int i = threadIdx.x; i < sp; i += kThreads) Lk[(size_t)(c.nv + 1) * sp + i] = make_pair<PairT>(0.f, 0.f);
 }
 
 // ------------------------------------------------------------------ radix-2 fallback (P <= 8)
@@ -354,8 +359,8 @@ __global__ void k_small_cols(const float2* __restrict__ S, float2* __restrict__ 
   }
 }
 
-template <typename OutT>
-__global__ void k_small_rows_inv(const float2* __restrict__ T, OutT* __restrict__ stack,
+template <typename PairT>
+__global__ void k_small_rows_inv(const float2* __restrict__ T, PairT* __restrict__ stack,
                                  const float2* __restrict__ twg, StageAConst c) {
   __shared__ float2 tw[8];
   __shared__ float2 z[8];
@@ -379,15 +384,15 @@ __global__ void k_small_rows_inv(const float2* __restrict__ T, OutT* __restrict_
     z[bitrev(m, c.logP)] = make_float2(a.x - b.y, a.y + b.x);
   }
   fft_radix2<true>(z, c.P, c.logP, tw);
-  OutT* L = stack + ((size_t)n * c.nz_layers + k) * c.layer_elems;
-  const int su = c.su;
-  for (int u = (int)threadIdx.x - 1; u <= c.nu; u += blockDim.x) {
-    const bool in = u >= 0 && u < c.nu;
-    const float2 zu = in ? z[u] : make_float2(0.f, 0.f);
-    L[(size_t)(v0 + 1) * su + (u + 1)] = to_stack<OutT>(zu.x);
-    if (two) L[(size_t)(v0 + 2) * su + (u + 1)] = to_stack<OutT>(zu.y);
-    if (v0 == 0) L[u + 1] = to_stack<OutT>(0.f);
-    if (v0 + 2 >= c.nv) L[(size_t)(c.nv + 1) * su + (u + 1)] = to_stack<OutT>(0.f);
+  PairT* L = stack + ((size_t)n * c.nz_layers + k) * c.layer_elems;
+  const int sp = c.su;
+  for (int cc = threadIdx.x; cc <= c.nu; cc += blockDim.x) {
+    const float2 left = cc >= 1 ? z[cc - 1] : make_float2(0.f, 0.f);
+    const float2 right = cc < c.nu ? z[cc] : make_float2(0.f, 0.f);
+    L[(size_t)(v0 + 1) * sp + cc] = make_pair<PairT>(left.x, right.x);
+    if (two) L[(size_t)(v0 + 2) * sp + cc] = make_pair<PairT>(left.y, right.y);
+    if (v0 == 0) L[cc] = make_pair<PairT>(0.f, 0.f);
+    if (v0 + 2 >= c.nv) L[(size_t)(c.nv + 1) * sp + cc] = make_pair<PairT>(0.f, 0.f);
   }
 }
 
@@ -404,9 +409,9 @@ cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* i
   if (ev) cudaEventRecord(ev[1], stream);
   const dim3 gi((c.nv + 2 * G - 1) / (2 * G), c.nz_layers, dir_count);
   if (c.stack_bf16)
-    k_rows_inv<P, __nv_bfloat16><<<gi, kThreads, 0, stream>>>(ws.T, (__nv_bfloat16*)ws.stack, ws.twp, c);
+    k_rows_inv<P, __nv_bfloat162><<<gi, kThreads, 0, stream>>>(ws.T, (__nv_bfloat162*)ws.stack, ws.twp, c);
   else
-    k_rows_inv<P, float><<<gi, kThreads, 0, stream>>>(ws.T, (float*)ws.stack, ws.twp, c);
+    k_rows_inv<P, float2><<<gi, kThreads, 0, stream>>>(ws.T, (float2*)ws.stack, ws.twp, c);
   return cudaGetLastError();
 }
 
@@ -418,9 +423,9 @@ cudaError_t launch_small(const StageAConst& c, const Workspace& ws, const float*
   if (ev) cudaEventRecord(ev[1], stream);
   const dim3 gi((c.nv + 1) / 2, c.nz_layers, dir_count);
   if (c.stack_bf16)
-    k_small_rows_inv<__nv_bfloat16><<<gi, 32, 0, stream>>>(ws.T, (__nv_bfloat16*)ws.stack, ws.tw, c);
+    k_small_rows_inv<__nv_bfloat162><<<gi, 32, 0, stream>>>(ws.T, (__nv_bfloat162*)ws.stack, ws.tw, c);
   else
-    k_small_rows_inv<float><<<gi, 32, 0, stream>>>(ws.T, (float*)ws.stack, ws.tw, c);
+    k_small_rows_inv<float2><<<gi, 32, 0, stream>>>(ws.T, (float2*)ws.stack, ws.tw, c);
   return cudaGetLastError();
 }
 

@@ -70,20 +70,21 @@ class Reconstructor:
         return volume
 
     def filter_stage(self, images: torch.Tensor, dir_begin: int, dir_count: int, stream=None) -> torch.Tensor:
-        """``recon_filter_stage``: a view of the workspace holding the layer stacks,
-        shape (dir_count, Nz, nv + 2, nu + 2), zero border included."""
+        """``recon_filter_stage``: a view of the workspace holding the layer stacks as
+        horizontal tap pairs, shape (dir_count, Nz, nv + 2, nu + 1, 2): entry
+        [n, k, v + 1, c] = (Y[v][c - 1], Y[v][c]), zero outside the image."""
         self._check_images(images)
         ptr = _abi.recon_filter_stage(self.plan, images.data_ptr(), dir_begin, dir_count,
                                       self.workspace.data_ptr(), self.ws_bytes, self._stream(stream))
         off = ptr - self.workspace.data_ptr()
         esz = 2 if self.stack_dtype == torch.bfloat16 else 4
-        n = dir_count * self.nz_layers * (self.nv + 2) * (self.nu + 2)
+        n = dir_count * self.nz_layers * (self.nv + 2) * (self.nu + 1) * 2
         return self.workspace[off:off + n * esz].view(self.stack_dtype).view(
-            dir_count, self.nz_layers, self.nv + 2, self.nu + 2)
+            dir_count, self.nz_layers, self.nv + 2, self.nu + 1, 2)
 
     def backproject(self, stack: torch.Tensor, dir_begin: int, dir_count: int, volume: torch.Tensor,
                     accumulate: bool, stream=None) -> torch.Tensor:
-        """``recon_backproject``: layered backprojection of ``stack`` (layout of
+        """``recon_backproject``: layered backprojection of ``stack`` (tap-pair layout of
         :meth:`filter_stage`) into ``volume``."""
         if stack.dtype != self.stack_dtype or not stack.is_contiguous():
             raise ValueError("stack dtype/layout does not match the plan")

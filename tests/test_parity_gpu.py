@@ -71,12 +71,13 @@ def test_stage_a_layer_stack_matches_oracle(case):
         ref = O.layer_stack(img[n], delta=delta, lam=lam, r_n=defocus[n], z_layers=zc[n], n_dir=D, sigma=sigma,
                             eps=eps, cs=cs, filt=O.FILTER_TIKHONOV if filt == "tikhonov" else O.FILTER_OFF,
                             input_mode=O.INPUT_INTENSITY if inp == "intensity" else O.INPUT_CONTRAST)
-        got = st[n, :, 1:-1, 1:-1]
+        got = st[n, :, 1:-1, 1:, 0]  # pair (Y[u], Y[u+1]) at column u + 1
         for k in range(nzl):
             assert rel_l2(got[k], ref[k]) <= TOL_F32, (n, k, rel_l2(got[k], ref[k]))
-        # the one-pixel border is exactly zero
-        assert not st[n, :, 0, :].any() and not st[n, :, -1, :].any()
-        assert not st[n, :, :, 0].any() and not st[n, :, :, -1].any()
+        # pairs are consistent, and the border (rows 0 and nv+1, columns -1 and nu) is zero
+        assert np.array_equal(st[n, :, :, :-1, 1], st[n, :, :, 1:, 0])
+        assert not st[n, :, 0].any() and not st[n, :, -1].any()
+        assert not st[n, :, :, 0, 0].any() and not st[n, :, :, -1, 1].any()
     r.close()
 
 
@@ -88,8 +89,9 @@ def _stage_b_case(grid, nu, nv, nzl, D, seed, start=0.1, span=math.pi, axis=None
     stacks = rng.standard_normal((D, nzl, nv, nu)).astype(np.float32)
     padded = np.zeros((D, nzl, nv + 2, nu + 2), np.float32)
     padded[:, :, 1:-1, 1:-1] = stacks
+    pairs = np.stack([padded[..., :-1], padded[..., 1:]], axis=-1).copy()  # (Y[c-1], Y[c])
     vol = torch.full((grid[2], grid[1], grid[0]), 7.0, device="cuda")
-    r.backproject(torch.from_numpy(padded).cuda(), 0, D, vol, accumulate=False)
+    r.backproject(torch.from_numpy(pairs).cuda(), 0, D, vol, accumulate=False)
     got = vol.cpu().numpy()
     A, B = O.pixel_coefficients(rot, grid, nu, nv)
     T = O.layer_constants(rot, grid, nzl)
