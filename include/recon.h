@@ -65,7 +65,9 @@ extern "C" {
 #define RECON_STACK_F32 0        /* layer stack stored in float32                       */
 #define RECON_STACK_BF16 1       /* layer stack stored in bfloat16 (FP32 FFT/accumulate) */
 
-#define RECON_RAMP_SINGLE_AXIS 0 /* ramp along u; every rot[n] must keep v = volume y   */
+#define RECON_RAMP_SINGLE_AXIS 0 /* ramp along u; every rot[n] must share one row 1 (axis) */
+#define RECON_RAMP_DENSITY 1     /* any geometry: W = g / (S(q) + eps_S), S the gridded
+                                    sampling density of all views' slices (Sec. 2)        */
 
 /* Limits (RECON_E_UNSUPPORTED_SIZE beyond them). */
 #define RECON_MAX_IMAGE 1024     /* nu, nv <= 1024, so P <= 2048                        */
@@ -92,7 +94,7 @@ typedef struct {
   int filter;      /* RECON_FILTER_*                                                    */
   int input_mode;  /* RECON_INPUT_*                                                     */
   int stack_dtype; /* RECON_STACK_*                                                     */
-  int ramp_mode;   /* RECON_RAMP_*                                                      */
+  int ramp_mode;   /* RECON_RAMP_* (single-axis ramp, or sampling-density weighting)       */
   int accumulate;  /* 0: run overwrites vol; 1: run adds into vol                       */
   int dir_block;   /* directions per block (stack held in workspace), 0 = automatic    */
 } recon_options;

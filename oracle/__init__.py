@@ -6,6 +6,6 @@ no code.  See ``recon_fp64`` for what it computes and the passage each step foll
 """
 from .recon_fp64 import (  # noqa: F401
     FILTER_OFF, FILTER_TIKHONOV, INPUT_CONTRAST, INPUT_INTENSITY, INTENSITY_FLOOR, LAYER_FRAC_BITS,
-    backproject_direction, bilinear, contrast, ctf_filter, depth_extent, layer_centres, layer_constants,
+    backproject_direction, bilinear, contrast, ctf_filter, density_geometry, density_grid, density_weights, depth_extent, layer_centres, layer_constants,
     layer_index, layer_stack, padded_size, pixel_coefficients, ramp_weights, recon, signed_freq,
 )

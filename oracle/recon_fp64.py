@@ -151,6 +151,100 @@ def ctf_filter(P: int, delta: float, lam: float, r_eff: float, sigma: float, eps
     return lam / (4.0 * math.pi * math.sqrt(1.0 + sigma * sigma)) * s / (s * s + eps)
 
 
+# ----------------------------------------------------------------------------- density
+DENSITY_EPS_REL = 1e-3
+
+
+def density_geometry(P: int) -> tuple[int, int]:
+    """Sampling step s (in DFT bins) and half-width Gh of the 3D density grid: the grid
+    has (2 Gh + 1)^3 cells of s bins, covering every slice point of norm <= sqrt(2) P/2."""
+    s = max(1, P // 128)
+    Gh = int(math.ceil(math.sqrt(2.0) * (P / 2) / s)) + 2
+    return s, Gh
+
+
+def density_grid(rot: np.ndarray, P: int) -> np.ndarray:
+    """S: the sampling matrix of Sec. 2.  Every image's 2D DFT samples (m_u, m_v), taken
+    every s bins with weight s^2, sit at m_u u_n + m_v v_n in 3D frequency space (u_n, v_n:
+    the detector axes, rows 0 and 1 of Rot_n) and are spread over the 8 surrounding cells
+    of the grid with trilinear weights summing to one; each sample is entered at q and at
+    -q with half weight, so that S (and the weight) are even in q."""
+    s, Gh = density_geometry(P)
+    G = 2 * Gh + 1
+    S = np.zeros(G * G * G)
+    m = np.arange(-P // 2, P // 2, s, dtype=np.float64)
+    mu, mv = np.meshgrid(m, m, indexing="ij")
+    mu, mv = mu.ravel(), mv.ravel()
+    for n in range(rot.shape[0]):
+        q0 = (mu[:, None] * rot[n, 0][None, :] + mv[:, None] * rot[n, 1][None, :]) / s  # grid units
+        for q in (q0, -q0):  # the sample and its mirror, half weight each (S even in q)
+            base = np.floor(q).astype(np.int64)
+            f = q - base
+            idx = base + Gh
+            for dz in (0, 1):
+                for dy in (0, 1):
+                    for dx in (0, 1):
+                        w = ((f[:, 0] if dx else 1 - f[:, 0]) * (f[:, 1] if dy else 1 - f[:, 1])
+                             * (f[:, 2] if dz else 1 - f[:, 2]))
+                        cell = ((idx[:, 2] + dz) * G + (idx[:, 1] + dy)) * G + (idx[:, 0] + dx)
+                        np.add.at(S, cell, w * 0.5 * s * s)
+    return S.reshape(G, G, G)  # [z][y][x]
+
+
+def density_ball_count(Gh: int) -> tuple[np.ndarray, int]:
+    """Cells within Gh - 2 of the grid centre (the band): mask and count."""
+    G = 2 * Gh + 1
+    c = np.arange(G) - Gh
+    zz, yy, xx = np.meshgrid(c, c, c, indexing="ij")
+    mask = (xx * xx + yy * yy + zz * zz) <= (Gh - 2) ** 2
+    return mask, int(mask.sum())
+
+
+def density_weights(rot: np.ndarray, P: int, delta: float) -> np.ndarray:
+    """W_n(q) = g / (S(m_u u_n + m_v v_n) + eps_S) on each direction's P x P DFT grid
+    (Sec. 2: the regularised inverse S_eps^-1 of the sampling matrix replaces the 1/n_q of
+    Eq. 11).  S is interpolated trilinearly; g = s^3 / (P delta) turns sample counts into
+    the density of slices per unit frequency, so that a 180-degree single-axis scan gives
+    pi |q_u| / D; eps_S = 1e-3 times the mean of S over the band.  On the Nyquist row and
+    column (bin -P/2, which is also +P/2) the weight is the mean over both aliases, so
+    that it is even on the DFT grid."""
+    s, Gh = density_geometry(P)
+    G = 2 * Gh + 1
+    S = density_grid(rot, P)
+    mask, count = density_ball_count(Gh)
+    eps_s = DENSITY_EPS_REL * S[mask].sum() / count
+    g = s ** 3 / (P * delta)
+    m = signed_freq(P).astype(np.float64)
+    mv, mu = np.meshgrid(m, m, indexing="ij")  # [v][u]
+    out = np.empty((rot.shape[0], P, P))
+    Sf = S.ravel()
+
+    def weight(n, a, b):
+        q = (a[..., None] * rot[n, 0] + b[..., None] * rot[n, 1]) / s
+        base = np.floor(q).astype(np.int64)
+        f = q - base
+        idx = base + Gh
+        val = np.zeros(a.shape)
+        for dz in (0, 1):
+            for dy in (0, 1):
+                for dx in (0, 1):
+                    w = ((f[..., 0] if dx else 1 - f[..., 0]) * (f[..., 1] if dy else 1 - f[..., 1])
+                         * (f[..., 2] if dz else 1 - f[..., 2]))
+                    cell = ((idx[..., 2] + dz) * G + (idx[..., 1] + dy)) * G + (idx[..., 0] + dx)
+                    val += w * Sf[cell]
+        return g / (val + eps_s)
+
+    # the Nyquist bin -P/2 is also +P/2: there the weight is the mean over both aliases,
+    # which keeps it even on the DFT grid (a real inverse transform)
+    nyq_u = mu == -(P // 2)
+    nyq_v = (mv == -(P // 2)) & ~nyq_u
+    for n in range(rot.shape[0]):
+        w0 = weight(n, mu, mv)
+        w1 = weight(n, np.where(nyq_u, -mu, mu), np.where(nyq_v, -mv, mv))
+        out[n] = np.where(nyq_u | nyq_v, 0.5 * (w0 + w1), w0)
+    return out
+
+
 # ----------------------------------------------------------------------------- stage A
 def contrast(image: np.ndarray, input_mode: int) -> np.ndarray:
     """g = ln(I/I_in) (left side of Eq. 4), intensities floored at 1e-6, or the image
@@ -162,17 +256,19 @@ def contrast(image: np.ndarray, input_mode: int) -> np.ndarray:
 
 
 def layer_stack(image: np.ndarray, *, delta: float, lam: float, r_n: float, z_layers: np.ndarray,
-                n_dir: int, sigma: float, eps: float, cs: float, filt: int, input_mode: int) -> np.ndarray:
+                n_dir: int, sigma: float, eps: float, cs: float, filt: int, input_mode: int,
+                weight: np.ndarray | None = None) -> np.ndarray:
     """Layer stack Y_k (k over ``z_layers``) of one image, float64 ``(Nz, nv, nu)``:
     crop(Re IDFT[G * H_k * W]) with G the DFT of the zero-padded contrast, image
-    centred in the P x P frame."""
+    centred in the P x P frame; W is the single-axis ramp, or ``weight`` (P x P, the
+    density weighting of an arbitrary scan)."""
     nv, nu = image.shape
     P = padded_size(max(nu, nv))
     ou, ov = (P - nu) // 2, (P - nv) // 2
     g = np.zeros((P, P))
     g[ov:ov + nv, ou:ou + nu] = contrast(image, input_mode)
     G = np.fft.fft2(g)
-    W = ramp_weights(P, delta, n_dir)[None, :]
+    W = ramp_weights(P, delta, n_dir)[None, :] if weight is None else weight
     out = np.empty((len(z_layers), nv, nu))
     for k, z in enumerate(z_layers):
         F = W * ctf_filter(P, delta, lam, r_n - z, sigma, eps, cs) if filt == FILTER_TIKHONOV else W
@@ -216,8 +312,9 @@ def backproject_direction(stack: np.ndarray, A: np.ndarray, B: np.ndarray, T: np
 def _partial_recon(args):
     """Sum over directions ``dirs`` of their contributions to voxels (i, j, k)."""
     (images, rot, dirs, lam, delta, defocus, nz_layers, grid, sigma, eps, cs, filt, input_mode, i, j, k,
-     n_dir) = args
+     n_dir, density) = args
     nu, nv = images.shape[2], images.shape[1]
+    dens = density_weights(rot, padded_size(max(nu, nv)), delta) if density else None
     A, B = pixel_coefficients(rot, grid, nu, nv)
     T = layer_constants(rot, grid, nz_layers)
     zc = layer_centres(rot, grid, nz_layers, delta)
@@ -225,7 +322,8 @@ def _partial_recon(args):
     chunk = 1 << 21
     for n in dirs:
         st = layer_stack(images[n], delta=delta, lam=lam, r_n=float(defocus[n]), z_layers=zc[n], n_dir=n_dir,
-                         sigma=sigma, eps=eps, cs=cs, filt=filt, input_mode=input_mode)
+                         sigma=sigma, eps=eps, cs=cs, filt=filt, input_mode=input_mode,
+                         weight=None if dens is None else dens[n])
         for s0 in range(0, i.size, chunk):
             sl = slice(s0, s0 + chunk)
             acc[sl] += backproject_direction(st, A[n], B[n], T[n], i[sl], j[sl], k[sl])
@@ -234,13 +332,14 @@ def _partial_recon(args):
 
 def recon(images, rot, *, lam: float, delta: float, defocus, nz_layers: int, grid, sigma: float = 0.0,
           eps: float = 0.1, cs: float = 0.0, filt: int = FILTER_TIKHONOV, input_mode: int = INPUT_INTENSITY,
-          voxels=None, dirs=None, workers: int = 1) -> np.ndarray:
+          voxels=None, dirs=None, workers: int = 1, density: bool = False) -> np.ndarray:
     """The whole operator, FP64.  ``images`` (D, nv, nu); ``rot`` (D, 3, 3);
     ``defocus`` (D,).  Returns vol[z][y][x] float64, or, when ``voxels = (i, j, k)``
     index arrays are given, the values at those voxels only.  ``dirs`` restricts the
     sum to a subset of the directions (the ramp keeps its pi/D for all D);
     ``workers`` > 1 splits the directions over a spawned process pool (the same
-    arithmetic, summed in a different order)."""
+    arithmetic, summed in a different order).  ``density`` selects the sampling-density
+    weighting of an arbitrary scan instead of the single-axis ramp."""
     images = np.asarray(images)
     rot = np.asarray(rot, dtype=np.float64)
     D = images.shape[0]
@@ -252,7 +351,7 @@ def recon(images, rot, *, lam: float, delta: float, defocus, nz_layers: int, gri
         i, j, k = (np.asarray(x, np.int64) for x in voxels)
     dirs = list(range(D)) if dirs is None else list(dirs)
     common = (lam, delta, np.asarray(defocus, np.float64), nz_layers, tuple(grid), sigma, eps, cs, filt,
-              input_mode, i, j, k, D)
+              input_mode, i, j, k, D, density)
     if workers <= 1 or len(dirs) < 2:
         acc = _partial_recon((images, rot, dirs) + common)
     else:

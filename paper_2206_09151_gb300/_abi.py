@@ -27,6 +27,7 @@ RECON_INPUT_CONTRAST = 1
 RECON_STACK_F32 = 0
 RECON_STACK_BF16 = 1
 RECON_RAMP_SINGLE_AXIS = 0
+RECON_RAMP_DENSITY = 1
 RECON_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 

@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "density.cuh"
 #include "recon_internal.h"
 
 namespace {
@@ -53,7 +54,8 @@ struct recon_plan_s {
   recon::StageAConst ca;
   recon::BackprojConst cb;
   // workspace layout (byte offsets)
-  size_t off_dirs, off_uA, off_ramp, off_tw, off_twp, off_S, off_T, off_stack, ws_bytes, table_bytes;
+  size_t off_dirs, off_uA, off_ramp, off_tw, off_twp, off_dens, off_dsum, off_S, off_T, off_stack, ws_bytes,
+      table_bytes;
   size_t stack_dir_bytes;
   // optional profiling: 4 events per block plus one at the start of the run
   bool profile = false;
@@ -118,7 +120,8 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
     return fail(RECON_E_INVALID_ARG, "recon_plan: unknown input_mode");
   if (o.stack_dtype != RECON_STACK_F32 && o.stack_dtype != RECON_STACK_BF16)
     return fail(RECON_E_INVALID_ARG, "recon_plan: unknown stack_dtype");
-  if (o.ramp_mode != RECON_RAMP_SINGLE_AXIS) return fail(RECON_E_INVALID_ARG, "recon_plan: unknown ramp_mode");
+  if (o.ramp_mode != RECON_RAMP_SINGLE_AXIS && o.ramp_mode != RECON_RAMP_DENSITY)
+    return fail(RECON_E_INVALID_ARG, "recon_plan: unknown ramp_mode");
   if (o.filter == RECON_FILTER_TIKHONOV && !(o.eps > 0.0))
     return fail(RECON_E_INVALID_ARG, "recon_plan: eps must be > 0 with the Tikhonov filter");
   if (!std::isfinite(o.sigma) || !std::isfinite(o.eps) || !std::isfinite(o.cs))
@@ -268,6 +271,27 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
   ca.half = p->half;
   ca.su = p->nu + 1;
   ca.layer_elems = (size_t)(p->nv + 2) * (p->nu + 1);
+  {  // sampling-density grid (density weighting only), see density.cuh
+    recon::DensityConst& dc = ca.dens;
+    std::memset(&dc, 0, sizeof(dc));
+    dc.enabled = o.ramp_mode == RECON_RAMP_DENSITY;
+    dc.s = P / 128 > 1 ? P / 128 : 1;
+    dc.Gh = (int)std::ceil(std::sqrt(2.0) * (P / 2.0) / dc.s) + 2;
+    dc.G = 2 * dc.Gh + 1;
+    dc.n_samples1 = P / dc.s;
+    dc.inv_s = 1.0f / (float)dc.s;
+    dc.g_over_p2 = (float)((double)dc.s * dc.s * dc.s / ((double)P * delta) / ((double)P * P));
+    long long band = 0;
+    const long long r2 = (long long)(dc.Gh - 2) * (dc.Gh - 2);
+    for (int z = -dc.Gh; z <= dc.Gh; ++z)
+      for (int y = -dc.Gh; y <= dc.Gh; ++y) {
+        const long long rem = r2 - (long long)z * z - (long long)y * y;
+        if (rem < 0) continue;
+        const int xm = (int)std::floor(std::sqrt((double)rem));
+        band += 2 * (long long)xm + 1;
+      }
+    dc.eps_scale = (float)(1e-3 / (double)band);
+  }
 
   recon::BackprojConst& cb = p->cb;
   cb.nx = p->nx;
@@ -324,6 +348,10 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
   off = align256(off + sizeof(float2) * P);
   p->off_twp = off;
   off = align256(off + sizeof(float2) * p->twp.size());
+  p->off_dens = off;
+  if (ca.dens.enabled) off = align256(off + sizeof(float) * (size_t)ca.dens.G * ca.dens.G * ca.dens.G);
+  p->off_dsum = off;
+  off = align256(off + sizeof(double));
   p->table_bytes = off;
   p->off_S = off;
   off = align256(off + (size_t)db * p->nv * p->half * 8);
@@ -376,6 +404,8 @@ recon::Workspace carve(recon_plan_t p, void* ws) {
   w.ramp = (float*)(b + p->off_ramp);
   w.tw = (float2*)(b + p->off_tw);
   w.twp = (float2*)(b + p->off_twp);
+  w.dens = (float*)(b + p->off_dens);
+  w.band_sum = (double*)(b + p->off_dsum);
   w.S = (float2*)(b + p->off_S);
   w.T = (float2*)(b + p->off_T);
   w.stack = (void*)(b + p->off_stack);
@@ -396,6 +426,10 @@ int upload_tables(recon_plan_t p, const recon::Workspace& w, cudaStream_t s) {
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(w.twp, p->twp.data(), sizeof(float2) * p->twp.size(), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e, "upload of plan tables");
+  if (p->ca.dens.enabled) {
+    e = recon::launch_density_setup(p->ca.dens, w.dirs, p->D, p->P, w.dens, w.band_sum, s);
+    if (e != cudaSuccess) return cuda_fail(e, "sampling-density setup");
+  }
   return RECON_OK;
 }
 
@@ -564,6 +598,8 @@ int run_in_scratch(recon_plan_t p, const float* images, float* volume, char* scr
   w.ramp = (float*)(scratch + p->off_ramp);
   w.tw = (float2*)(scratch + p->off_tw);
   w.twp = (float2*)(scratch + p->off_twp);
+  w.dens = (float*)(scratch + p->off_dens);
+  w.band_sum = (double*)(scratch + p->off_dsum);
   size_t off = p->table_bytes;
   w.S = (float2*)(scratch + off);
   off += align256(db * spec);

@@ -21,6 +21,17 @@ struct DirParams {
 };
 static_assert(sizeof(DirParams) == 128, "DirParams must stay 128 bytes");
 
+// Constants of the sampling-density weighting (density.cuh).
+struct DensityConst {
+  int enabled;       // ramp_mode == RECON_RAMP_DENSITY
+  int s;             // sampling step, DFT bins per cell
+  int Gh, G;         // half width, side (2 Gh + 1)
+  int n_samples1;    // P / s samples per image axis
+  float inv_s;       // 1 / s
+  float g_over_p2;   // g / P^2 (the inverse DFT's 1/P^2 folded in)
+  float eps_scale;   // 1e-3 / (cells in the band)
+};
+
 // Constants of stage A (FFT -> per-layer filter -> inverse FFT -> stack).
 struct StageAConst {
   int P, logP;          // padded FFT size and its log2
@@ -36,6 +47,7 @@ struct StageAConst {
   int half;             // P/2 + 1 (columns of the half spectrum)
   int su;               // stack row pitch in tap pairs, nu + 1
   size_t layer_elems;   // pairs per layer, (nv + 2) * (nu + 1)
+  DensityConst dens;
 };
 
 // Device pointers into the workspace.
@@ -48,6 +60,8 @@ struct Workspace {
   float2* S;            // [DB][nv][P/2+1]: row transforms
   float2* T;            // [DB][Nz][P/2+1][nv]: per-layer column inverse transforms (column-major)
   void* stack;          // [DB][Nz][nv+2][nu+1] tap pairs (Y[v][u-1], Y[v][u]), zero outside
+  float* dens;          // [G][G][G] sampling density S (density weighting only)
+  double* band_sum;     // sum of S over the band (sets eps_S)
 };
 
 // Kernel launchers (stage_a.cu, backproject.cu).  They return cudaGetLastError().

@@ -16,6 +16,7 @@
 // circular filters this equals any other placement with the same crop.
 #include <cuda_bf16.h>
 
+#include "density.cuh"
 #include "fft_reg.cuh"
 #include "recon_internal.h"
 #include "sinpi_poly.h"
@@ -121,7 +122,10 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(const float* __restrict__
 template <int P>
 __global__ void __launch_bounds__(kThreads, 4) k_cols(const float2* __restrict__ S, float2* __restrict__ T,
                                                     const float2* __restrict__ twg, const uint64_t* __restrict__ uA,
-                                                    const float* __restrict__ ramp, StageAConst c, int dir_begin) {
+                                                    const float* __restrict__ ramp, const DirParams* __restrict__ dirs,
+                                                    const float* __restrict__ dens,
+                                                    const double* __restrict__ band_sum, StageAConst c,
+                                                    int dir_begin) {
   constexpr int TT = P / 8, CB = groups_per_cta<P>(), L = fft::buffer_len(P), NT = fft::pass_table_len(P);
   __shared__ float2 tw[NT];
   __shared__ float2 buf_all[CB * L];
@@ -148,7 +152,29 @@ __global__ void __launch_bounds__(kThreads, 4) k_cols(const float2* __restrict__
 
   const bool ok = col < c.half;
   const int colc = ok ? col : c.half - 1;
-  const float w = ramp[colc];
+  // ramp (single-axis scans) or sampling-density weight (any geometry), 1/P^2 included
+  float wgt[8];
+  if (c.dens.enabled) {
+    const DirParams& dp = dirs[dir_begin + n];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      const int m = j + s * TT;
+      const int mv = m < P / 2 ? m : m - P;
+      float wv = density_weight(c.dens, dens, band_sum, dp.af, dp.bf, (float)colc, (float)mv);
+      // the Nyquist bin is its own alias (+-P/2): mean over both, so that W stays even
+      const bool nyq_u = colc == P / 2, nyq_v = m == P / 2;
+      if (nyq_u || nyq_v) {
+        const float w2 = density_weight(c.dens, dens, band_sum, dp.af, dp.bf, nyq_u ? -(float)colc : (float)colc,
+                                        (nyq_v && !nyq_u) ? -(float)mv : (float)mv);
+        wv = 0.5f * (wv + w2);
+      }
+      wgt[s] = wv;
+    }
+  } else {
+    const float w = ramp[colc];
+#pragma unroll
+    for (int s = 0; s < 8; ++s) wgt[s] = w;
+  }
   // chi/(2 pi) in 2^-32 turns needs only the top 32 bits of the 64-bit fixed-point
   // sum: the per-layer product uA_k * m is formed as hi(uA) * m + umulhi(lo(uA), m), and
   // the layer-independent part uC * m^2 - uW once per element (dropped low-word carries
@@ -170,7 +196,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_cols(const float2* __restrict__
     float2 x[8];
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-      float f = w;
+      float f = wgt[s];
       if (c.filter) {
         const uint32_t hi = a_hi * msq[s] + __umulhi(a_lo, msq[s]) + base_hi[s];
         const float sn = sin_half_turns((int32_t)hi);
@@ -328,8 +354,9 @@ __global__ void k_small_rows_fwd(const float* __restrict__ images, float2* __res
 }
 
 __global__ void k_small_cols(const float2* __restrict__ S, float2* __restrict__ T, const float2* __restrict__ twg,
-                             const uint64_t* __restrict__ uA, const float* __restrict__ ramp, StageAConst c,
-                             int dir_begin) {
+                             const uint64_t* __restrict__ uA, const float* __restrict__ ramp,
+                             const DirParams* __restrict__ dirs, const float* __restrict__ dens,
+                             const double* __restrict__ band_sum, StageAConst c, int dir_begin) {
   __shared__ float2 tw[8];
   __shared__ float2 G[8];
   __shared__ float2 Wk[8];
@@ -341,11 +368,20 @@ __global__ void k_small_cols(const float2* __restrict__ S, float2* __restrict__ 
     G[bitrev(v, c.logP)] = v < c.nv ? Sn[(size_t)v * c.half + col] : make_float2(0.f, 0.f);
   fft_radix2<false>(G, c.P, c.logP, tw);
   const uint64_t* uAn = uA + (size_t)(dir_begin + n) * c.nz_layers;
+  const int hP = c.P >> 1;
   for (int k = 0; k < c.nz_layers; ++k) {
     for (int m = threadIdx.x; m < c.P; m += blockDim.x) {
       const int mv = m < (c.P >> 1) ? m : m - c.P;
       const uint64_t msq = (uint64_t)(col * col + mv * mv);
       float f = ramp[col];
+      if (c.dens.enabled) {
+        const DirParams& dp = dirs[dir_begin + n];
+        f = density_weight(c.dens, dens, band_sum, dp.af, dp.bf, (float)col, (float)mv);
+        const bool nyq_u = col == hP, nyq_v = m == hP;  // the Nyquist bin is its own alias
+        if (nyq_u || nyq_v)
+          f = 0.5f * (f + density_weight(c.dens, dens, band_sum, dp.af, dp.bf, nyq_u ? -(float)col : (float)col,
+                                         (nyq_v && !nyq_u) ? -(float)mv : (float)mv));
+      }
       if (c.filter) {
         const float sn = sin_from_turns(uAn[k] * msq + c.uC * (msq * msq) - c.uW);
         f *= c.pref * __fdividef(sn, fmaf(sn, sn, c.eps));
@@ -404,8 +440,8 @@ cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* i
   k_rows_fwd<P><<<dim3((c.nv + 2 * G - 1) / (2 * G), dir_count), kThreads, 0, stream>>>(images, ws.S, ws.twp, c,
                                                                                          dir_begin);
   if (ev) cudaEventRecord(ev[0], stream);
-  k_cols<P><<<dim3((c.half + G - 1) / G, dir_count), kThreads, 0, stream>>>(ws.S, ws.T, ws.twp, ws.uA, ws.ramp, c,
-                                                                             dir_begin);
+  k_cols<P><<<dim3((c.half + G - 1) / G, dir_count), kThreads, 0, stream>>>(
+      ws.S, ws.T, ws.twp, ws.uA, ws.ramp, ws.dirs, ws.dens, ws.band_sum, c, dir_begin);
   if (ev) cudaEventRecord(ev[1], stream);
   const dim3 gi((c.nv + 2 * G - 1) / (2 * G), c.nz_layers, dir_count);
   if (c.stack_bf16)
@@ -419,7 +455,8 @@ cudaError_t launch_small(const StageAConst& c, const Workspace& ws, const float*
                          int dir_count, cudaStream_t stream, cudaEvent_t* ev) {
   k_small_rows_fwd<<<dim3((c.nv + 1) / 2, dir_count), 32, 0, stream>>>(images, ws.S, ws.tw, c, dir_begin);
   if (ev) cudaEventRecord(ev[0], stream);
-  k_small_cols<<<dim3(c.half, dir_count), 32, 0, stream>>>(ws.S, ws.T, ws.tw, ws.uA, ws.ramp, c, dir_begin);
+  k_small_cols<<<dim3(c.half, dir_count), 32, 0, stream>>>(ws.S, ws.T, ws.tw, ws.uA, ws.ramp, ws.dirs, ws.dens,
+                                                          ws.band_sum, c, dir_begin);
   if (ev) cudaEventRecord(ev[1], stream);
   const dim3 gi((c.nv + 1) / 2, c.nz_layers, dir_count);
   if (c.stack_bf16)

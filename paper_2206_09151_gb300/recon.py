@@ -10,6 +10,7 @@ from . import _abi
 _FILTERS = {"off": _abi.RECON_FILTER_OFF, "tikhonov": _abi.RECON_FILTER_TIKHONOV}
 _INPUTS = {"intensity": _abi.RECON_INPUT_INTENSITY, "contrast": _abi.RECON_INPUT_CONTRAST}
 _STACKS = {"f32": _abi.RECON_STACK_F32, "bf16": _abi.RECON_STACK_BF16}
+_RAMPS = {"single_axis": _abi.RECON_RAMP_SINGLE_AXIS, "density": _abi.RECON_RAMP_DENSITY}
 
 
 class Reconstructor:
@@ -22,11 +23,12 @@ class Reconstructor:
     def __init__(self, rot, nu: int, nv: int, grid, *, lam: float, delta: float, defocus, nz_layers: int,
                  sigma: float = 0.0, eps: float = 0.1, cs: float = 0.0, filter: str = "tikhonov",
                  input_mode: str = "intensity", stack_dtype: str = "f32", accumulate: bool = False,
-                 dir_block: int = 0, device=None, allocate: bool = True):
+                 dir_block: int = 0, ramp: str = "single_axis", device=None, allocate: bool = True):
         o = _abi.recon_default_options()
         o.sigma, o.eps, o.cs = float(sigma), float(eps), float(cs)
         o.filter, o.input_mode, o.stack_dtype = _FILTERS[filter], _INPUTS[input_mode], _STACKS[stack_dtype]
         o.accumulate, o.dir_block = int(bool(accumulate)), int(dir_block)
+        o.ramp_mode = _RAMPS[ramp]
         self.rot = np.ascontiguousarray(rot, np.float64).reshape(-1, 3, 3)
         self.D = self.rot.shape[0]
         self.nu, self.nv, self.grid, self.nz_layers = nu, nv, tuple(grid), nz_layers

@@ -79,6 +79,14 @@ def test_plan_rejects_bad_arguments(lib, kw, code):
     assert _abi.recon_last_error() != ""
 
 
+def test_density_weighting_accepts_any_geometry(lib):
+    o = _abi.recon_default_options()
+    o.ramp_mode = _abi.RECON_RAMP_DENSITY
+    p = _plan(rot=ph.cone_rotations(12, 40.0, seed=1), opts=o)
+    assert _abi.recon_workspace_size(p) > 0
+    _abi.recon_destroy(p)
+
+
 def test_plan_rejects_bad_options(lib):
     o = _abi.recon_default_options()
     o.eps = 0.0
