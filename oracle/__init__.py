@@ -9,3 +9,4 @@ from .recon_fp64 import (  # noqa: F401
     backproject_direction, bilinear, contrast, ctf_filter, density_geometry, density_grid, density_weights, depth_extent, layer_centres, layer_constants,
     layer_index, layer_stack, padded_size, pixel_coefficients, ramp_weights, recon, signed_freq,
 )
+from . import learned_fp64 as learned  # noqa: F401,E402

@@ -43,6 +43,8 @@ __all__ = [
     "multislice_images",
     "ball_projections",
     "config_workload",
+    "mlp_init",
+    "layer_projections",
 ]
 
 
@@ -262,6 +264,47 @@ def multislice_images(ph: Phantom, rot: np.ndarray, nu: int, nv: int, delta: flo
         if photons is not None:
             I = torch.poisson(I * photons, generator=gen) / photons
         out[n] = I.to(dtype)
+    return out
+
+
+# ----------------------------------------------------------------------------- learned filter
+def mlp_init(seed: int, eps0: float = 0.1) -> np.ndarray:
+    """Seeded initial parameters of the 3 -> 64 -> 64 -> 1 regulariser network (4481 floats,
+    layout W1[64][3], b1, W2[64][64], b2, w3, b3): He-uniform weights, zero hidden biases,
+    and an output bias at softplus^-1(eps0) so that the untrained network sits near the
+    Tikhonov value eps0."""
+    rng = np.random.default_rng(seed)
+    h = 64
+    W1 = rng.uniform(-1, 1, (h, 3)) * math.sqrt(6.0 / 3)
+    W2 = rng.uniform(-1, 1, (h, h)) * math.sqrt(6.0 / h)
+    w3 = rng.uniform(-1, 1, h) * math.sqrt(6.0 / h) * 0.01
+    b3 = math.log(math.expm1(eps0))
+    return np.concatenate([W1.ravel(), np.zeros(h), W2.ravel(), np.zeros(h), w3, [b3]]).astype(np.float64)
+
+
+def layer_projections(ph: Phantom, rot: np.ndarray, nu: int, nv: int, grid, nz_layers: int,
+                      delta: float) -> np.ndarray:
+    """True projections (metres) of the parts of the phantom that fall in each depth layer
+    (Nz equal slabs over the volume's bounding-box extent along the beam), float64
+    (D, Nz, nv, nu): the targets of the learned regulariser.  A primitive is assigned to
+    the layer holding its centre."""
+    nx, ny, nz = grid
+    out = np.zeros((rot.shape[0], nz_layers, nv, nu))
+    uu = np.arange(nu) - (nu - 1) / 2.0
+    vv = np.arange(nv) - (nv - 1) / 2.0
+    for n in range(rot.shape[0]):
+        d = rot[n, 2]
+        ext = abs(d[0]) * nx + abs(d[1]) * ny + abs(d[2]) * nz
+        c = ph.centre @ rot[n].T
+        layer = np.clip(np.floor((c[:, 2] + ext / 2) / (ext / nz_layers)), 0, nz_layers - 1).astype(int)
+        for b in range(c.shape[0]):
+            r2 = (uu[None, :] - c[b, 0]) ** 2 + (vv[:, None] - c[b, 1]) ** 2
+            s = ph.size[b]
+            if ph.kind == "ball":
+                p = 2.0 * ph.amp[b] * np.sqrt(np.maximum(s * s - r2, 0.0))
+            else:
+                p = ph.amp[b] * math.sqrt(2.0 * math.pi) * s * np.exp(-r2 / (2.0 * s * s))
+            out[n, layer[b]] += p * delta
     return out
 
 
