@@ -58,6 +58,11 @@ extern "C" {
 /* ---------------------------------------------------------------- option values */
 #define RECON_FILTER_OFF 0       /* H = 1: ramp-filtered backprojection of g (Eq. 15)   */
 #define RECON_FILTER_TIKHONOV 1  /* H_k above (real part of Eq. 11, per layer)         */
+#define RECON_FILTER_MLP 2       /* H_k with eps from the learned network (see below)   */
+
+/* Parameters of the learned regulariser: a 3 -> 64 -> 64 -> 1 ReLU network, float32,
+ * laid out W1[64][3], b1[64], W2[64][64], b2[64], w3[64], b3. */
+#define RECON_MLP_PARAMS 4481
 
 #define RECON_INPUT_INTENSITY 0  /* images are I/I_in; g = ln(max(I/I_in, 1e-6))       */
 #define RECON_INPUT_CONTRAST 1   /* images already are g (a contrast or a projection)  */
@@ -97,6 +102,9 @@ typedef struct {
   int ramp_mode;   /* RECON_RAMP_* (single-axis ramp, or sampling-density weighting)       */
   int accumulate;  /* 0: run overwrites vol; 1: run adds into vol                       */
   int dir_block;   /* directions per block (stack held in workspace), 0 = automatic    */
+  const float* mlp_weights; /* host [RECON_MLP_PARAMS], copied; needed by RECON_FILTER_MLP  */
+  double nsr;      /* noise-to-signal ratio of one image pixel (the NSR of Sec. 3); sets
+                      the Poisson floor (nsr M)^2 per DFT coefficient of the SNR feature   */
 } recon_options;
 
 /* Fills *opts with defaults: sigma 0, eps 0.1 (the value of Sec. 3), cs 0, Tikhonov
@@ -146,6 +154,38 @@ int recon_backproject(recon_plan_t plan, const void* stack, int dir_begin, int d
 
 /* Plan facts: padded FFT size P, directions per block, number of blocks. */
 int recon_plan_info(recon_plan_t plan, int* padded, int* dir_block, int* n_blocks);
+
+/* The learned regulariser (RECON_FILTER_MLP).  eps of Eq. 11 (chosen "ad hoc" in
+ * Sec. 3) becomes eps_theta = softplus(network(x)) per (direction, layer, radial bin b),
+ * bins b = min(isqrt(m_u^2 + m_v^2) / w, n_b - 1), w = max(1, P/128).  Inputs x:
+ * log10(SNR_b)/3 clamped to [-1, 2], with SNR_b the radial power of the image spectrum
+ * over the Poisson floor nsr^2 nu nv (the Parseval scaling of Sec. 3's noise filter);
+ * the bin-centre radius / (P/2); lambda (R_n - z_k) / delta^2 / 100.
+ *
+ * recon_mlp_train fits the parameters on training images with known layer contents:
+ * it minimises sum over images n, layers k and frequencies q of |H_nk(q) G_n(q) -
+ * T_nk(q)|^2 / sum |T_nk(q)|^2 (G: DFT of the contrast, T: DFT of the true projection of
+ * layer k's slab, in metres) with Adam (beta 0.9 / 0.999), on the GPU.  steps = 0
+ * returns the loss and (if grad != NULL) its gradient at the given weights.  The call
+ * waits for `stream` before returning. */
+typedef struct {
+  int n_img, nu, nv, nz_layers;  /* training images, image size, layers per image        */
+  const double* rot;             /* host [n_img][9] rotations (as in recon_geometry)      */
+  const double* defocus;         /* host [n_img] R_n (m)                                  */
+  int grid_nx, grid_ny, grid_nz; /* volume whose bounding box defines the layers         */
+  double lambda, delta, sigma, cs, nsr;
+  int input_mode;                /* RECON_INPUT_*                                         */
+  const float* images;           /* device [n_img][nv][nu]                                */
+  const float* targets;          /* device [n_img][nz_layers][nv][nu] layer projections   */
+  int steps;                     /* Adam steps                                            */
+  float lr;                      /* Adam step size                                        */
+} recon_train_cfg;
+
+int recon_mlp_train_workspace_size(const recon_train_cfg* cfg, size_t* bytes);
+/* weights: host [RECON_MLP_PARAMS] in/out; loss_history: host [max(steps, 1)], the loss
+ * before each step; grad: host [RECON_MLP_PARAMS] or NULL (filled when steps = 0). */
+int recon_mlp_train(const recon_train_cfg* cfg, float* weights, float* loss_history, float* grad, void* workspace,
+                    size_t ws_bytes, void* stream);
 
 /* Optional kernel timing.  While enabled, recon_run records CUDA events on its
  * stream around each kernel of each direction block (row FFTs, column filter/iFFTs,

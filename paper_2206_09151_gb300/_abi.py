@@ -22,6 +22,8 @@ RECON_E_NO_MEMORY = -5
 
 RECON_FILTER_OFF = 0
 RECON_FILTER_TIKHONOV = 1
+RECON_FILTER_MLP = 2
+RECON_MLP_PARAMS = 4481
 RECON_INPUT_INTENSITY = 0
 RECON_INPUT_CONTRAST = 1
 RECON_STACK_F32 = 0
@@ -43,7 +45,18 @@ class ReconGeometry(ctypes.Structure):
 class ReconOptions(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("eps", ctypes.c_double), ("cs", ctypes.c_double),
                 ("filter", ctypes.c_int), ("input_mode", ctypes.c_int), ("stack_dtype", ctypes.c_int),
-                ("ramp_mode", ctypes.c_int), ("accumulate", ctypes.c_int), ("dir_block", ctypes.c_int)]
+                ("ramp_mode", ctypes.c_int), ("accumulate", ctypes.c_int), ("dir_block", ctypes.c_int),
+                ("mlp_weights", ctypes.POINTER(ctypes.c_float)), ("nsr", ctypes.c_double)]
+
+
+class ReconTrainCfg(ctypes.Structure):
+    _fields_ = [("n_img", ctypes.c_int), ("nu", ctypes.c_int), ("nv", ctypes.c_int), ("nz_layers", ctypes.c_int),
+                ("rot", ctypes.POINTER(ctypes.c_double)), ("defocus", ctypes.POINTER(ctypes.c_double)),
+                ("grid_nx", ctypes.c_int), ("grid_ny", ctypes.c_int), ("grid_nz", ctypes.c_int),
+                ("lambda_", ctypes.c_double), ("delta", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("cs", ctypes.c_double), ("nsr", ctypes.c_double), ("input_mode", ctypes.c_int),
+                ("images", ctypes.c_void_p), ("targets", ctypes.c_void_p), ("steps", ctypes.c_int),
+                ("lr", ctypes.c_float)]
 
 
 class ReconError(RuntimeError):
@@ -75,6 +88,9 @@ def load_library(path: str = LIB_PATH):
     L.recon_backproject.argtypes = [vp, vp, ip, ip, vp, ip, vp, sz, vp]
     L.recon_plan_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.recon_run_noalloc.argtypes = [vp, vp, vp, vp]
+    L.recon_mlp_train_workspace_size.argtypes = [ctypes.POINTER(ReconTrainCfg), ctypes.POINTER(sz)]
+    L.recon_mlp_train.argtypes = [ctypes.POINTER(ReconTrainCfg), ctypes.POINTER(ctypes.c_float),
+                                  ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), vp, sz, vp]
     L.recon_profile_enable.argtypes = [vp, ip]
     L.recon_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ip)]
     L.recon_sync.argtypes = [vp]
@@ -85,7 +101,7 @@ def load_library(path: str = LIB_PATH):
     L.recon_last_error.restype = ctypes.c_char_p
     for name in ("recon_plan", "recon_workspace_size", "recon_run", "recon_filter_stage", "recon_backproject",
                  "recon_plan_info", "recon_sync", "recon_destroy", "recon_profile_enable", "recon_profile_read",
-                 "recon_run_noalloc"):
+                 "recon_run_noalloc", "recon_mlp_train_workspace_size", "recon_mlp_train"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -123,6 +139,39 @@ def recon_plan(rot: np.ndarray, nu: int, nv: int, lam: float, delta: float, defo
                       nz_layers, ctypes.byref(g), ctypes.byref(opts) if opts is not None else None, ctypes.byref(out))
     _check(rc, "recon_plan")
     return out
+
+
+def make_train_cfg(rot, defocus, nu, nv, nz_layers, grid, lam, delta, sigma, cs, nsr, input_mode, images_ptr,
+                   targets_ptr, steps, lr):
+    """A recon_train_cfg; returns it with the host arrays it points to (keep both alive)."""
+    rot = np.ascontiguousarray(rot, dtype=np.float64).reshape(-1, 3, 3)
+    defocus = np.ascontiguousarray(defocus, dtype=np.float64).reshape(-1)
+    cfg = ReconTrainCfg(rot.shape[0], nu, nv, nz_layers, rot.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                        defocus.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), grid[0], grid[1], grid[2], lam,
+                        delta, sigma, cs, nsr, input_mode, images_ptr, targets_ptr, steps, lr)
+    return cfg, (rot, defocus)
+
+
+def recon_mlp_train_workspace_size(cfg: ReconTrainCfg) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().recon_mlp_train_workspace_size(ctypes.byref(cfg), ctypes.byref(n)),
+           "recon_mlp_train_workspace_size")
+    return n.value
+
+
+def recon_mlp_train(cfg: ReconTrainCfg, weights: np.ndarray, ws_ptr: int, ws_bytes: int, stream: int,
+                    want_grad: bool = False):
+    """Runs the training; returns (weights, loss history, gradient or None)."""
+    w = np.ascontiguousarray(weights, dtype=np.float32).copy()
+    if w.size != RECON_MLP_PARAMS:
+        raise ValueError("weights must hold RECON_MLP_PARAMS values")
+    loss = np.zeros(max(cfg.steps, 1), np.float32)
+    grad = np.zeros(RECON_MLP_PARAMS, np.float32) if want_grad else None
+    fp = ctypes.POINTER(ctypes.c_float)
+    _check(load_library().recon_mlp_train(ctypes.byref(cfg), w.ctypes.data_as(fp), loss.ctypes.data_as(fp),
+                                          grad.ctypes.data_as(fp) if grad is not None else None, ws_ptr, ws_bytes,
+                                          stream), "recon_mlp_train")
+    return w, loss, grad
 
 
 def recon_workspace_size(plan) -> int:

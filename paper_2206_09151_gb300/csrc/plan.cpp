@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "density.cuh"
+#include "learned.cuh"
 #include "recon_internal.h"
 
 namespace {
@@ -51,11 +52,14 @@ struct recon_plan_s {
   std::vector<float> ramp;
   std::vector<float2> tw;
   std::vector<float2> twp;
+  std::vector<float> theta, cnt, x2;  // learned regulariser: weights, bin counts, defocus feature
+  recon::LearnConst lc;
+  bool training = false;
   recon::StageAConst ca;
   recon::BackprojConst cb;
   // workspace layout (byte offsets)
-  size_t off_dirs, off_uA, off_ramp, off_tw, off_twp, off_dens, off_dsum, off_S, off_T, off_stack, ws_bytes,
-      table_bytes;
+  size_t off_dirs, off_uA, off_ramp, off_tw, off_twp, off_dens, off_dsum, off_theta, off_cnt, off_x2, off_S, off_T,
+      off_stack, off_pow, off_eps, ws_bytes, table_bytes;
   size_t stack_dir_bytes;
   // optional profiling: 4 events per block plus one at the start of the run
   bool profile = false;
@@ -79,6 +83,8 @@ void recon_default_options(recon_options* o) {
   o->ramp_mode = RECON_RAMP_SINGLE_AXIS;
   o->accumulate = 0;
   o->dir_block = 0;
+  o->mlp_weights = nullptr;
+  o->nsr = 0.0;
 }
 
 const char* recon_error_string(int code) {
@@ -95,8 +101,13 @@ const char* recon_error_string(int code) {
 
 const char* recon_last_error(void) { return g_last_error.c_str(); }
 
-int recon_plan(const recon_geometry* geom, double lambda, double delta, const double* defocus, int nz_layers,
-               const recon_grid* grid, const recon_options* opts, recon_plan_t* out) {
+}  // extern "C"
+
+// Builds a plan; `training` (recon_mlp_train's internal plan) accepts any geometry and
+// skips the ramp, density and learned-filter set-up.
+static int plan_create(const recon_geometry* geom, double lambda, double delta, const double* defocus,
+                       int nz_layers, const recon_grid* grid, const recon_options* opts, recon_plan_t* out,
+                       bool training) {
   if (!geom || !grid || !out) return fail(RECON_E_INVALID_ARG, "recon_plan: null geometry, grid or out");
   const int D = geom->n_dir;
   if (D < 0) return fail(RECON_E_INVALID_ARG, "recon_plan: n_dir < 0");
@@ -114,14 +125,20 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
   recon_options o;
   recon_default_options(&o);
   if (opts) o = *opts;
-  if (o.filter != RECON_FILTER_OFF && o.filter != RECON_FILTER_TIKHONOV)
+  if (o.filter != RECON_FILTER_OFF && o.filter != RECON_FILTER_TIKHONOV && o.filter != RECON_FILTER_MLP)
     return fail(RECON_E_INVALID_ARG, "recon_plan: unknown filter");
+  if (o.filter == RECON_FILTER_MLP && !training && (!o.mlp_weights || !(o.nsr > 0.0) || !std::isfinite(o.nsr)))
+    return fail(RECON_E_INVALID_ARG, "recon_plan: the learned filter needs mlp_weights and nsr > 0");
   if (o.input_mode != RECON_INPUT_INTENSITY && o.input_mode != RECON_INPUT_CONTRAST)
     return fail(RECON_E_INVALID_ARG, "recon_plan: unknown input_mode");
   if (o.stack_dtype != RECON_STACK_F32 && o.stack_dtype != RECON_STACK_BF16)
     return fail(RECON_E_INVALID_ARG, "recon_plan: unknown stack_dtype");
   if (o.ramp_mode != RECON_RAMP_SINGLE_AXIS && o.ramp_mode != RECON_RAMP_DENSITY)
     return fail(RECON_E_INVALID_ARG, "recon_plan: unknown ramp_mode");
+  if (training) {
+    o.ramp_mode = RECON_RAMP_SINGLE_AXIS;
+    o.filter = RECON_FILTER_MLP;
+  }
   if (o.filter == RECON_FILTER_TIKHONOV && !(o.eps > 0.0))
     return fail(RECON_E_INVALID_ARG, "recon_plan: eps must be > 0 with the Tikhonov filter");
   if (!std::isfinite(o.sigma) || !std::isfinite(o.eps) || !std::isfinite(o.cs))
@@ -140,6 +157,7 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
   p->lambda = lambda;
   p->delta = delta;
   p->opt = o;
+  p->training = training;
   int P = 1, logP = 0;
   while (P < 2 * (p->nu > p->nv ? p->nu : p->nv)) {
     P *= 2;
@@ -169,7 +187,7 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
             return fail(RECON_E_INVALID_ARG, "recon_plan: rot[" + std::to_string(n) + "] is not orthonormal");
           }
         }
-      if (o.ramp_mode == RECON_RAMP_SINGLE_AXIS &&
+      if (o.ramp_mode == RECON_RAMP_SINGLE_AXIS && !training &&
           (std::fabs(R[3] - geom->rot[3]) > 1e-9 || std::fabs(R[4] - geom->rot[4]) > 1e-9 ||
            std::fabs(R[5] - geom->rot[5]) > 1e-9)) {
         delete p;
@@ -292,6 +310,44 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
       }
     dc.eps_scale = (float)(1e-3 / (double)band);
   }
+  {  // learned regulariser tables
+    recon::LearnConst& lc = p->lc;
+    lc.bin_width = P / 128 > 1 ? P / 128 : 1;
+    long long half_sq = (long long)P * P / 2, r = (long long)std::sqrt((double)half_sq);
+    while (r * r > half_sq) --r;
+    while ((r + 1) * (r + 1) <= half_sq) ++r;
+    lc.n_bins = (int)(r / lc.bin_width) + 1;
+    lc.inv_half_p = 2.0f / (float)P;
+    lc.noise_floor = (float)(o.nsr * o.nsr * (double)p->nu * (double)p->nv);
+    if (o.filter == RECON_FILTER_MLP) {
+      try {
+        p->theta.assign(recon::kMlpParams, 0.f);
+        if (o.mlp_weights) std::memcpy(p->theta.data(), o.mlp_weights, sizeof(float) * recon::kMlpParams);
+        p->cnt.assign(lc.n_bins, 0.f);
+        for (int a = -P / 2; a < P / 2; ++a)
+          for (int b = -P / 2; b < P / 2; ++b) {
+            const long long msq = (long long)a * a + (long long)b * b;
+            long long q = (long long)std::sqrt((double)msq);
+            while (q * q > msq) --q;
+            while ((q + 1) * (q + 1) <= msq) ++q;
+            const int bin = (int)(q / lc.bin_width);
+            p->cnt[bin < lc.n_bins - 1 ? bin : lc.n_bins - 1] += 1.f;
+          }
+        p->x2.assign((size_t)(D > 0 ? D : 1) * nz_layers, 0.f);
+        for (int n = 0; n < D; ++n) {
+          const double* R = geom->rot + 9 * (size_t)n;
+          const double ext = ((std::fabs(R[6]) * p->nx + std::fabs(R[7]) * p->ny) + std::fabs(R[8]) * p->nz) * delta;
+          for (int k = 0; k < nz_layers; ++k) {
+            const double zk = -0.5 * ext + (k + 0.5) * (ext / nz_layers);
+            p->x2[(size_t)n * nz_layers + k] = (float)(lambda * (defocus[n] - zk) / (delta * delta) / 100.0);
+          }
+        }
+      } catch (const std::bad_alloc&) {
+        delete p;
+        return fail(RECON_E_NO_MEMORY, "recon_plan: out of host memory");
+      }
+    }
+  }
 
   recon::BackprojConst& cb = p->cb;
   cb.nx = p->nx;
@@ -352,6 +408,12 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
   if (ca.dens.enabled) off = align256(off + sizeof(float) * (size_t)ca.dens.G * ca.dens.G * ca.dens.G);
   p->off_dsum = off;
   off = align256(off + sizeof(double));
+  p->off_theta = off;
+  off = align256(off + sizeof(float) * p->theta.size());
+  p->off_cnt = off;
+  off = align256(off + sizeof(float) * p->cnt.size());
+  p->off_x2 = off;
+  off = align256(off + sizeof(float) * p->x2.size());
   p->table_bytes = off;
   p->off_S = off;
   off = align256(off + (size_t)db * p->nv * p->half * 8);
@@ -359,10 +421,28 @@ int recon_plan(const recon_geometry* geom, double lambda, double delta, const do
   off = align256(off + (size_t)db * nz_layers * p->nv * p->half * 8);
   p->off_stack = off;
   off = align256(off + (size_t)db * p->stack_dir_bytes);
+  p->off_pow = off;
+  p->off_eps = off;
+  if (o.filter == RECON_FILTER_MLP && !training) {
+    off = align256(off + sizeof(float) * (size_t)db * p->lc.n_bins);
+    p->off_eps = off;
+    off = align256(off + sizeof(float) * (size_t)db * nz_layers * p->lc.n_bins);
+  }
   p->ws_bytes = off;
+  if (o.filter == RECON_FILTER_MLP && !training && P < 16) {
+    delete p;
+    return fail(RECON_E_UNSUPPORTED_SIZE, "recon_plan: the learned filter needs images of more than 4 pixels");
+  }
   *out = p;
   return RECON_OK;
 }
+
+extern "C" int recon_plan(const recon_geometry* geom, double lambda, double delta, const double* defocus,
+                          int nz_layers, const recon_grid* grid, const recon_options* opts, recon_plan_t* out) {
+  return plan_create(geom, lambda, delta, defocus, nz_layers, grid, opts, out, false);
+}
+
+extern "C" {
 
 int recon_workspace_size(recon_plan_t p, size_t* bytes) {
   if (!p || !bytes) return fail(RECON_E_INVALID_ARG, "recon_workspace_size: null argument");
@@ -406,6 +486,9 @@ recon::Workspace carve(recon_plan_t p, void* ws) {
   w.twp = (float2*)(b + p->off_twp);
   w.dens = (float*)(b + p->off_dens);
   w.band_sum = (double*)(b + p->off_dsum);
+  w.eps = (float*)(b + p->off_eps);
+  w.n_bins = p->lc.n_bins;
+  w.bin_width = p->lc.bin_width;
   w.S = (float2*)(b + p->off_S);
   w.T = (float2*)(b + p->off_T);
   w.stack = (void*)(b + p->off_stack);
@@ -425,12 +508,43 @@ int upload_tables(recon_plan_t p, const recon::Workspace& w, cudaStream_t s) {
     e = cudaMemcpyAsync(w.tw, p->tw.data(), sizeof(float2) * p->tw.size(), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(w.twp, p->twp.data(), sizeof(float2) * p->twp.size(), cudaMemcpyHostToDevice, s);
+  char* base = (char*)w.dirs - p->off_dirs;
+  if (e == cudaSuccess && !p->theta.empty())
+    e = cudaMemcpyAsync(base + p->off_theta, p->theta.data(), sizeof(float) * p->theta.size(), cudaMemcpyHostToDevice,
+                        s);
+  if (e == cudaSuccess && !p->cnt.empty())
+    e = cudaMemcpyAsync(base + p->off_cnt, p->cnt.data(), sizeof(float) * p->cnt.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !p->x2.empty())
+    e = cudaMemcpyAsync(base + p->off_x2, p->x2.data(), sizeof(float) * p->x2.size(), cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e, "upload of plan tables");
   if (p->ca.dens.enabled) {
     e = recon::launch_density_setup(p->ca.dens, w.dirs, p->D, p->P, w.dens, w.band_sum, s);
     if (e != cudaSuccess) return cuda_fail(e, "sampling-density setup");
   }
   return RECON_OK;
+}
+
+// Learned regulariser, between the row FFTs and the column kernel of each block: radial
+// power spectrum of every image (column FFTs), then the eps table of the block.
+struct MlpHookCtx {
+  recon_plan_t p;
+  const char* base;  // workspace start (tables)
+  float* pow;        // [DB][n_bins]
+  float* eps;        // [DB][Nz][n_bins]
+  const float2* S;
+  const float2* twp;
+};
+
+cudaError_t mlp_hook(void* vctx, int dir_begin, int dir_count, cudaStream_t s) {
+  MlpHookCtx* x = (MlpHookCtx*)vctx;
+  recon_plan_t p = x->p;
+  cudaError_t e = cudaMemsetAsync(x->pow, 0, sizeof(float) * (size_t)dir_count * p->lc.n_bins, s);
+  if (e != cudaSuccess) return e;
+  e = recon::launch_cols_forward(p->ca, p->lc, x->S, nullptr, x->pow, x->twp, dir_count, s);
+  if (e != cudaSuccess) return e;
+  return recon::launch_eps_table(p->lc, x->pow, (const float*)(x->base + p->off_cnt),
+                                 (const float*)(x->base + p->off_x2), (const float*)(x->base + p->off_theta),
+                                 x->eps, nullptr, dir_count, p->nzl, dir_begin, s);
 }
 
 }  // namespace
@@ -456,11 +570,14 @@ int recon_run(recon_plan_t p, const float* images, float* volume, void* workspac
   rc = upload_tables(p, w, s);
   if (rc) return rc;
   cudaEvent_t* ev = p->profile ? p->events.data() : nullptr;
+  MlpHookCtx hctx{p, (const char*)workspace, (float*)((char*)workspace + p->off_pow), w.eps, w.S, w.twp};
+  const recon::StageAHook hook{mlp_hook, &hctx};
+  const recon::StageAHook* hk = p->ca.filter == RECON_FILTER_MLP ? &hook : nullptr;
   if (ev) cudaEventRecord(ev[0], s);
   for (int b = 0; b < p->n_blocks; ++b) {
     const int d0 = b * p->db;
     const int cnt = (p->D - d0) < p->db ? (p->D - d0) : p->db;
-    cudaError_t e = recon::launch_stage_a(p->ca, w, images, d0, cnt, s, ev ? ev + 1 + 4 * b : nullptr);
+    cudaError_t e = recon::launch_stage_a(p->ca, w, images, d0, cnt, s, ev ? ev + 1 + 4 * b : nullptr, hk);
     if (e != cudaSuccess) return cuda_fail(e, "recon_run: stage A launch");
     if (ev) cudaEventRecord(ev[3 + 4 * b], s);
     e = recon::launch_backproject(p->cb, w.dirs, w.stack, d0, cnt, volume, p->opt.accumulate || b > 0, s);
@@ -483,7 +600,10 @@ int recon_filter_stage(recon_plan_t p, const float* images, int dir_begin, int d
   const recon::Workspace w = carve(p, workspace);
   rc = upload_tables(p, w, s);
   if (rc) return rc;
-  cudaError_t e = recon::launch_stage_a(p->ca, w, images, dir_begin, dir_count, s);
+  MlpHookCtx hctx{p, (const char*)workspace, (float*)((char*)workspace + p->off_pow), w.eps, w.S, w.twp};
+  const recon::StageAHook hook{mlp_hook, &hctx};
+  cudaError_t e = recon::launch_stage_a(p->ca, w, images, dir_begin, dir_count, s, nullptr,
+                                        p->ca.filter == RECON_FILTER_MLP ? &hook : nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "recon_filter_stage: launch");
   *stack_out = w.stack;
   return RECON_OK;
@@ -576,8 +696,11 @@ int run_in_scratch(recon_plan_t p, const float* images, float* volume, char* scr
   // whose spectra, intermediates and stacks still fit the scratch.
   const size_t spec = (size_t)p->nv * p->half * 8;
   const size_t inter = spec * p->nzl;
+  const bool mlp = p->ca.filter == RECON_FILTER_MLP;
   auto need = [&](size_t db) {
-    return p->table_bytes + align256(db * spec) + align256(db * inter) + align256(db * p->stack_dir_bytes);
+    size_t b = p->table_bytes + align256(db * spec) + align256(db * inter) + align256(db * p->stack_dir_bytes);
+    if (mlp) b += align256(sizeof(float) * db * p->lc.n_bins) + align256(sizeof(float) * db * p->nzl * p->lc.n_bins);
+    return b;
   };
   if (need(1) > scratch_bytes)
     return fail(RECON_E_UNSUPPORTED_SIZE, "recon_run_noalloc: this plan needs " + std::to_string(need(1)) +
@@ -606,13 +729,21 @@ int run_in_scratch(recon_plan_t p, const float* images, float* volume, char* scr
   w.T = (float2*)(scratch + off);
   off += align256(db * inter);
   w.stack = (void*)(scratch + off);
+  off += align256(db * p->stack_dir_bytes);
+  float* pow = (float*)(scratch + off);
+  if (mlp) off += align256(sizeof(float) * db * p->lc.n_bins);
+  w.eps = (float*)(scratch + off);
+  w.n_bins = p->lc.n_bins;
+  w.bin_width = p->lc.bin_width;
   int rc = upload_tables(p, w, s);
   if (rc) return rc;
+  MlpHookCtx hctx{p, scratch, pow, w.eps, w.S, w.twp};
+  const recon::StageAHook hook{mlp_hook, &hctx};
   const int n_blocks = (int)((p->D + db - 1) / db);
   for (int b = 0; b < n_blocks; ++b) {
     const int d0 = b * (int)db;
     const int cnt = (p->D - d0) < (int)db ? (p->D - d0) : (int)db;
-    cudaError_t e = recon::launch_stage_a(p->ca, w, images, d0, cnt, s);
+    cudaError_t e = recon::launch_stage_a(p->ca, w, images, d0, cnt, s, nullptr, mlp ? &hook : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "recon_run_noalloc: stage A launch");
     e = recon::launch_backproject(p->cb, w.dirs, w.stack, d0, cnt, volume, p->opt.accumulate || b > 0, s);
     if (e != cudaSuccess) return cuda_fail(e, "recon_run_noalloc: backprojection launch");
@@ -621,3 +752,149 @@ int run_in_scratch(recon_plan_t p, const float* images, float* volume, char* scr
 }
 
 }  // namespace recon
+
+// ------------------------------------------------------------------ training
+namespace {
+
+struct TrainLayout {
+  size_t S, G, T, pow, eps, acts, deps, theta, grad, m1, m2, sums, loss, total;
+};
+
+int train_plan(const recon_train_cfg* c, recon_plan_t* out) {
+  recon_geometry g{c->n_img, c->nu, c->nv, c->rot};
+  recon_grid gr{c->grid_nx, c->grid_ny, c->grid_nz};
+  recon_options o;
+  recon_default_options(&o);
+  o.sigma = c->sigma;
+  o.cs = c->cs;
+  o.nsr = c->nsr;
+  o.input_mode = c->input_mode;
+  o.dir_block = c->n_img;
+  return plan_create(&g, c->lambda, c->delta, c->defocus, c->nz_layers, &gr, &o, out, true);
+}
+
+int train_check(const recon_train_cfg* c) {
+  if (!c) return fail(RECON_E_INVALID_ARG, "recon_mlp_train: null config");
+  if (c->n_img < 1 || c->nz_layers < 1 || c->steps < 0)
+    return fail(RECON_E_INVALID_ARG, "recon_mlp_train: n_img, nz_layers >= 1 and steps >= 0 needed");
+  if (!(c->nsr > 0.0) || !std::isfinite(c->nsr)) return fail(RECON_E_INVALID_ARG, "recon_mlp_train: nsr must be > 0");
+  if (c->steps > 0 && !(c->lr > 0.f)) return fail(RECON_E_INVALID_ARG, "recon_mlp_train: lr must be > 0");
+  return RECON_OK;
+}
+
+TrainLayout train_layout(recon_plan_t p, const recon_train_cfg* c) {
+  TrainLayout L;
+  const size_t N = c->n_img, K = c->nz_layers, NB = p->lc.n_bins, half = p->half, P = p->P;
+  size_t off = p->table_bytes;
+  L.S = off;
+  off = align256(off + N * K * p->nv * half * 8);
+  L.G = off;
+  off = align256(off + N * half * P * 8);
+  L.T = off;
+  off = align256(off + N * K * half * P * 8);
+  L.pow = off;
+  off = align256(off + N * NB * 4);
+  L.eps = off;
+  off = align256(off + N * K * NB * 4);
+  L.acts = off;
+  off = align256(off + N * K * NB * recon::kActStride * 4);
+  L.deps = off;
+  off = align256(off + N * K * NB * 8);
+  L.theta = off;
+  off = align256(off + recon::kMlpParams * 4);
+  L.grad = off;
+  off = align256(off + recon::kMlpParams * 4);
+  L.m1 = off;
+  off = align256(off + recon::kMlpParams * 4);
+  L.m2 = off;
+  off = align256(off + recon::kMlpParams * 4);
+  L.sums = off;
+  off = align256(off + 2 * sizeof(double));
+  L.loss = off;
+  off = align256(off + sizeof(float) * (size_t)(c->steps > 0 ? c->steps : 1));
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+extern "C" int recon_mlp_train_workspace_size(const recon_train_cfg* cfg, size_t* bytes) {
+  int rc = train_check(cfg);
+  if (rc) return rc;
+  if (!bytes) return fail(RECON_E_INVALID_ARG, "recon_mlp_train_workspace_size: null bytes");
+  recon_plan_t p = nullptr;
+  rc = train_plan(cfg, &p);
+  if (rc) return rc;
+  *bytes = train_layout(p, cfg).total;
+  recon_destroy(p);
+  return RECON_OK;
+}
+
+extern "C" int recon_mlp_train(const recon_train_cfg* cfg, float* weights, float* loss_history, float* grad,
+                               void* workspace, size_t ws_bytes, void* stream) {
+  int rc = train_check(cfg);
+  if (rc) return rc;
+  if (!weights || !loss_history || !cfg->images || !cfg->targets)
+    return fail(RECON_E_INVALID_ARG, "recon_mlp_train: null weights, loss_history, images or targets");
+  recon_plan_t p = nullptr;
+  rc = train_plan(cfg, &p);
+  if (rc) return rc;
+  struct Guard {
+    recon_plan_t p;
+    ~Guard() { recon_destroy(p); }
+  } guard{p};
+  if (p->P < 16) return fail(RECON_E_UNSUPPORTED_SIZE, "recon_mlp_train: images of more than 4 pixels needed");
+  const TrainLayout L = train_layout(p, cfg);
+  if (!workspace || ((uintptr_t)workspace & 255) != 0 || ws_bytes < L.total)
+    return fail(RECON_E_WORKSPACE, "recon_mlp_train: workspace too small or misaligned (needs " +
+                                       std::to_string(L.total) + " bytes)");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* b = (char*)workspace;
+  const recon::Workspace w = carve(p, workspace);
+  rc = upload_tables(p, w, s);
+  if (rc) return rc;
+  const int N = cfg->n_img, K = cfg->nz_layers;
+  float2* S = (float2*)(b + L.S);
+  float2* G = (float2*)(b + L.G);
+  float2* T = (float2*)(b + L.T);
+  float* pow = (float*)(b + L.pow);
+  float* eps = (float*)(b + L.eps);
+  float* acts = (float*)(b + L.acts);
+  double* deps = (double*)(b + L.deps);
+  float* theta = (float*)(b + L.theta);
+  float* g = (float*)(b + L.grad);
+  float* m1 = (float*)(b + L.m1);
+  float* m2 = (float*)(b + L.m2);
+  double* sums = (double*)(b + L.sums);
+  float* loss = (float*)(b + L.loss);
+  const float* cnt = (const float*)(b + p->off_cnt);
+  const float* x2 = (const float*)(b + p->off_x2);
+  cudaError_t e = cudaMemcpyAsync(theta, weights, sizeof(float) * recon::kMlpParams, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(pow, 0, sizeof(float) * (size_t)N * p->lc.n_bins, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g, 0, sizeof(float) * recon::kMlpParams * 3, s);  // grad, m1, m2
+  // spectra of the images (and their radial power) and of the layer targets
+  if (e == cudaSuccess) e = recon::launch_rows_fwd(p->ca, S, w.twp, cfg->images, 0, N, s);
+  if (e == cudaSuccess) e = recon::launch_cols_forward(p->ca, p->lc, S, G, pow, w.twp, N, s);
+  recon::StageAConst ct = p->ca;
+  ct.input_mode = RECON_INPUT_CONTRAST;
+  if (e == cudaSuccess) e = recon::launch_rows_fwd(ct, S, w.twp, cfg->targets, 0, N * K, s);
+  if (e == cudaSuccess) e = recon::launch_cols_forward(ct, p->lc, S, T, nullptr, w.twp, N * K, s);
+  const int iters = cfg->steps > 0 ? cfg->steps : 1;
+  for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+    e = cudaMemsetAsync(sums, 0, 2 * sizeof(double), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(deps, 0, sizeof(double) * (size_t)N * K * p->lc.n_bins, s);
+    if (e == cudaSuccess) e = recon::launch_eps_table(p->lc, pow, cnt, x2, theta, eps, acts, N, K, 0, s);
+    if (e == cudaSuccess)
+      e = recon::launch_train_step(p->ca, p->lc, G, T, eps, w.uA, acts, theta, theta, g, m1, m2, N, sums, deps,
+                                   cfg->steps > 0 ? it + 1 : 0, cfg->lr, loss + it, s);
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(loss_history, loss, sizeof(float) * iters, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && cfg->steps > 0)
+    e = cudaMemcpyAsync(weights, theta, sizeof(float) * recon::kMlpParams, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && cfg->steps == 0 && grad)
+    e = cudaMemcpyAsync(grad, g, sizeof(float) * recon::kMlpParams, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_mlp_train");
+  return RECON_OK;
+}

@@ -37,7 +37,7 @@ struct StageAConst {
   int P, logP;          // padded FFT size and its log2
   int nu, nv;           // image size
   int nz_layers;        // Nz
-  int filter;           // RECON_FILTER_*
+  int filter;           // RECON_FILTER_* (2: eps from the learned table)
   int input_mode;       // RECON_INPUT_*
   int stack_bf16;       // 0: float32 stack, 1: bfloat16 stack
   uint64_t uC;          // Cs phase per m^2 as a fraction of 2 pi, 2^-64 units
@@ -62,13 +62,26 @@ struct Workspace {
   void* stack;          // [DB][Nz][nv+2][nu+1] tap pairs (Y[v][u-1], Y[v][u]), zero outside
   float* dens;          // [G][G][G] sampling density S (density weighting only)
   double* band_sum;     // sum of S over the band (sets eps_S)
+  float* eps;           // [DB][Nz][n_bins] learned regulariser (learned filter only)
+  int n_bins, bin_width;
 };
 
 // Kernel launchers (stage_a.cu, backproject.cu).  They return cudaGetLastError().
-// `ev`, when not null, holds two events recorded after the row FFTs and after the
-// column kernel (the caller records the ones before and after the whole stage).
+// Optional work between the row FFTs and the column kernel (the learned regulariser's
+// power spectrum and eps table).
+struct StageAHook {
+  cudaError_t (*fn)(void* ctx, int dir_begin, int dir_count, cudaStream_t stream);
+  void* ctx;
+};
+
+// `ev`, when not null, holds two events recorded after the row FFTs (and the hook) and
+// after the column kernel (the caller records the ones before and after the whole stage).
 cudaError_t launch_stage_a(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin,
-                           int dir_count, cudaStream_t stream, cudaEvent_t* ev = nullptr);
+                           int dir_count, cudaStream_t stream, cudaEvent_t* ev = nullptr,
+                           const StageAHook* hook = nullptr);
+// The row FFTs alone (S of `count` images starting at image `first`), P >= 16.
+cudaError_t launch_rows_fwd(const StageAConst& c, float2* S, const float2* twp, const float* images, int first,
+                            int count, cudaStream_t stream);
 
 struct BackprojConst {
   int nx, ny, nz;

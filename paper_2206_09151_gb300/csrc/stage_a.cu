@@ -124,8 +124,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_cols(const float2* __restrict__
                                                     const float2* __restrict__ twg, const uint64_t* __restrict__ uA,
                                                     const float* __restrict__ ramp, const DirParams* __restrict__ dirs,
                                                     const float* __restrict__ dens,
-                                                    const double* __restrict__ band_sum, StageAConst c,
-                                                    int dir_begin) {
+                                                    const double* __restrict__ band_sum,
+                                                    const float* __restrict__ eps_tab, int n_bins, int bin_width,
+                                                    StageAConst c, int dir_begin) {
   constexpr int TT = P / 8, CB = groups_per_cta<P>(), L = fft::buffer_len(P), NT = fft::pass_table_len(P);
   __shared__ float2 tw[NT];
   __shared__ float2 buf_all[CB * L];
@@ -188,11 +189,24 @@ __global__ void __launch_bounds__(kThreads, 4) k_cols(const float2* __restrict__
     const uint64_t m64 = msq[s];
     base_hi[s] = (uint32_t)((c.uC * (m64 * m64) - c.uW) >> 32);
   }
+  // learned regulariser: the radial bin of each frequency (isqrt, exact integers)
+  int bin[8];
+  if (c.filter == 2) {
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      int r = (int)sqrtf((float)msq[s]);
+      while ((uint32_t)r * (uint32_t)r > msq[s]) --r;
+      while ((uint32_t)(r + 1) * (uint32_t)(r + 1) <= msq[s]) ++r;
+      const int b = r / bin_width;
+      bin[s] = b < n_bins - 1 ? b : n_bins - 1;
+    }
+  }
   const uint64_t* uAn = uA + (size_t)(dir_begin + n) * c.nz_layers;
   float2* Tn = T + (size_t)n * c.nz_layers * c.half * c.nv;
   for (int k = 0; k < c.nz_layers; ++k) {
     const uint64_t uAk = uAn[k];
     const uint32_t a_hi = (uint32_t)(uAk >> 32), a_lo = (uint32_t)uAk;
+    const float* eps_k = eps_tab + ((size_t)n * c.nz_layers + k) * n_bins;
     float2 x[8];
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
@@ -200,7 +214,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_cols(const float2* __restrict__
       if (c.filter) {
         const uint32_t hi = a_hi * msq[s] + __umulhi(a_lo, msq[s]) + base_hi[s];
         const float sn = sin_half_turns((int32_t)hi);
-        f *= c.pref * __fdividef(sn, fmaf(sn, sn, c.eps));  // real part of the Eq. 11 bracket
+        const float e = c.filter == 2 ? __ldg(eps_k + bin[s]) : c.eps;  // learned or Tikhonov eps
+        f *= c.pref * __fdividef(sn, fmaf(sn, sn, e));  // real part of the Eq. 11 bracket
       }
       x[s] = make_float2(xg[s].x * f, xg[s].y * f);
     }
@@ -356,7 +371,8 @@ __global__ void k_small_rows_fwd(const float* __restrict__ images, float2* __res
 __global__ void k_small_cols(const float2* __restrict__ S, float2* __restrict__ T, const float2* __restrict__ twg,
                              const uint64_t* __restrict__ uA, const float* __restrict__ ramp,
                              const DirParams* __restrict__ dirs, const float* __restrict__ dens,
-                             const double* __restrict__ band_sum, StageAConst c, int dir_begin) {
+                             const double* __restrict__ band_sum, const float* __restrict__ eps_tab, int n_bins,
+                             int bin_width, StageAConst c, int dir_begin) {
   __shared__ float2 tw[8];
   __shared__ float2 G[8];
   __shared__ float2 Wk[8];
@@ -384,7 +400,14 @@ __global__ void k_small_cols(const float2* __restrict__ S, float2* __restrict__ 
       }
       if (c.filter) {
         const float sn = sin_from_turns(uAn[k] * msq + c.uC * (msq * msq) - c.uW);
-        f *= c.pref * __fdividef(sn, fmaf(sn, sn, c.eps));
+        float e = c.eps;
+        if (c.filter == 2) {
+          int r = 0;
+          while ((uint64_t)(r + 1) * (uint64_t)(r + 1) <= msq) ++r;
+          const int b = r / bin_width;
+          e = eps_tab[((size_t)n * c.nz_layers + k) * n_bins + (b < n_bins - 1 ? b : n_bins - 1)];
+        }
+        f *= c.pref * __fdividef(sn, fmaf(sn, sn, e));
       }
       Wk[bitrev(m, c.logP)] = make_float2(G[m].x * f, G[m].y * f);
     }
@@ -435,13 +458,18 @@ __global__ void k_small_rows_inv(const float2* __restrict__ T, PairT* __restrict
 // ------------------------------------------------------------------ launch
 template <int P>
 cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin, int dir_count,
-                       cudaStream_t stream, cudaEvent_t* ev) {
+                       cudaStream_t stream, cudaEvent_t* ev, const StageAHook* hook) {
   constexpr int G = groups_per_cta<P>();
   k_rows_fwd<P><<<dim3((c.nv + 2 * G - 1) / (2 * G), dir_count), kThreads, 0, stream>>>(images, ws.S, ws.twp, c,
                                                                                          dir_begin);
+  if (hook) {
+    const cudaError_t e = hook->fn(hook->ctx, dir_begin, dir_count, stream);
+    if (e != cudaSuccess) return e;
+  }
   if (ev) cudaEventRecord(ev[0], stream);
   k_cols<P><<<dim3((c.half + G - 1) / G, dir_count), kThreads, 0, stream>>>(
-      ws.S, ws.T, ws.twp, ws.uA, ws.ramp, ws.dirs, ws.dens, ws.band_sum, c, dir_begin);
+      ws.S, ws.T, ws.twp, ws.uA, ws.ramp, ws.dirs, ws.dens, ws.band_sum, ws.eps, ws.n_bins, ws.bin_width, c,
+      dir_begin);
   if (ev) cudaEventRecord(ev[1], stream);
   const dim3 gi((c.nv + 2 * G - 1) / (2 * G), c.nz_layers, dir_count);
   if (c.stack_bf16)
@@ -451,12 +479,21 @@ cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* i
   return cudaGetLastError();
 }
 
+template <int P>
+cudaError_t rows_fwd_only(const StageAConst& c, float2* S, const float2* twp, const float* images, int first,
+                          int count, cudaStream_t stream) {
+  constexpr int G = groups_per_cta<P>();
+  k_rows_fwd<P><<<dim3((c.nv + 2 * G - 1) / (2 * G), count), kThreads, 0, stream>>>(images, S, twp, c, first);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_small(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin,
                          int dir_count, cudaStream_t stream, cudaEvent_t* ev) {
   k_small_rows_fwd<<<dim3((c.nv + 1) / 2, dir_count), 32, 0, stream>>>(images, ws.S, ws.tw, c, dir_begin);
   if (ev) cudaEventRecord(ev[0], stream);
   k_small_cols<<<dim3(c.half, dir_count), 32, 0, stream>>>(ws.S, ws.T, ws.tw, ws.uA, ws.ramp, ws.dirs, ws.dens,
-                                                          ws.band_sum, c, dir_begin);
+                                                          ws.band_sum, ws.eps, ws.n_bins, ws.bin_width, c,
+                                                          dir_begin);
   if (ev) cudaEventRecord(ev[1], stream);
   const dim3 gi((c.nv + 1) / 2, c.nz_layers, dir_count);
   if (c.stack_bf16)
@@ -469,18 +506,34 @@ cudaError_t launch_small(const StageAConst& c, const Workspace& ws, const float*
 }  // namespace
 
 cudaError_t launch_stage_a(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin,
-                           int dir_count, cudaStream_t stream, cudaEvent_t* ev) {
+                           int dir_count, cudaStream_t stream, cudaEvent_t* ev, const StageAHook* hook) {
   if (dir_count <= 0) return cudaSuccess;
   switch (c.P) {
-    case 16: return launch_reg<16>(c, ws, images, dir_begin, dir_count, stream, ev);
-    case 32: return launch_reg<32>(c, ws, images, dir_begin, dir_count, stream, ev);
-    case 64: return launch_reg<64>(c, ws, images, dir_begin, dir_count, stream, ev);
-    case 128: return launch_reg<128>(c, ws, images, dir_begin, dir_count, stream, ev);
-    case 256: return launch_reg<256>(c, ws, images, dir_begin, dir_count, stream, ev);
-    case 512: return launch_reg<512>(c, ws, images, dir_begin, dir_count, stream, ev);
-    case 1024: return launch_reg<1024>(c, ws, images, dir_begin, dir_count, stream, ev);
-    case 2048: return launch_reg<2048>(c, ws, images, dir_begin, dir_count, stream, ev);
-    default: return launch_small(c, ws, images, dir_begin, dir_count, stream, ev);
+    case 16: return launch_reg<16>(c, ws, images, dir_begin, dir_count, stream, ev, hook);
+    case 32: return launch_reg<32>(c, ws, images, dir_begin, dir_count, stream, ev, hook);
+    case 64: return launch_reg<64>(c, ws, images, dir_begin, dir_count, stream, ev, hook);
+    case 128: return launch_reg<128>(c, ws, images, dir_begin, dir_count, stream, ev, hook);
+    case 256: return launch_reg<256>(c, ws, images, dir_begin, dir_count, stream, ev, hook);
+    case 512: return launch_reg<512>(c, ws, images, dir_begin, dir_count, stream, ev, hook);
+    case 1024: return launch_reg<1024>(c, ws, images, dir_begin, dir_count, stream, ev, hook);
+    case 2048: return launch_reg<2048>(c, ws, images, dir_begin, dir_count, stream, ev, hook);
+    default: return hook ? cudaErrorInvalidValue : launch_small(c, ws, images, dir_begin, dir_count, stream, ev);
+  }
+}
+
+cudaError_t launch_rows_fwd(const StageAConst& c, float2* S, const float2* twp, const float* images, int first,
+                            int count, cudaStream_t stream) {
+  if (count <= 0) return cudaSuccess;
+  switch (c.P) {
+    case 16: return rows_fwd_only<16>(c, S, twp, images, first, count, stream);
+    case 32: return rows_fwd_only<32>(c, S, twp, images, first, count, stream);
+    case 64: return rows_fwd_only<64>(c, S, twp, images, first, count, stream);
+    case 128: return rows_fwd_only<128>(c, S, twp, images, first, count, stream);
+    case 256: return rows_fwd_only<256>(c, S, twp, images, first, count, stream);
+    case 512: return rows_fwd_only<512>(c, S, twp, images, first, count, stream);
+    case 1024: return rows_fwd_only<1024>(c, S, twp, images, first, count, stream);
+    case 2048: return rows_fwd_only<2048>(c, S, twp, images, first, count, stream);
+    default: return cudaErrorInvalidValue;
   }
 }
 

@@ -2,12 +2,14 @@
 the computation is ``librecon.so``'s kernels (``recon_run`` and the stage entry points)."""
 from __future__ import annotations
 
+import ctypes
+
 import numpy as np
 import torch
 
 from . import _abi
 
-_FILTERS = {"off": _abi.RECON_FILTER_OFF, "tikhonov": _abi.RECON_FILTER_TIKHONOV}
+_FILTERS = {"off": _abi.RECON_FILTER_OFF, "tikhonov": _abi.RECON_FILTER_TIKHONOV, "mlp": _abi.RECON_FILTER_MLP}
 _INPUTS = {"intensity": _abi.RECON_INPUT_INTENSITY, "contrast": _abi.RECON_INPUT_CONTRAST}
 _STACKS = {"f32": _abi.RECON_STACK_F32, "bf16": _abi.RECON_STACK_BF16}
 _RAMPS = {"single_axis": _abi.RECON_RAMP_SINGLE_AXIS, "density": _abi.RECON_RAMP_DENSITY}
@@ -23,12 +25,18 @@ class Reconstructor:
     def __init__(self, rot, nu: int, nv: int, grid, *, lam: float, delta: float, defocus, nz_layers: int,
                  sigma: float = 0.0, eps: float = 0.1, cs: float = 0.0, filter: str = "tikhonov",
                  input_mode: str = "intensity", stack_dtype: str = "f32", accumulate: bool = False,
-                 dir_block: int = 0, ramp: str = "single_axis", device=None, allocate: bool = True):
+                 dir_block: int = 0, ramp: str = "single_axis", mlp_weights=None, nsr: float = 0.0,
+                 device=None, allocate: bool = True):
         o = _abi.recon_default_options()
         o.sigma, o.eps, o.cs = float(sigma), float(eps), float(cs)
         o.filter, o.input_mode, o.stack_dtype = _FILTERS[filter], _INPUTS[input_mode], _STACKS[stack_dtype]
         o.accumulate, o.dir_block = int(bool(accumulate)), int(dir_block)
         o.ramp_mode = _RAMPS[ramp]
+        o.nsr = float(nsr)
+        self._weights = None
+        if mlp_weights is not None:
+            self._weights = np.ascontiguousarray(mlp_weights, dtype=np.float32)
+            o.mlp_weights = self._weights.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         self.rot = np.ascontiguousarray(rot, np.float64).reshape(-1, 3, 3)
         self.D = self.rot.shape[0]
         self.nu, self.nv, self.grid, self.nz_layers = nu, nv, tuple(grid), nz_layers
@@ -104,3 +112,22 @@ class Reconstructor:
             self.close()
         except Exception:
             pass
+
+
+def train_mlp(weights, images: torch.Tensor, targets: torch.Tensor, rot, defocus, grid, *, nz_layers: int,
+              lam: float, delta: float, sigma: float, nsr: float, cs: float = 0.0, input_mode: str = "intensity",
+              steps: int = 200, lr: float = 1e-3, want_grad: bool = False, stream=None):
+    """``recon_mlp_train``: fits the regulariser network on the GPU.  ``images`` (N, nv, nu)
+    and ``targets`` (N, Nz, nv, nu) are contiguous float32 CUDA tensors.  Returns
+    (weights, loss history, gradient at the input weights when steps == 0 and want_grad)."""
+    N, nv, nu = images.shape
+    if tuple(targets.shape) != (N, nz_layers, nv, nu):
+        raise ValueError("targets must be (N, nz_layers, nv, nu)")
+    cfg, keep = _abi.make_train_cfg(rot, defocus, nu, nv, nz_layers, grid, lam, delta, sigma, cs, nsr,
+                                    _INPUTS[input_mode], images.data_ptr(), targets.data_ptr(), steps, lr)
+    ws_bytes = _abi.recon_mlp_train_workspace_size(cfg)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=images.device)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = _abi.recon_mlp_train(cfg, weights, ws.data_ptr(), ws_bytes, int(s.cuda_stream), want_grad)
+    del keep
+    return out

@@ -113,3 +113,25 @@ def test_null_arguments_are_errors_not_crashes(lib):
 def test_error_strings(lib):
     for c in (0, -1, -2, -3, -4, -5):
         assert _abi.recon_error_string(c)
+
+
+def test_training_config_is_validated_on_the_host(lib):
+    rot = ph.single_axis_rotations(2)
+    cfg, keep = _abi.make_train_cfg(rot, np.zeros(2), 16, 16, 2, (8, 8, 8), 1e-10, 1e-9, 0.1, 0.0, 0.0, 0, 16, 16,
+                                    10, 1e-3)
+    with pytest.raises(_abi.ReconError) as e:
+        _abi.recon_mlp_train_workspace_size(cfg)  # nsr = 0
+    assert e.value.code == _abi.RECON_E_INVALID_ARG
+    cfg.nsr = 1e-2
+    assert _abi.recon_mlp_train_workspace_size(cfg) > 0
+    cfg.steps = -1
+    with pytest.raises(_abi.ReconError):
+        _abi.recon_mlp_train_workspace_size(cfg)
+    del keep
+
+
+def test_learned_filter_needs_weights_and_nsr(lib):
+    o = _abi.recon_default_options()
+    o.filter = _abi.RECON_FILTER_MLP
+    with pytest.raises(_abi.ReconError):
+        _plan(opts=o)
