@@ -146,12 +146,16 @@ def make_images(cfg, device):
                                 dtype=torch.float32)
 
 
-def oracle_sample(cfg, images_np, dirs):
-    """FP64 oracle on the directions ``dirs`` alone (a D = len(dirs) scan), full volume."""
+def oracle_sample(cfg, images_np, dirs, mlp=None):
+    """FP64 oracle on the directions ``dirs`` alone (a D = len(dirs) scan), full volume;
+    ``mlp`` = (weights, nsr) selects the learned regulariser."""
     import oracle as O
-    return O.recon(images_np[dirs], cfg["rot"][dirs], lam=cfg["lam"], delta=cfg["delta"],
-                   defocus=cfg["defocus"][dirs], nz_layers=cfg["nz_layers"], grid=cfg["grid"], sigma=cfg["sigma"],
-                   eps=cfg["eps"], cs=cfg["cs"])
+    kw = dict(lam=cfg["lam"], delta=cfg["delta"], defocus=cfg["defocus"][dirs], nz_layers=cfg["nz_layers"],
+              grid=cfg["grid"], sigma=cfg["sigma"], cs=cfg["cs"])
+    if mlp is not None:
+        return O.learned.recon_learned(images_np[dirs], cfg["rot"][dirs], mlp[0].astype(np.float64), nsr=mlp[1],
+                                       **kw)
+    return O.recon(images_np[dirs], cfg["rot"][dirs], eps=cfg["eps"], **kw)
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -238,9 +242,15 @@ def run_ours(args):
     V = int(np.prod(cfg["grid"]))
     D = cfg["n_dir"]
     U = V * D
+    filt_kw = {}
+    mlp = None
+    if args.filter == "mlp":
+        from paper_2206_09151_gb300 import phantoms as ph
+        mlp = (ph.mlp_init(17).astype(np.float32), float(cfg["photons"]) ** -0.5)
+        filt_kw = dict(filter="mlp", mlp_weights=mlp[0], nsr=mlp[1])
     r = Reconstructor(cfg["rot"], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
                       defocus=cfg["defocus"], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"], eps=cfg["eps"],
-                      cs=cfg["cs"], stack_dtype=args.stack, dir_block=args.dir_block, device=dev)
+                      cs=cfg["cs"], stack_dtype=args.stack, dir_block=args.dir_block, device=dev, **filt_kw)
     vol = r.new_volume()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -337,13 +347,13 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.stack, "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload] + (f" [first {D} directions only]" if args.dirs else ""),
-                       "stack": args.stack, "dir_block": db,
+                       "stack": args.stack, "filter": args.filter, "dir_block": db,
                        "blocks": nb, "padded_fft": r.padded, "updates_per_step": U,
                        "l2": "flushed between timed steps (256 MiB write outside the timed span)",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": images.numel() * 4,
                     "d2h_bytes_per_step": vol.numel() * 4},
-            "gpu_launches": sum(kern_n), "roofline": roofline, "kernels": kernels, "clocks": clocks}
+            "gpu_launches": sum(kern_n) + (2 * nb * args.steps if args.filter == "mlp" else 0), "roofline": roofline, "kernels": kernels, "clocks": clocks}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle on a bounded sample (a few directions, full volume), beside the same
@@ -351,11 +361,11 @@ def run_ours(args):
         sel = [int(x) for x in np.linspace(0, D - 1, args.cpu_dirs).round()]
         img_np = images.cpu().numpy()
         t0 = time.perf_counter()
-        ref = oracle_sample(cfg, img_np, sel)
+        ref = oracle_sample(cfg, img_np, sel, mlp)
         dt = time.perf_counter() - t0
         rs = Reconstructor(cfg["rot"][sel], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
                            defocus=cfg["defocus"][sel], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"],
-                           eps=cfg["eps"], cs=cfg["cs"], stack_dtype=args.stack, device=dev)
+                           eps=cfg["eps"], cs=cfg["cs"], stack_dtype=args.stack, device=dev, **filt_kw)
         got = rs.run(images[sel].contiguous()).cpu().numpy()
         rs.close()
         rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
@@ -380,6 +390,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOAD_TEXT), default="mid")
     ap.add_argument("--stack", choices=["f32", "bf16"], default="f32")
+    ap.add_argument("--filter", choices=["tikhonov", "mlp"], default="tikhonov",
+                    help="mlp: the learned regulariser (seeded untrained weights; speed and parity)")
     ap.add_argument("--dir-block", type=int, default=0)
     ap.add_argument("--dirs", type=int, default=None, help="first N directions only (small profiling cases)")
     ap.add_argument("--cpu-dirs", type=int, default=3)

@@ -152,6 +152,32 @@ int recon_filter_stage(recon_plan_t plan, const float* images, int dir_begin, in
 int recon_backproject(recon_plan_t plan, const void* stack, int dir_begin, int dir_count, float* volume,
                       int accumulate, void* workspace, size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------- batches
+ * Many tomograms of uneven sizes (each with its own plan: grid, images, directions,
+ * layers, filter) reconstructed together.  Directions are taken in rounds of
+ * `dir_block` (0 = 32) per tomogram: in each round every tomogram's stage A writes its
+ * layer stacks, then ONE persistent backprojection kernel takes (tomogram, voxel tile)
+ * items from an atomic counter until all are done.  The workspace holds every plan's
+ * tables, one stack slot per tomogram and shared stage-A scratch.
+ *   recon_batch_run        uploads tables and descriptors (host copies) and launches.
+ *   recon_batch_run_graph  the same launches captured once as a CUDA graph on `stream`
+ *                          (a created stream, not the legacy default) and replayed on
+ *                          later calls with the same pointers; the tables and descriptors
+ *                          stay in the workspace, which must not be reused in between.
+ * The plans must outlive the batch.  Images and volumes as in recon_run, one per plan. */
+typedef struct recon_batch_s* recon_batch_t;
+int recon_batch_create(int n, const recon_plan_t* plans, int dir_block, recon_batch_t* out);
+int recon_batch_workspace_size(recon_batch_t batch, size_t* bytes);
+int recon_batch_run(recon_batch_t batch, const float* const* images, float* const* volumes, void* workspace,
+                    size_t ws_bytes, void* stream);
+int recon_batch_run_graph(recon_batch_t batch, const float* const* images, float* const* volumes, void* workspace,
+                          size_t ws_bytes, void* stream);
+int recon_batch_destroy(recon_batch_t batch); /* NULL is a no-op */
+/* One-call form: create, run, destroy (default rounds of 32 directions). */
+int recon_run_batch_workspace_size(int n, const recon_plan_t* plans, size_t* bytes);
+int recon_run_batch(int n, const recon_plan_t* plans, const float* const* images, float* const* volumes,
+                    void* workspace, size_t ws_bytes, void* stream);
+
 /* Plan facts: padded FFT size P, directions per block, number of blocks. */
 int recon_plan_info(recon_plan_t plan, int* padded, int* dir_block, int* n_blocks);
 

@@ -91,6 +91,14 @@ def load_library(path: str = LIB_PATH):
     L.recon_mlp_train_workspace_size.argtypes = [ctypes.POINTER(ReconTrainCfg), ctypes.POINTER(sz)]
     L.recon_mlp_train.argtypes = [ctypes.POINTER(ReconTrainCfg), ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), vp, sz, vp]
+    pp = ctypes.POINTER(vp)
+    L.recon_batch_create.argtypes = [ip, pp, ip, pp]
+    L.recon_batch_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
+    L.recon_batch_run.argtypes = [vp, pp, pp, vp, sz, vp]
+    L.recon_batch_run_graph.argtypes = [vp, pp, pp, vp, sz, vp]
+    L.recon_batch_destroy.argtypes = [vp]
+    L.recon_run_batch_workspace_size.argtypes = [ip, pp, ctypes.POINTER(sz)]
+    L.recon_run_batch.argtypes = [ip, pp, pp, pp, vp, sz, vp]
     L.recon_profile_enable.argtypes = [vp, ip]
     L.recon_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ip)]
     L.recon_sync.argtypes = [vp]
@@ -101,7 +109,9 @@ def load_library(path: str = LIB_PATH):
     L.recon_last_error.restype = ctypes.c_char_p
     for name in ("recon_plan", "recon_workspace_size", "recon_run", "recon_filter_stage", "recon_backproject",
                  "recon_plan_info", "recon_sync", "recon_destroy", "recon_profile_enable", "recon_profile_read",
-                 "recon_run_noalloc", "recon_mlp_train_workspace_size", "recon_mlp_train"):
+                 "recon_run_noalloc", "recon_mlp_train_workspace_size", "recon_mlp_train", "recon_batch_create",
+                 "recon_batch_workspace_size", "recon_batch_run", "recon_batch_run_graph", "recon_batch_destroy",
+                 "recon_run_batch_workspace_size", "recon_run_batch"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -221,6 +231,49 @@ def recon_profile_read(plan) -> tuple[list[float], list[int]]:
     n = (ctypes.c_int * 4)()
     _check(load_library().recon_profile_read(plan, ms, n), "recon_profile_read")
     return list(ms), list(n)
+
+
+def _ptrs(values):
+    arr = (ctypes.c_void_p * max(len(values), 1))()
+    for i, v in enumerate(values):
+        arr[i] = v
+    return arr
+
+
+def recon_batch_create(plans, dir_block: int = 0):
+    out = ctypes.c_void_p()
+    _check(load_library().recon_batch_create(len(plans), _ptrs([p.value for p in plans]), dir_block,
+                                             ctypes.byref(out)), "recon_batch_create")
+    return out
+
+
+def recon_batch_workspace_size(batch) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().recon_batch_workspace_size(batch, ctypes.byref(n)), "recon_batch_workspace_size")
+    return n.value
+
+
+def recon_batch_run(batch, image_ptrs, volume_ptrs, ws_ptr: int, ws_bytes: int, stream: int, graph: bool = False):
+    L = load_library()
+    fn = L.recon_batch_run_graph if graph else L.recon_batch_run
+    _check(fn(batch, _ptrs(image_ptrs), _ptrs(volume_ptrs), ws_ptr, ws_bytes, stream),
+           "recon_batch_run_graph" if graph else "recon_batch_run")
+
+
+def recon_batch_destroy(batch):
+    load_library().recon_batch_destroy(batch)
+
+
+def recon_run_batch_workspace_size(plans) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().recon_run_batch_workspace_size(len(plans), _ptrs([p.value for p in plans]),
+                                                         ctypes.byref(n)), "recon_run_batch_workspace_size")
+    return n.value
+
+
+def recon_run_batch(plans, image_ptrs, volume_ptrs, ws_ptr: int, ws_bytes: int, stream: int):
+    _check(load_library().recon_run_batch(len(plans), _ptrs([p.value for p in plans]), _ptrs(image_ptrs),
+                                          _ptrs(volume_ptrs), ws_ptr, ws_bytes, stream), "recon_run_batch")
 
 
 def recon_sync(stream: int):

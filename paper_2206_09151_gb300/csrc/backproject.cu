@@ -41,13 +41,13 @@ __device__ __forceinline__ float2 stack_pair(const __nv_bfloat162* p) { return _
 constexpr float kMagic = 12582912.0f;
 constexpr int kMagicBits = 0x4B400000;
 
+// One 32 x 8 x 4 tile (tile coordinates bx, by, bz); s_dir: dir_count TileDir records.
 template <typename ST>
-__global__ void __launch_bounds__(kTX* kTY) k_backproject(const DirParams* __restrict__ dirs,
-                                                           const ST* __restrict__ stack, BackprojConst c,
-                                                           int dir_begin, int dir_count, float* __restrict__ vol,
-                                                           int accumulate) {
-  extern __shared__ TileDir s_dir[];
-  const int i0 = blockIdx.x * kTX, j0 = blockIdx.y * kTY, k0 = blockIdx.z * kTZ;
+__device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const DirParams* __restrict__ dirs,
+                                                const ST* __restrict__ stack, const BackprojConst& c,
+                                                int dir_begin, int dir_count, float* __restrict__ vol,
+                                                int accumulate, TileDir* s_dir) {
+  const int i0 = bx * kTX, j0 = by * kTY, k0 = bz * kTZ;
   const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
   for (int d = threadIdx.x; d < dir_count; d += blockDim.x) {
     const DirParams& p = dirs[dir_begin + d];
@@ -120,6 +120,16 @@ __global__ void __launch_bounds__(kTX* kTY) k_backproject(const DirParams* __res
   }
 }
 
+template <typename ST>
+__global__ void __launch_bounds__(kTX* kTY) k_backproject(const DirParams* __restrict__ dirs,
+                                                           const ST* __restrict__ stack, BackprojConst c,
+                                                           int dir_begin, int dir_count, float* __restrict__ vol,
+                                                           int accumulate) {
+  extern __shared__ TileDir s_dir[];
+  bp_generic_tile<ST>(blockIdx.x, blockIdx.y, blockIdx.z, dirs, stack, c, dir_begin, dir_count, vol, accumulate,
+                      s_dir);
+}
+
 // ---------------------------------------------------------------------------------
 // Single-axis scans about the volume y axis (rot row 1 = (0,1,0) for every view): the
 // detector row is v = j + b_off for every direction, and the u coordinate and the depth
@@ -144,13 +154,13 @@ __device__ __forceinline__ float lerp_row(const ST* p, float fa) {
   return fmaf(fa, v.y - v.x, v.x);
 }
 
+// One 32 (i) x 8 (k) x 16 (j) tile (tile coordinates bx, by = k tile, bz = j tile).
 template <typename ST, bool TWO_ROWS>
-__global__ void __launch_bounds__(kAX* kAZ) k_backproject_axis(const DirParams* __restrict__ dirs,
-                                                                const ST* __restrict__ stack, BackprojConst c,
-                                                                int dir_begin, int dir_count,
-                                                                float* __restrict__ vol, int accumulate) {
-  extern __shared__ AxisDir s_ax[];
-  const int i0 = blockIdx.x * kAX, k0 = blockIdx.y * kAZ, j0 = blockIdx.z * kJ;
+__device__ __forceinline__ void bp_axis_tile(int bx, int by, int bz, const DirParams* __restrict__ dirs,
+                                             const ST* __restrict__ stack, const BackprojConst& c, int dir_begin,
+                                             int dir_count, float* __restrict__ vol, int accumulate,
+                                             AxisDir* s_ax) {
+  const int i0 = bx * kAX, k0 = by * kAZ, j0 = bz * kJ;
   const int tx = threadIdx.x % kAX, tz = threadIdx.x / kAX;
   for (int d = threadIdx.x; d < dir_count; d += blockDim.x) {
     const DirParams& p = dirs[dir_begin + d];
@@ -229,6 +239,16 @@ __global__ void __launch_bounds__(kAX* kAZ) k_backproject_axis(const DirParams* 
 }
 
 template <typename ST, bool TWO_ROWS>
+__global__ void __launch_bounds__(kAX* kAZ) k_backproject_axis(const DirParams* __restrict__ dirs,
+                                                                const ST* __restrict__ stack, BackprojConst c,
+                                                                int dir_begin, int dir_count,
+                                                                float* __restrict__ vol, int accumulate) {
+  extern __shared__ AxisDir s_ax[];
+  bp_axis_tile<ST, TWO_ROWS>(blockIdx.x, blockIdx.y, blockIdx.z, dirs, stack, c, dir_begin, dir_count, vol,
+                             accumulate, s_ax);
+}
+
+template <typename ST, bool TWO_ROWS>
 cudaError_t launch_axis(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
                         int dir_count, float* volume, int accumulate, cudaStream_t stream) {
   dim3 grid((c.nx + kAX - 1) / kAX, (c.nz + kAZ - 1) / kAZ, (c.ny + kJ - 1) / kJ);
@@ -241,6 +261,61 @@ cudaError_t launch_axis(const BackprojConst& c, const DirParams* dirs, const voi
   k_backproject_axis<ST, TWO_ROWS><<<grid, kAX * kAZ, smem, stream>>>(dirs, (const ST*)stack, c, dir_begin,
                                                                       dir_count, volume, accumulate);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// Persistent backprojection over many tomograms: CTAs take (tomogram, tile) items from
+// one atomic counter until the items run out; each item runs the tile body of its
+// tomogram's kind.  No CTA waits on another, so the loop always ends.
+__global__ void __launch_bounds__(256) k_backproject_persistent(const BatchBp* __restrict__ desc, int n_desc,
+                                                                unsigned long long total,
+                                                                unsigned long long* __restrict__ counter) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ unsigned long long s_item;
+  __shared__ int s_p;
+  for (;;) {
+    __syncthreads();  // the previous item is done with the shared records
+    if (threadIdx.x == 0) {
+      const unsigned long long it = atomicAdd(counter, 1ull);
+      int p = 0;
+      if (it < total)
+        while (p + 1 < n_desc && desc[p + 1].first_item <= it) ++p;
+      s_item = it;
+      s_p = p;
+    }
+    __syncthreads();
+    const unsigned long long it = s_item;
+    if (it >= total) return;
+    const BatchBp& d = desc[s_p];
+    const unsigned long long t = it - d.first_item;
+    const int bx = (int)(t % d.gx), by = (int)((t / d.gx) % d.gy), bz = (int)(t / ((unsigned long long)d.gx * d.gy));
+    switch (d.kind) {
+      case 0:
+        bp_generic_tile<float2>(bx, by, bz, d.dirs, (const float2*)d.stack, d.c, d.dir_begin, d.dir_count, d.vol,
+                                d.accumulate, (TileDir*)smem_raw);
+        break;
+      case 1:
+        bp_generic_tile<__nv_bfloat162>(bx, by, bz, d.dirs, (const __nv_bfloat162*)d.stack, d.c, d.dir_begin,
+                                        d.dir_count, d.vol, d.accumulate, (TileDir*)smem_raw);
+        break;
+      case 2:
+        bp_axis_tile<float2, false>(bx, by, bz, d.dirs, (const float2*)d.stack, d.c, d.dir_begin, d.dir_count, d.vol,
+                                    d.accumulate, (AxisDir*)smem_raw);
+        break;
+      case 3:
+        bp_axis_tile<float2, true>(bx, by, bz, d.dirs, (const float2*)d.stack, d.c, d.dir_begin, d.dir_count, d.vol,
+                                   d.accumulate, (AxisDir*)smem_raw);
+        break;
+      case 4:
+        bp_axis_tile<__nv_bfloat162, false>(bx, by, bz, d.dirs, (const __nv_bfloat162*)d.stack, d.c, d.dir_begin,
+                                            d.dir_count, d.vol, d.accumulate, (AxisDir*)smem_raw);
+        break;
+      default:
+        bp_axis_tile<__nv_bfloat162, true>(bx, by, bz, d.dirs, (const __nv_bfloat162*)d.stack, d.c, d.dir_begin,
+                                           d.dir_count, d.vol, d.accumulate, (AxisDir*)smem_raw);
+        break;
+    }
+  }
 }
 
 }  // namespace
@@ -275,6 +350,49 @@ cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, co
     k_backproject<float2><<<grid, kTX * kTY, smem, stream>>>(dirs, (const float2*)stack, c, dir_begin, dir_count,
                                                               volume, accumulate);
   }
+  return cudaGetLastError();
+}
+
+void describe_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
+                          int dir_count, float* volume, int accumulate, BatchBp* out) {
+  out->c = c;
+  out->dirs = dirs;
+  out->stack = stack;
+  out->vol = volume;
+  out->dir_begin = dir_begin;
+  out->dir_count = dir_count;
+  out->accumulate = accumulate;
+  if (c.axis_y) {
+    out->kind = 2 + (c.stack_bf16 ? 2 : 0) + (c.b_frac != 0.f ? 1 : 0);
+    out->gx = (c.nx + kAX - 1) / kAX;
+    out->gy = (c.nz + kAZ - 1) / kAZ;
+    out->gz = (c.ny + kJ - 1) / kJ;
+  } else {
+    out->kind = c.stack_bf16 ? 1 : 0;
+    out->gx = (c.nx + kTX - 1) / kTX;
+    out->gy = (c.ny + kTY - 1) / kTY;
+    out->gz = (c.nz + kTZ - 1) / kTZ;
+  }
+  out->smem = (size_t)dir_count * (c.axis_y ? sizeof(AxisDir) : sizeof(TileDir));
+}
+
+cudaError_t launch_backproject_persistent(const BatchBp* desc_dev, int n_desc, unsigned long long total,
+                                          unsigned long long* counter, size_t smem, cudaStream_t stream) {
+  if (total == 0) return cudaSuccess;
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_backproject_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backproject_persistent, 256, smem);
+  if (per_sm < 1) per_sm = 1;
+  const unsigned long long ctas = (unsigned long long)sms * per_sm;
+  const unsigned grid = (unsigned)(ctas < total ? ctas : total);
+  k_backproject_persistent<<<grid, 256, smem, stream>>>(desc_dev, n_desc, total, counter);
   return cudaGetLastError();
 }
 

@@ -5,6 +5,7 @@
 // results of the written operation order (they define the layer decision).
 #include "recon.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -898,3 +899,253 @@ extern "C" int recon_mlp_train(const recon_train_cfg* cfg, float* weights, float
   if (e != cudaSuccess) return cuda_fail(e, "recon_mlp_train");
   return RECON_OK;
 }
+
+// ------------------------------------------------------------------ batches of tomograms
+struct recon_batch_s {
+  int n = 0, dbb = 0, n_rounds = 0;
+  std::vector<recon_plan_t> plans;
+  std::vector<size_t> off_tables, off_stack;
+  size_t off_S = 0, off_T = 0, off_pow = 0, off_eps = 0, off_desc = 0, off_ctr = 0, ws_bytes = 0, smem = 0;
+  std::vector<recon::BatchBp> desc;        // [n_rounds][n] (first round_count[r] used)
+  std::vector<int> round_count;
+  std::vector<unsigned long long> round_total;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<const void*> graph_ptrs;     // pointers the captured graph was built for
+  ~recon_batch_s() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+namespace {
+
+// Fills the device tables of every plan and the per-round backprojection descriptors.
+int batch_prepare(recon_batch_t bt, const float* const* images, float* const* volumes, char* base, cudaStream_t s) {
+  for (int q = 0; q < bt->n; ++q) {
+    recon_plan_t p = bt->plans[q];
+    const recon::Workspace w = carve(p, base + bt->off_tables[q]);
+    int rc = upload_tables(p, w, s);
+    if (rc) return rc;
+  }
+  for (int r = 0; r < bt->n_rounds; ++r) {
+    unsigned long long first = 0;
+    int cntr = 0;
+    for (int q = 0; q < bt->n; ++q) {
+      recon_plan_t p = bt->plans[q];
+      const int d0 = r * bt->dbb;
+      if (d0 >= p->D) continue;
+      const int cnt = (p->D - d0) < bt->dbb ? (p->D - d0) : bt->dbb;
+      recon::BatchBp& d = bt->desc[(size_t)r * bt->n + cntr];
+      const recon::Workspace w = carve(p, base + bt->off_tables[q]);
+      recon::describe_backproject(p->cb, w.dirs, base + bt->off_stack[q], d0, cnt, volumes[q],
+                                  p->opt.accumulate || r > 0, &d);
+      d.first_item = first;
+      first += (unsigned long long)d.gx * d.gy * d.gz;
+      ++cntr;
+    }
+    bt->round_count[r] = cntr;
+    bt->round_total[r] = first;
+  }
+  cudaError_t e = cudaMemcpyAsync(base + bt->off_desc, bt->desc.data(), sizeof(recon::BatchBp) * bt->desc.size(),
+                                  cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_batch: descriptor upload");
+  (void)images;
+  return RECON_OK;
+}
+
+// The kernels of one batch run (capturable: no host copies).
+int batch_launch(recon_batch_t bt, const float* const* images, float* const* volumes, char* base, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(base + bt->off_ctr, 0, sizeof(unsigned long long) * bt->n_rounds, s);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_batch: counters");
+  for (int q = 0; q < bt->n; ++q) {  // tomograms without directions: clear the volume
+    recon_plan_t p = bt->plans[q];
+    const size_t nvox = (size_t)p->nx * p->ny * p->nz;
+    if (p->D == 0 && nvox > 0 && !p->opt.accumulate) {
+      e = cudaMemsetAsync(volumes[q], 0, nvox * sizeof(float), s);
+      if (e != cudaSuccess) return cuda_fail(e, "recon_batch: clearing a volume");
+    }
+  }
+  for (int r = 0; r < bt->n_rounds; ++r) {
+    for (int q = 0; q < bt->n; ++q) {
+      recon_plan_t p = bt->plans[q];
+      const int d0 = r * bt->dbb;
+      if (d0 >= p->D) continue;
+      const int cnt = (p->D - d0) < bt->dbb ? (p->D - d0) : bt->dbb;
+      recon::Workspace w = carve(p, base + bt->off_tables[q]);
+      w.S = (float2*)(base + bt->off_S);
+      w.T = (float2*)(base + bt->off_T);
+      w.stack = base + bt->off_stack[q];
+      w.eps = (float*)(base + bt->off_eps);
+      MlpHookCtx hctx{p, base + bt->off_tables[q], (float*)(base + bt->off_pow), w.eps, w.S, w.twp};
+      const recon::StageAHook hook{mlp_hook, &hctx};
+      e = recon::launch_stage_a(p->ca, w, images[q], d0, cnt, s, nullptr,
+                                p->ca.filter == RECON_FILTER_MLP ? &hook : nullptr);
+      if (e != cudaSuccess) return cuda_fail(e, "recon_batch: stage A launch");
+    }
+    e = recon::launch_backproject_persistent((const recon::BatchBp*)(base + bt->off_desc) + (size_t)r * bt->n,
+                                             bt->round_count[r], bt->round_total[r],
+                                             (unsigned long long*)(base + bt->off_ctr) + r, bt->smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "recon_batch: persistent backprojection launch");
+  }
+  return RECON_OK;
+}
+
+int batch_args(recon_batch_t bt, const float* const* images, float* const* volumes, void* ws, size_t ws_bytes,
+               const char* who) {
+  if (!bt) return fail(RECON_E_INVALID_ARG, std::string(who) + ": null batch");
+  if (bt->n > 0 && (!images || !volumes)) return fail(RECON_E_INVALID_ARG, std::string(who) + ": null arrays");
+  for (int q = 0; q < bt->n; ++q) {
+    recon_plan_t p = bt->plans[q];
+    if ((p->D > 0 && !images[q]) || ((size_t)p->nx * p->ny * p->nz > 0 && !volumes[q]))
+      return fail(RECON_E_INVALID_ARG, std::string(who) + ": null image or volume of tomogram " + std::to_string(q));
+  }
+  if (bt->ws_bytes > 0 && (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < bt->ws_bytes))
+    return fail(RECON_E_WORKSPACE, std::string(who) + ": workspace too small or misaligned (needs " +
+                                       std::to_string(bt->ws_bytes) + " bytes)");
+  return RECON_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int recon_batch_create(int n, const recon_plan_t* plans, int dir_block, recon_batch_t* out) {
+  if (n < 0 || (n > 0 && !plans) || !out) return fail(RECON_E_INVALID_ARG, "recon_batch_create: bad arguments");
+  if (dir_block < 0 || dir_block > 1024) return fail(RECON_E_INVALID_ARG, "recon_batch_create: dir_block in [0, 1024]");
+  for (int q = 0; q < n; ++q)
+    if (!plans[q]) return fail(RECON_E_INVALID_ARG, "recon_batch_create: null plan");
+  recon_batch_s* bt = new (std::nothrow) recon_batch_s();
+  if (!bt) return fail(RECON_E_NO_MEMORY, "recon_batch_create: out of host memory");
+  bt->n = n;
+  bt->plans.assign(plans, plans + n);
+  bt->dbb = dir_block > 0 ? dir_block : 32;
+  size_t off = 0, maxS = 0, maxT = 0, maxpow = 0, maxeps = 0, smem = 0;
+  bt->off_tables.resize(n);
+  bt->off_stack.resize(n);
+  int rounds = 0;
+  for (int q = 0; q < n; ++q) {
+    recon_plan_t p = plans[q];
+    bt->off_tables[q] = off;
+    off = align256(off + p->table_bytes);
+    const size_t db = (size_t)bt->dbb;
+    maxS = std::max(maxS, db * p->nv * p->half * 8);
+    maxT = std::max(maxT, db * p->nzl * p->nv * p->half * 8);
+    maxpow = std::max(maxpow, db * p->lc.n_bins * 4);
+    maxeps = std::max(maxeps, db * p->nzl * p->lc.n_bins * 4);
+    smem = std::max(smem, db * 64);
+    rounds = std::max(rounds, (p->D + bt->dbb - 1) / bt->dbb);
+  }
+  for (int q = 0; q < n; ++q) {
+    bt->off_stack[q] = off;
+    off = align256(off + (size_t)bt->dbb * plans[q]->stack_dir_bytes);
+  }
+  bt->off_S = off;
+  off = align256(off + maxS);
+  bt->off_T = off;
+  off = align256(off + maxT);
+  bt->off_pow = off;
+  off = align256(off + maxpow);
+  bt->off_eps = off;
+  off = align256(off + maxeps);
+  bt->n_rounds = rounds;
+  bt->off_desc = off;
+  off = align256(off + sizeof(recon::BatchBp) * (size_t)rounds * n);
+  bt->off_ctr = off;
+  off = align256(off + sizeof(unsigned long long) * (size_t)(rounds > 0 ? rounds : 1));
+  bt->ws_bytes = off;
+  bt->smem = smem;
+  bt->desc.assign((size_t)rounds * n, recon::BatchBp{});
+  bt->round_count.assign(rounds, 0);
+  bt->round_total.assign(rounds, 0);
+  *out = bt;
+  return RECON_OK;
+}
+
+int recon_batch_workspace_size(recon_batch_t bt, size_t* bytes) {
+  if (!bt || !bytes) return fail(RECON_E_INVALID_ARG, "recon_batch_workspace_size: null argument");
+  *bytes = bt->ws_bytes;
+  return RECON_OK;
+}
+
+int recon_batch_run(recon_batch_t bt, const float* const* images, float* const* volumes, void* ws, size_t ws_bytes,
+                    void* stream) {
+  int rc = batch_args(bt, images, volumes, ws, ws_bytes, "recon_batch_run");
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  rc = batch_prepare(bt, images, volumes, (char*)ws, s);
+  if (rc) return rc;
+  return batch_launch(bt, images, volumes, (char*)ws, s);
+}
+
+int recon_batch_run_graph(recon_batch_t bt, const float* const* images, float* const* volumes, void* ws,
+                          size_t ws_bytes, void* stream) {
+  int rc = batch_args(bt, images, volumes, ws, ws_bytes, "recon_batch_run_graph");
+  if (rc) return rc;
+  if (!stream) return fail(RECON_E_INVALID_ARG, "recon_batch_run_graph: needs a created (non-default) stream");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<const void*> ptrs;
+  ptrs.push_back(ws);
+  for (int q = 0; q < bt->n; ++q) {
+    ptrs.push_back(images[q]);
+    ptrs.push_back(volumes[q]);
+  }
+  if (!bt->gexec || ptrs != bt->graph_ptrs) {
+    if (bt->gexec) {
+      cudaGraphExecDestroy(bt->gexec);
+      bt->gexec = nullptr;
+    }
+    if (bt->graph) {
+      cudaGraphDestroy(bt->graph);
+      bt->graph = nullptr;
+    }
+    rc = batch_prepare(bt, images, volumes, (char*)ws, s);  // host copies stay outside the graph
+    if (rc) return rc;
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "recon_batch_run_graph: begin capture");
+    rc = batch_launch(bt, images, volumes, (char*)ws, s);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    if (rc) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "recon_batch_run_graph: end capture");
+    e = cudaGraphInstantiate(&bt->gexec, g, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return cuda_fail(e, "recon_batch_run_graph: instantiate");
+    }
+    bt->graph = g;
+    bt->graph_ptrs = ptrs;
+  }
+  cudaError_t e = cudaGraphLaunch(bt->gexec, s);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_batch_run_graph: launch");
+  return RECON_OK;
+}
+
+int recon_batch_destroy(recon_batch_t bt) {
+  delete bt;
+  return RECON_OK;
+}
+
+int recon_run_batch_workspace_size(int n, const recon_plan_t* plans, size_t* bytes) {
+  recon_batch_t bt = nullptr;
+  int rc = recon_batch_create(n, plans, 0, &bt);
+  if (rc) return rc;
+  rc = recon_batch_workspace_size(bt, bytes);
+  recon_batch_destroy(bt);
+  return rc;
+}
+
+int recon_run_batch(int n, const recon_plan_t* plans, const float* const* images, float* const* volumes,
+                    void* workspace, size_t ws_bytes, void* stream) {
+  recon_batch_t bt = nullptr;
+  int rc = recon_batch_create(n, plans, 0, &bt);
+  if (rc) return rc;
+  rc = recon_batch_run(bt, images, volumes, workspace, ws_bytes, stream);
+  recon_batch_destroy(bt);
+  return rc;
+}
+
+}  // extern "C"

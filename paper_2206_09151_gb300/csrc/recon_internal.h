@@ -100,6 +100,24 @@ struct BackprojConst {
 cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
                                int dir_count, float* volume, int accumulate, cudaStream_t stream);
 
+// One tomogram's share of a persistent batched backprojection: its constants, pointers,
+// kernel kind (general / single-axis, float32 / bfloat16 stack, one or two detector rows),
+// tile grid and the index of its first work item.
+struct BatchBp {
+  BackprojConst c;
+  const DirParams* dirs;
+  const void* stack;
+  float* vol;
+  int dir_begin, dir_count, accumulate, kind;
+  int gx, gy, gz;
+  unsigned long long first_item;
+  size_t smem;  // shared bytes its tiles need
+};
+void describe_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
+                          int dir_count, float* volume, int accumulate, BatchBp* out);
+cudaError_t launch_backproject_persistent(const BatchBp* desc_dev, int n_desc, unsigned long long total,
+                                          unsigned long long* counter, size_t smem, cudaStream_t stream);
+
 // Whole-operator run with its workspace carved from `scratch` (tables first, then
 // the largest direction block that fits); used by recon_run_noalloc.
 int run_in_scratch(struct ::recon_plan_s* plan, const float* images, float* volume, char* scratch,

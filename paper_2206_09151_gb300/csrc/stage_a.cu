@@ -119,8 +119,11 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(const float* __restrict__
   }
 }
 
-template <int P>
-__global__ void __launch_bounds__(kThreads, 4) k_cols(const float2* __restrict__ S, float2* __restrict__ T,
+// FILT: 0 ramp only (filter off), 1 Tikhonov eps, 2 learned eps table; DENS: density
+// weighting (any geometry) instead of the ramp.  Compile-time, so that each variant keeps
+// only the registers it uses.
+template <int P, int FILT, bool DENS>
+__global__ void __launch_bounds__(kThreads, (FILT == 2 || DENS) ? 3 : 4) k_cols(const float2* __restrict__ S, float2* __restrict__ T,
                                                     const float2* __restrict__ twg, const uint64_t* __restrict__ uA,
                                                     const float* __restrict__ ramp, const DirParams* __restrict__ dirs,
                                                     const float* __restrict__ dens,
@@ -154,8 +157,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_cols(const float2* __restrict__
   const bool ok = col < c.half;
   const int colc = ok ? col : c.half - 1;
   // ramp (single-axis scans) or sampling-density weight (any geometry), 1/P^2 included
-  float wgt[8];
-  if (c.dens.enabled) {
+  float wgt[DENS ? 8 : 1];
+  if constexpr (DENS) {
     const DirParams& dp = dirs[dir_begin + n];
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
@@ -172,9 +175,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_cols(const float2* __restrict__
       wgt[s] = wv;
     }
   } else {
-    const float w = ramp[colc];
-#pragma unroll
-    for (int s = 0; s < 8; ++s) wgt[s] = w;
+    wgt[0] = ramp[colc];
   }
   // chi/(2 pi) in 2^-32 turns needs only the top 32 bits of the 64-bit fixed-point
   // sum: the per-layer product uA_k * m is formed as hi(uA) * m + umulhi(lo(uA), m), and
@@ -190,8 +191,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_cols(const float2* __restrict__
     base_hi[s] = (uint32_t)((c.uC * (m64 * m64) - c.uW) >> 32);
   }
   // learned regulariser: the radial bin of each frequency (isqrt, exact integers)
-  int bin[8];
-  if (c.filter == 2) {
+  int bin[FILT == 2 ? 8 : 1];
+  if constexpr (FILT == 2) {
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       int r = (int)sqrtf((float)msq[s]);
@@ -210,12 +211,14 @@ __global__ void __launch_bounds__(kThreads, 4) k_cols(const float2* __restrict__
     float2 x[8];
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
-      float f = wgt[s];
-      if (c.filter) {
+      float f = wgt[DENS ? s : 0];
+      if constexpr (FILT != 0) {
         const uint32_t hi = a_hi * msq[s] + __umulhi(a_lo, msq[s]) + base_hi[s];
         const float sn = sin_half_turns((int32_t)hi);
-        const float e = c.filter == 2 ? __ldg(eps_k + bin[s]) : c.eps;  // learned or Tikhonov eps
-        f *= c.pref * __fdividef(sn, fmaf(sn, sn, e));  // real part of the Eq. 11 bracket
+        float e;
+        if constexpr (FILT == 2) e = __ldg(eps_k + bin[s]);  // learned eps
+        else e = c.eps;                                      // Tikhonov eps
+        f *= c.pref * __fdividef(sn, fmaf(sn, sn, e));       // real part of the Eq. 11 bracket
       }
       x[s] = make_float2(xg[s].x * f, xg[s].y * f);
     }
@@ -467,9 +470,19 @@ cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* i
     if (e != cudaSuccess) return e;
   }
   if (ev) cudaEventRecord(ev[0], stream);
-  k_cols<P><<<dim3((c.half + G - 1) / G, dir_count), kThreads, 0, stream>>>(
-      ws.S, ws.T, ws.twp, ws.uA, ws.ramp, ws.dirs, ws.dens, ws.band_sum, ws.eps, ws.n_bins, ws.bin_width, c,
-      dir_begin);
+  const dim3 gc((c.half + G - 1) / G, dir_count);
+#define RECON_K_COLS(F, D)                                                                                      \
+  k_cols<P, F, D><<<gc, kThreads, 0, stream>>>(ws.S, ws.T, ws.twp, ws.uA, ws.ramp, ws.dirs, ws.dens, ws.band_sum, \
+                                               ws.eps, ws.n_bins, ws.bin_width, c, dir_begin)
+  const bool dens = c.dens.enabled != 0;
+  if (c.filter == 0) {
+    if (dens) RECON_K_COLS(0, true); else RECON_K_COLS(0, false);
+  } else if (c.filter == 2) {
+    if (dens) RECON_K_COLS(2, true); else RECON_K_COLS(2, false);
+  } else {
+    if (dens) RECON_K_COLS(1, true); else RECON_K_COLS(1, false);
+  }
+#undef RECON_K_COLS
   if (ev) cudaEventRecord(ev[1], stream);
   const dim3 gi((c.nv + 2 * G - 1) / (2 * G), c.nz_layers, dir_count);
   if (c.stack_bf16)

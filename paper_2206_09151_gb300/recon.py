@@ -131,3 +131,47 @@ def train_mlp(weights, images: torch.Tensor, targets: torch.Tensor, rot, defocus
     out = _abi.recon_mlp_train(cfg, weights, ws.data_ptr(), ws_bytes, int(s.cuda_stream), want_grad)
     del keep
     return out
+
+
+class Batch:
+    """``recon_batch_*``: several :class:`Reconstructor` plans (uneven sizes) run together,
+    stage A per tomogram and one persistent backprojection per round of ``dir_block``
+    directions; ``run(..., graph=True)`` captures the launches once as a CUDA graph and
+    replays it."""
+
+    def __init__(self, recons, dir_block: int = 0, device=None):
+        self.recons = list(recons)
+        self.batch = _abi.recon_batch_create([r.plan for r in self.recons], dir_block)
+        self.ws_bytes = _abi.recon_batch_workspace_size(self.batch)
+        dev = device if device is not None else self.recons[0].device if self.recons else None
+        self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        self.stream = None
+
+    def run(self, images, volumes=None, graph: bool = False, stream=None):
+        if volumes is None:
+            volumes = [r.new_volume() for r in self.recons]
+        for r, im in zip(self.recons, images):
+            r._check_images(im)
+        if graph:
+            if stream is None:
+                if self.stream is None:
+                    self.stream = torch.cuda.Stream()
+                stream = self.stream
+            stream.wait_stream(torch.cuda.current_stream())
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _abi.recon_batch_run(self.batch, [im.data_ptr() for im in images], [v.data_ptr() for v in volumes],
+                             self.workspace.data_ptr(), self.ws_bytes, int(s.cuda_stream), graph)
+        if graph:
+            torch.cuda.current_stream().wait_stream(stream)
+        return volumes
+
+    def close(self):
+        if getattr(self, "batch", None) is not None:
+            _abi.recon_batch_destroy(self.batch)
+            self.batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
