@@ -194,6 +194,25 @@ def run_reference(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- replicas
+def max_over_ranks(value: float, device=None) -> float:
+    """The largest ``value`` over the ranks of the default process group (the slowest
+    replica's time); the value itself without a group."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_step: float, steps: int, world: int, total_ms_max: float) -> float:
+    """Whole-job throughput of ``world`` independent replicas, each doing ``units_per_step``
+    per step, timed by the slowest one."""
+    return world * units_per_step * steps / (total_ms_max / 1e3)
+
+
 # ----------------------------------------------------------------------------- our arm
 KERNELS = ["k_rows_fwd", "k_cols", "k_rows_inv", "k_backproject"]
 
@@ -250,7 +269,8 @@ def run_ours(args):
         filt_kw = dict(filter="mlp", mlp_weights=mlp[0], nsr=mlp[1])
     r = Reconstructor(cfg["rot"], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
                       defocus=cfg["defocus"], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"], eps=cfg["eps"],
-                      cs=cfg["cs"], stack_dtype=args.stack, dir_block=args.dir_block, device=dev, **filt_kw)
+                      cs=cfg["cs"], stack_dtype=args.stack, dir_block=args.dir_block, stage_block=args.stage_block,
+                      device=dev, **filt_kw)
     vol = r.new_volume()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -287,13 +307,9 @@ def run_ours(args):
         dist.barrier()
     clocks = sampler.stop()
     _abi.recon_profile_enable(r.plan, False)
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dev)
     ms_per_step = total_ms / args.steps
-    value = world * U * args.steps / (total_ms / 1e3)
+    value = aggregate_rate(U, args.steps, world, total_ms)
 
     # end to end through the public API: pinned host images in, volume out, every step
     host_img = images.cpu().pin_memory()
@@ -312,12 +328,8 @@ def run_ours(args):
         e1.synchronize()
         if s >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * U * args.steps / (e2e_total / 1e3)
+    e2e_total = max_over_ranks(sum(e2e_ms), dev)
+    e2e_value = aggregate_rate(U, args.steps, world, e2e_total)
 
     # roofline of the dominant kernel
     peaks, peak_src = load_peaks()
@@ -332,7 +344,8 @@ def run_ours(args):
                          "share": kern_ms[q] / max(sum(kern_ms), 1e-12), "algorithmic_GBps": gbs}
     dom = max(range(4), key=lambda q: kern_ms[q])
     dom_name = KERNELS[dom]
-    achieved = algo[dom] / nb / (kern_ms[dom] / max(kern_n[dom], 1) / 1e3) / 1e9
+    # bytes of all launches over their summed time (a launch is a block or a sub-block)
+    achieved = algo[dom] * args.steps / (kern_ms[dom] / 1e3) / 1e9
     src = "backproject.cu" if dom == 3 else "stage_a.cu"
     key = (dom_name, args.workload, args.stack)
     tr = NCU_TRAFFIC.get(key)
@@ -340,20 +353,22 @@ def run_ours(args):
     roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else
-                "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": algo[dom] / nb,
-                "units_per_launch": V * db if dom == 3 else db}
+                "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": algo[dom] * args.steps / max(kern_n[dom], 1),
+                "launches": kern_n[dom], "ms_per_launch": kern_ms[dom] / max(kern_n[dom], 1),
+                "units_per_launch": (V * D if dom == 3 else D) * args.steps / max(kern_n[dom], 1)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.stack, "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload] + (f" [first {D} directions only]" if args.dirs else ""),
                        "stack": args.stack, "filter": args.filter, "dir_block": db,
+                       "stage_block": r.stage_block,
                        "blocks": nb, "padded_fft": r.padded, "updates_per_step": U,
                        "l2": "flushed between timed steps (256 MiB write outside the timed span)",
                        "parallelism": f"replicas x{world}"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": images.numel() * 4,
                     "d2h_bytes_per_step": vol.numel() * 4},
-            "gpu_launches": sum(kern_n) + (2 * nb * args.steps if args.filter == "mlp" else 0), "roofline": roofline, "kernels": kernels, "clocks": clocks}
+            "gpu_launches": sum(kern_n) + (2 * kern_n[0] if args.filter == "mlp" else 0), "roofline": roofline, "kernels": kernels, "clocks": clocks}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle on a bounded sample (a few directions, full volume), beside the same
@@ -393,6 +408,7 @@ def main():
     ap.add_argument("--filter", choices=["tikhonov", "mlp"], default="tikhonov",
                     help="mlp: the learned regulariser (seeded untrained weights; speed and parity)")
     ap.add_argument("--dir-block", type=int, default=0)
+    ap.add_argument("--stage-block", type=int, default=0, help="directions per FFT/filter sub-block, 0 = auto")
     ap.add_argument("--dirs", type=int, default=None, help="first N directions only (small profiling cases)")
     ap.add_argument("--cpu-dirs", type=int, default=3)
     ap.add_argument("--ref-dirs", type=int, default=1)

@@ -105,6 +105,8 @@ typedef struct {
   const float* mlp_weights; /* host [RECON_MLP_PARAMS], copied; needed by RECON_FILTER_MLP  */
   double nsr;      /* noise-to-signal ratio of one image pixel (the NSR of Sec. 3); sets
                       the Poisson floor (nsr M)^2 per DFT coefficient of the SNR feature   */
+  int stage_block; /* directions per FFT/filter sub-block (their spectra and per-layer
+                      intermediates sized for it), 0 = the whole direction block           */
 } recon_options;
 
 /* Fills *opts with defaults: sigma 0, eps 0.1 (the value of Sec. 3), cs 0, Tikhonov
@@ -178,8 +180,9 @@ int recon_run_batch_workspace_size(int n, const recon_plan_t* plans, size_t* byt
 int recon_run_batch(int n, const recon_plan_t* plans, const float* const* images, float* const* volumes,
                     void* workspace, size_t ws_bytes, void* stream);
 
-/* Plan facts: padded FFT size P, directions per block, number of blocks. */
-int recon_plan_info(recon_plan_t plan, int* padded, int* dir_block, int* n_blocks);
+/* Plan facts: padded FFT size P, directions per block, number of blocks, directions per
+ * FFT/filter sub-block (any pointer may be NULL). */
+int recon_plan_info(recon_plan_t plan, int* padded, int* dir_block, int* n_blocks, int* stage_block);
 
 /* The learned regulariser (RECON_FILTER_MLP).  eps of Eq. 11 (chosen "ad hoc" in
  * Sec. 3) becomes eps_theta = softplus(network(x)) per (direction, layer, radial bin b),

@@ -46,7 +46,8 @@ class ReconOptions(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("eps", ctypes.c_double), ("cs", ctypes.c_double),
                 ("filter", ctypes.c_int), ("input_mode", ctypes.c_int), ("stack_dtype", ctypes.c_int),
                 ("ramp_mode", ctypes.c_int), ("accumulate", ctypes.c_int), ("dir_block", ctypes.c_int),
-                ("mlp_weights", ctypes.POINTER(ctypes.c_float)), ("nsr", ctypes.c_double)]
+                ("mlp_weights", ctypes.POINTER(ctypes.c_float)), ("nsr", ctypes.c_double),
+                ("stage_block", ctypes.c_int)]
 
 
 class ReconTrainCfg(ctypes.Structure):
@@ -86,7 +87,7 @@ def load_library(path: str = LIB_PATH):
     L.recon_run.argtypes = [vp, vp, vp, vp, sz, vp]
     L.recon_filter_stage.argtypes = [vp, vp, ip, ip, vp, sz, vp, ctypes.POINTER(vp)]
     L.recon_backproject.argtypes = [vp, vp, ip, ip, vp, ip, vp, sz, vp]
-    L.recon_plan_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]
+    L.recon_plan_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.recon_run_noalloc.argtypes = [vp, vp, vp, vp]
     L.recon_mlp_train_workspace_size.argtypes = [ctypes.POINTER(ReconTrainCfg), ctypes.POINTER(sz)]
     L.recon_mlp_train.argtypes = [ctypes.POINTER(ReconTrainCfg), ctypes.POINTER(ctypes.c_float),
@@ -190,11 +191,12 @@ def recon_workspace_size(plan) -> int:
     return n.value
 
 
-def recon_plan_info(plan) -> tuple[int, int, int]:
-    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-    _check(load_library().recon_plan_info(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+def recon_plan_info(plan) -> tuple[int, int, int, int]:
+    """(padded FFT size, directions per block, blocks, directions per FFT/filter sub-block)"""
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load_library().recon_plan_info(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
            "recon_plan_info")
-    return a.value, b.value, c.value
+    return a.value, b.value, c.value, d.value
 
 
 def recon_run(plan, images_ptr: int, volume_ptr: int, ws_ptr: int, ws_bytes: int, stream: int):

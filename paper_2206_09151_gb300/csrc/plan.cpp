@@ -62,10 +62,11 @@ struct recon_plan_s {
   size_t off_dirs, off_uA, off_ramp, off_tw, off_twp, off_dens, off_dsum, off_theta, off_cnt, off_x2, off_S, off_T,
       off_stack, off_pow, off_eps, ws_bytes, table_bytes;
   size_t stack_dir_bytes;
-  // optional profiling: 4 events per block plus one at the start of the run
+  // optional profiling: one event after every launch (see recon::EventRecorder)
   bool profile = false;
   std::vector<cudaEvent_t> events;
-  int profiled_blocks = 0;
+  std::vector<int> event_kind;
+  int profiled_events = 0;
   ~recon_plan_s() {
     for (cudaEvent_t e : events) cudaEventDestroy(e);
   }
@@ -86,6 +87,7 @@ void recon_default_options(recon_options* o) {
   o->dir_block = 0;
   o->mlp_weights = nullptr;
   o->nsr = 0.0;
+  o->stage_block = 0;
 }
 
 const char* recon_error_string(int code) {
@@ -145,6 +147,7 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   if (!std::isfinite(o.sigma) || !std::isfinite(o.eps) || !std::isfinite(o.cs))
     return fail(RECON_E_INVALID_ARG, "recon_plan: non-finite sigma, eps or cs");
   if (o.dir_block < 0) return fail(RECON_E_INVALID_ARG, "recon_plan: dir_block < 0");
+  if (o.stage_block < 0) return fail(RECON_E_INVALID_ARG, "recon_plan: stage_block < 0");
 
   recon_plan_s* p = new (std::nothrow) recon_plan_s();
   if (!p) return fail(RECON_E_NO_MEMORY, "recon_plan: out of host memory");
@@ -393,6 +396,13 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   if (db < 1) db = 1;
   p->db = db;
   p->n_blocks = D > 0 ? (D + db - 1) / db : 0;
+  {  // stage-A sub-blocks (option; measured slower than whole blocks at 256^2 / Nz = 32,
+     // where launch gaps outweigh the L2 residency of the intermediates)
+    int sub = o.stage_block > 0 ? o.stage_block : db;
+    if (sub < 1) sub = 1;
+    if (sub > db) sub = db;
+    ca.sub_block = P >= 16 ? sub : db;  // the radix-2 path (tiny images) runs whole blocks
+  }
 
   size_t off = 0;
   p->off_dirs = off;
@@ -417,17 +427,17 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   off = align256(off + sizeof(float) * p->x2.size());
   p->table_bytes = off;
   p->off_S = off;
-  off = align256(off + (size_t)db * p->nv * p->half * 8);
+  off = align256(off + (size_t)ca.sub_block * p->nv * p->half * 8);
   p->off_T = off;
-  off = align256(off + (size_t)db * nz_layers * p->nv * p->half * 8);
+  off = align256(off + (size_t)ca.sub_block * nz_layers * p->nv * p->half * 8);
   p->off_stack = off;
   off = align256(off + (size_t)db * p->stack_dir_bytes);
   p->off_pow = off;
   p->off_eps = off;
   if (o.filter == RECON_FILTER_MLP && !training) {
-    off = align256(off + sizeof(float) * (size_t)db * p->lc.n_bins);
+    off = align256(off + sizeof(float) * (size_t)ca.sub_block * p->lc.n_bins);
     p->off_eps = off;
-    off = align256(off + sizeof(float) * (size_t)db * nz_layers * p->lc.n_bins);
+    off = align256(off + sizeof(float) * (size_t)ca.sub_block * nz_layers * p->lc.n_bins);
   }
   p->ws_bytes = off;
   if (o.filter == RECON_FILTER_MLP && !training && P < 16) {
@@ -451,11 +461,12 @@ int recon_workspace_size(recon_plan_t p, size_t* bytes) {
   return RECON_OK;
 }
 
-int recon_plan_info(recon_plan_t p, int* padded, int* dir_block, int* n_blocks) {
+int recon_plan_info(recon_plan_t p, int* padded, int* dir_block, int* n_blocks, int* stage_block) {
   if (!p) return fail(RECON_E_INVALID_ARG, "recon_plan_info: null plan");
   if (padded) *padded = p->P;
   if (dir_block) *dir_block = p->db;
   if (n_blocks) *n_blocks = p->n_blocks;
+  if (stage_block) *stage_block = p->ca.sub_block;
   return RECON_OK;
 }
 
@@ -570,22 +581,22 @@ int recon_run(recon_plan_t p, const float* images, float* volume, void* workspac
   const recon::Workspace w = carve(p, workspace);
   rc = upload_tables(p, w, s);
   if (rc) return rc;
-  cudaEvent_t* ev = p->profile ? p->events.data() : nullptr;
+  recon::EventRecorder recorder{p->events.data(), p->event_kind.data(), 0, (int)p->events.size()};
+  recon::EventRecorder* rec = p->profile ? &recorder : nullptr;
   MlpHookCtx hctx{p, (const char*)workspace, (float*)((char*)workspace + p->off_pow), w.eps, w.S, w.twp};
   const recon::StageAHook hook{mlp_hook, &hctx};
   const recon::StageAHook* hk = p->ca.filter == RECON_FILTER_MLP ? &hook : nullptr;
-  if (ev) cudaEventRecord(ev[0], s);
+  if (rec) rec->mark(-1, s);
   for (int b = 0; b < p->n_blocks; ++b) {
     const int d0 = b * p->db;
     const int cnt = (p->D - d0) < p->db ? (p->D - d0) : p->db;
-    cudaError_t e = recon::launch_stage_a(p->ca, w, images, d0, cnt, s, ev ? ev + 1 + 4 * b : nullptr, hk);
+    cudaError_t e = recon::launch_stage_a(p->ca, w, images, d0, cnt, s, rec, hk);
     if (e != cudaSuccess) return cuda_fail(e, "recon_run: stage A launch");
-    if (ev) cudaEventRecord(ev[3 + 4 * b], s);
     e = recon::launch_backproject(p->cb, w.dirs, w.stack, d0, cnt, volume, p->opt.accumulate || b > 0, s);
     if (e != cudaSuccess) return cuda_fail(e, "recon_run: backprojection launch");
-    if (ev) cudaEventRecord(ev[4 + 4 * b], s);
+    if (rec) rec->mark(3, s);
   }
-  if (ev) p->profiled_blocks = p->n_blocks;
+  if (rec) p->profiled_events = recorder.n;
   return RECON_OK;
 }
 
@@ -639,8 +650,11 @@ int recon_backproject(recon_plan_t p, const void* stack, int dir_begin, int dir_
 int recon_profile_enable(recon_plan_t p, int enable) {
   if (!p) return fail(RECON_E_INVALID_ARG, "recon_profile_enable: null plan");
   if (enable && p->events.empty()) {
-    p->events.resize(1 + 4 * (size_t)p->n_blocks);
-    for (size_t i = 0; i < p->events.size(); ++i) {
+    const int sub = p->ca.sub_block > 0 ? p->ca.sub_block : 1;
+    const size_t n = 1 + (size_t)p->n_blocks * (3 * (size_t)((p->db + sub - 1) / sub) + 1);
+    p->events.resize(n);
+    p->event_kind.assign(n, -1);
+    for (size_t i = 0; i < n; ++i) {
       cudaError_t e = cudaEventCreate(&p->events[i]);
       if (e != cudaSuccess) {
         p->events.resize(i);
@@ -649,7 +663,7 @@ int recon_profile_enable(recon_plan_t p, int enable) {
     }
   }
   p->profile = enable != 0;
-  p->profiled_blocks = 0;
+  p->profiled_events = 0;
   return RECON_OK;
 }
 
@@ -659,17 +673,18 @@ int recon_profile_read(recon_plan_t p, double* ms, int* launches) {
     ms[q] = 0.0;
     launches[q] = 0;
   }
-  if (p->profiled_blocks == 0) return RECON_OK;
-  cudaError_t e = cudaEventSynchronize(p->events[4 * (size_t)p->profiled_blocks]);
+  if (p->profiled_events < 2) return RECON_OK;
+  cudaError_t e = cudaEventSynchronize(p->events[p->profiled_events - 1]);
   if (e != cudaSuccess) return cuda_fail(e, "recon_profile_read: cudaEventSynchronize");
-  for (int b = 0; b < p->profiled_blocks; ++b)
-    for (int q = 0; q < 4; ++q) {
-      float t = 0.f;
-      e = cudaEventElapsedTime(&t, p->events[4 * (size_t)b + q], p->events[4 * (size_t)b + q + 1]);
-      if (e != cudaSuccess) return cuda_fail(e, "recon_profile_read: cudaEventElapsedTime");
-      ms[q] += t;
-      launches[q] += 1;
-    }
+  for (int i = 1; i < p->profiled_events; ++i) {
+    const int k = p->event_kind[i];
+    if (k < 0 || k > 3) continue;
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, p->events[i - 1], p->events[i]);
+    if (e != cudaSuccess) return cuda_fail(e, "recon_profile_read: cudaEventElapsedTime");
+    ms[k] += t;
+    launches[k] += 1;
+  }
   return RECON_OK;
 }
 
@@ -698,9 +713,11 @@ int run_in_scratch(recon_plan_t p, const float* images, float* volume, char* scr
   const size_t spec = (size_t)p->nv * p->half * 8;
   const size_t inter = spec * p->nzl;
   const bool mlp = p->ca.filter == RECON_FILTER_MLP;
+  const size_t sub = (size_t)(p->ca.sub_block > 0 ? p->ca.sub_block : 1);
   auto need = [&](size_t db) {
-    size_t b = p->table_bytes + align256(db * spec) + align256(db * inter) + align256(db * p->stack_dir_bytes);
-    if (mlp) b += align256(sizeof(float) * db * p->lc.n_bins) + align256(sizeof(float) * db * p->nzl * p->lc.n_bins);
+    const size_t sb = db < sub ? db : sub;
+    size_t b = p->table_bytes + align256(sb * spec) + align256(sb * inter) + align256(db * p->stack_dir_bytes);
+    if (mlp) b += align256(sizeof(float) * sb * p->lc.n_bins) + align256(sizeof(float) * sb * p->nzl * p->lc.n_bins);
     return b;
   };
   if (need(1) > scratch_bytes)
@@ -724,15 +741,16 @@ int run_in_scratch(recon_plan_t p, const float* images, float* volume, char* scr
   w.twp = (float2*)(scratch + p->off_twp);
   w.dens = (float*)(scratch + p->off_dens);
   w.band_sum = (double*)(scratch + p->off_dsum);
+  const size_t sb = db < sub ? db : sub;
   size_t off = p->table_bytes;
   w.S = (float2*)(scratch + off);
-  off += align256(db * spec);
+  off += align256(sb * spec);
   w.T = (float2*)(scratch + off);
-  off += align256(db * inter);
+  off += align256(sb * inter);
   w.stack = (void*)(scratch + off);
   off += align256(db * p->stack_dir_bytes);
   float* pow = (float*)(scratch + off);
-  if (mlp) off += align256(sizeof(float) * db * p->lc.n_bins);
+  if (mlp) off += align256(sizeof(float) * sb * p->lc.n_bins);
   w.eps = (float*)(scratch + off);
   w.n_bins = p->lc.n_bins;
   w.bin_width = p->lc.bin_width;
@@ -740,11 +758,13 @@ int run_in_scratch(recon_plan_t p, const float* images, float* volume, char* scr
   if (rc) return rc;
   MlpHookCtx hctx{p, scratch, pow, w.eps, w.S, w.twp};
   const recon::StageAHook hook{mlp_hook, &hctx};
+  recon::StageAConst ca = p->ca;
+  if (p->P >= 16) ca.sub_block = (int)sb;
   const int n_blocks = (int)((p->D + db - 1) / db);
   for (int b = 0; b < n_blocks; ++b) {
     const int d0 = b * (int)db;
     const int cnt = (p->D - d0) < (int)db ? (p->D - d0) : (int)db;
-    cudaError_t e = recon::launch_stage_a(p->ca, w, images, d0, cnt, s, nullptr, mlp ? &hook : nullptr);
+    cudaError_t e = recon::launch_stage_a(ca, w, images, d0, cnt, s, nullptr, mlp ? &hook : nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "recon_run_noalloc: stage A launch");
     e = recon::launch_backproject(p->cb, w.dirs, w.stack, d0, cnt, volume, p->opt.accumulate || b > 0, s);
     if (e != cudaSuccess) return cuda_fail(e, "recon_run_noalloc: backprojection launch");
@@ -979,7 +999,9 @@ int batch_launch(recon_batch_t bt, const float* const* images, float* const* vol
       w.eps = (float*)(base + bt->off_eps);
       MlpHookCtx hctx{p, base + bt->off_tables[q], (float*)(base + bt->off_pow), w.eps, w.S, w.twp};
       const recon::StageAHook hook{mlp_hook, &hctx};
-      e = recon::launch_stage_a(p->ca, w, images[q], d0, cnt, s, nullptr,
+      recon::StageAConst ca = p->ca;
+      if (p->P >= 16) ca.sub_block = std::min(bt->dbb, p->ca.sub_block > 0 ? p->ca.sub_block : 1);
+      e = recon::launch_stage_a(ca, w, images[q], d0, cnt, s, nullptr,
                                 p->ca.filter == RECON_FILTER_MLP ? &hook : nullptr);
       if (e != cudaSuccess) return cuda_fail(e, "recon_batch: stage A launch");
     }
@@ -1029,10 +1051,11 @@ int recon_batch_create(int n, const recon_plan_t* plans, int dir_block, recon_ba
     bt->off_tables[q] = off;
     off = align256(off + p->table_bytes);
     const size_t db = (size_t)bt->dbb;
-    maxS = std::max(maxS, db * p->nv * p->half * 8);
-    maxT = std::max(maxT, db * p->nzl * p->nv * p->half * 8);
-    maxpow = std::max(maxpow, db * p->lc.n_bins * 4);
-    maxeps = std::max(maxeps, db * p->nzl * p->lc.n_bins * 4);
+    const size_t sb = std::min(db, (size_t)(p->ca.sub_block > 0 ? p->ca.sub_block : 1));
+    maxS = std::max(maxS, sb * p->nv * p->half * 8);
+    maxT = std::max(maxT, sb * p->nzl * p->nv * p->half * 8);
+    maxpow = std::max(maxpow, sb * p->lc.n_bins * 4);
+    maxeps = std::max(maxeps, sb * p->nzl * p->lc.n_bins * 4);
     smem = std::max(smem, db * 64);
     rounds = std::max(rounds, (p->D + bt->dbb - 1) / bt->dbb);
   }

@@ -48,6 +48,7 @@ struct StageAConst {
   int su;               // stack row pitch in tap pairs, nu + 1
   size_t layer_elems;   // pairs per layer, (nv + 2) * (nu + 1)
   DensityConst dens;
+  int sub_block;        // directions per stage-A sub-block (S and T sized for it), 0 = whole block
 };
 
 // Device pointers into the workspace.
@@ -74,10 +75,24 @@ struct StageAHook {
   void* ctx;
 };
 
-// `ev`, when not null, holds two events recorded after the row FFTs (and the hook) and
-// after the column kernel (the caller records the ones before and after the whole stage).
+// Optional kernel timing: an event is recorded after every launch and tagged with the
+// kernel it ends (0 row FFTs and the learned hook, 1 column kernel, 2 row iFFTs,
+// 3 backprojection); the interval between consecutive events is that kernel's time.
+struct EventRecorder {
+  cudaEvent_t* ev;
+  int* kind;
+  int n, cap;
+  void mark(int k, cudaStream_t s) {
+    if (n < cap) {
+      cudaEventRecord(ev[n], s);
+      kind[n] = k;
+      ++n;
+    }
+  }
+};
+
 cudaError_t launch_stage_a(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin,
-                           int dir_count, cudaStream_t stream, cudaEvent_t* ev = nullptr,
+                           int dir_count, cudaStream_t stream, EventRecorder* rec = nullptr,
                            const StageAHook* hook = nullptr);
 // The row FFTs alone (S of `count` images starting at image `first`), P >= 16.
 cudaError_t launch_rows_fwd(const StageAConst& c, float2* S, const float2* twp, const float* images, int first,

@@ -204,7 +204,11 @@ __global__ void __launch_bounds__(kThreads, (FILT == 2 || DENS) ? 3 : 4) k_cols(
   }
   const uint64_t* uAn = uA + (size_t)(dir_begin + n) * c.nz_layers;
   float2* Tn = T + (size_t)n * c.nz_layers * c.half * c.nv;
-  for (int k = 0; k < c.nz_layers; ++k) {
+  // this CTA's layers: group blockIdx.z of gridDim.z equal groups
+  const int lg = (c.nz_layers + gridDim.z - 1) / gridDim.z;
+  const int k_begin = blockIdx.z * lg;
+  const int k_end = min(c.nz_layers, k_begin + lg);
+  for (int k = k_begin; k < k_end; ++k) {
     const uint64_t uAk = uAn[k];
     const uint32_t a_hi = (uint32_t)(uAk >> 32), a_lo = (uint32_t)uAk;
     const float* eps_k = eps_tab + ((size_t)n * c.nz_layers + k) * n_bins;
@@ -461,34 +465,48 @@ __global__ void k_small_rows_inv(const float2* __restrict__ T, PairT* __restrict
 // ------------------------------------------------------------------ launch
 template <int P>
 cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin, int dir_count,
-                       cudaStream_t stream, cudaEvent_t* ev, const StageAHook* hook) {
+                       cudaStream_t stream, EventRecorder* rec, const StageAHook* hook) {
   constexpr int G = groups_per_cta<P>();
-  k_rows_fwd<P><<<dim3((c.nv + 2 * G - 1) / (2 * G), dir_count), kThreads, 0, stream>>>(images, ws.S, ws.twp, c,
-                                                                                         dir_begin);
-  if (hook) {
-    const cudaError_t e = hook->fn(hook->ctx, dir_begin, dir_count, stream);
-    if (e != cudaSuccess) return e;
-  }
-  if (ev) cudaEventRecord(ev[0], stream);
-  const dim3 gc((c.half + G - 1) / G, dir_count);
+  // Sub-blocks of c.sub_block directions: S and T of one sub-block stay in L2 between the
+  // column and the row kernels; each sub-block writes its part of the block's stack.
+  const int sub = c.sub_block > 0 ? c.sub_block : dir_count;
+  const int col_groups = (c.half + G - 1) / G;
+  for (int s0 = 0; s0 < dir_count; s0 += sub) {
+    const int cnt = min(sub, dir_count - s0);
+    const int d0 = dir_begin + s0;
+    k_rows_fwd<P><<<dim3((c.nv + 2 * G - 1) / (2 * G), cnt), kThreads, 0, stream>>>(images, ws.S, ws.twp, c, d0);
+    if (hook) {
+      const cudaError_t e = hook->fn(hook->ctx, d0, cnt, stream);
+      if (e != cudaSuccess) return e;
+    }
+    if (rec) rec->mark(0, stream);
+    // layer groups so that about 2 waves of CTAs run even for a small sub-block
+    const int target = 2 * 152 * 4;
+    int lgroups = (target + col_groups * cnt - 1) / (col_groups * cnt);
+    lgroups = max(1, min(lgroups, c.nz_layers / 2 > 0 ? c.nz_layers / 2 : 1));
+    const dim3 gc(col_groups, cnt, lgroups);
 #define RECON_K_COLS(F, D)                                                                                      \
   k_cols<P, F, D><<<gc, kThreads, 0, stream>>>(ws.S, ws.T, ws.twp, ws.uA, ws.ramp, ws.dirs, ws.dens, ws.band_sum, \
-                                               ws.eps, ws.n_bins, ws.bin_width, c, dir_begin)
-  const bool dens = c.dens.enabled != 0;
-  if (c.filter == 0) {
-    if (dens) RECON_K_COLS(0, true); else RECON_K_COLS(0, false);
-  } else if (c.filter == 2) {
-    if (dens) RECON_K_COLS(2, true); else RECON_K_COLS(2, false);
-  } else {
-    if (dens) RECON_K_COLS(1, true); else RECON_K_COLS(1, false);
-  }
+                                               ws.eps, ws.n_bins, ws.bin_width, c, d0)
+    const bool dens = c.dens.enabled != 0;
+    if (c.filter == 0) {
+      if (dens) RECON_K_COLS(0, true); else RECON_K_COLS(0, false);
+    } else if (c.filter == 2) {
+      if (dens) RECON_K_COLS(2, true); else RECON_K_COLS(2, false);
+    } else {
+      if (dens) RECON_K_COLS(1, true); else RECON_K_COLS(1, false);
+    }
 #undef RECON_K_COLS
-  if (ev) cudaEventRecord(ev[1], stream);
-  const dim3 gi((c.nv + 2 * G - 1) / (2 * G), c.nz_layers, dir_count);
-  if (c.stack_bf16)
-    k_rows_inv<P, __nv_bfloat162><<<gi, kThreads, 0, stream>>>(ws.T, (__nv_bfloat162*)ws.stack, ws.twp, c);
-  else
-    k_rows_inv<P, float2><<<gi, kThreads, 0, stream>>>(ws.T, (float2*)ws.stack, ws.twp, c);
+    if (rec) rec->mark(1, stream);
+    const dim3 gi((c.nv + 2 * G - 1) / (2 * G), c.nz_layers, cnt);
+    const size_t stack_off = (size_t)s0 * c.nz_layers * c.layer_elems;
+    if (c.stack_bf16)
+      k_rows_inv<P, __nv_bfloat162><<<gi, kThreads, 0, stream>>>(ws.T, (__nv_bfloat162*)ws.stack + stack_off, ws.twp,
+                                                                 c);
+    else
+      k_rows_inv<P, float2><<<gi, kThreads, 0, stream>>>(ws.T, (float2*)ws.stack + stack_off, ws.twp, c);
+    if (rec) rec->mark(2, stream);
+  }
   return cudaGetLastError();
 }
 
@@ -501,25 +519,26 @@ cudaError_t rows_fwd_only(const StageAConst& c, float2* S, const float2* twp, co
 }
 
 cudaError_t launch_small(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin,
-                         int dir_count, cudaStream_t stream, cudaEvent_t* ev) {
+                         int dir_count, cudaStream_t stream, EventRecorder* rec) {
   k_small_rows_fwd<<<dim3((c.nv + 1) / 2, dir_count), 32, 0, stream>>>(images, ws.S, ws.tw, c, dir_begin);
-  if (ev) cudaEventRecord(ev[0], stream);
+  if (rec) rec->mark(0, stream);
   k_small_cols<<<dim3(c.half, dir_count), 32, 0, stream>>>(ws.S, ws.T, ws.tw, ws.uA, ws.ramp, ws.dirs, ws.dens,
                                                           ws.band_sum, ws.eps, ws.n_bins, ws.bin_width, c,
                                                           dir_begin);
-  if (ev) cudaEventRecord(ev[1], stream);
+  if (rec) rec->mark(1, stream);
   const dim3 gi((c.nv + 1) / 2, c.nz_layers, dir_count);
   if (c.stack_bf16)
     k_small_rows_inv<__nv_bfloat162><<<gi, 32, 0, stream>>>(ws.T, (__nv_bfloat162*)ws.stack, ws.tw, c);
   else
     k_small_rows_inv<float2><<<gi, 32, 0, stream>>>(ws.T, (float2*)ws.stack, ws.tw, c);
+  if (rec) rec->mark(2, stream);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_stage_a(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin,
-                           int dir_count, cudaStream_t stream, cudaEvent_t* ev, const StageAHook* hook) {
+                           int dir_count, cudaStream_t stream, EventRecorder* ev, const StageAHook* hook) {
   if (dir_count <= 0) return cudaSuccess;
   switch (c.P) {
     case 16: return launch_reg<16>(c, ws, images, dir_begin, dir_count, stream, ev, hook);

@@ -26,13 +26,14 @@ class Reconstructor:
                  sigma: float = 0.0, eps: float = 0.1, cs: float = 0.0, filter: str = "tikhonov",
                  input_mode: str = "intensity", stack_dtype: str = "f32", accumulate: bool = False,
                  dir_block: int = 0, ramp: str = "single_axis", mlp_weights=None, nsr: float = 0.0,
-                 device=None, allocate: bool = True):
+                 stage_block: int = 0, device=None, allocate: bool = True):
         o = _abi.recon_default_options()
         o.sigma, o.eps, o.cs = float(sigma), float(eps), float(cs)
         o.filter, o.input_mode, o.stack_dtype = _FILTERS[filter], _INPUTS[input_mode], _STACKS[stack_dtype]
         o.accumulate, o.dir_block = int(bool(accumulate)), int(dir_block)
         o.ramp_mode = _RAMPS[ramp]
         o.nsr = float(nsr)
+        o.stage_block = int(stage_block)
         self._weights = None
         if mlp_weights is not None:
             self._weights = np.ascontiguousarray(mlp_weights, dtype=np.float32)
@@ -43,7 +44,7 @@ class Reconstructor:
         self.stack_dtype = torch.bfloat16 if stack_dtype == "bf16" else torch.float32
         self.plan = _abi.recon_plan(self.rot, nu, nv, lam, delta, defocus, nz_layers, self.grid, o)
         self.ws_bytes = _abi.recon_workspace_size(self.plan)
-        self.padded, self.dir_block, self.n_blocks = _abi.recon_plan_info(self.plan)
+        self.padded, self.dir_block, self.n_blocks, self.stage_block = _abi.recon_plan_info(self.plan)
         self.device = torch.device(device) if device is not None else (
             torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else None)
         self.workspace = None

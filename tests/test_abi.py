@@ -34,8 +34,8 @@ def _plan(**kw):
 
 def test_plan_builds_on_the_host_and_reports_its_layout(lib):
     p = _plan()
-    P, db, nb = _abi.recon_plan_info(p)
-    assert P == 128 and 1 <= db <= 12 and nb == -(-12 // db)
+    P, db, nb, sb = _abi.recon_plan_info(p)
+    assert P == 128 and 1 <= db <= 12 and nb == -(-12 // db) and 1 <= sb <= db
     ws = _abi.recon_workspace_size(p)
     assert ws > 0 and ws % 256 == 0
     _abi.recon_destroy(p)
@@ -48,7 +48,7 @@ def test_workspace_grows_with_the_direction_block(lib):
     o4 = _abi.recon_default_options()
     o4.dir_block = 4
     p1, p4 = _plan(opts=o1), _plan(opts=o4)
-    assert _abi.recon_plan_info(p1)[1:] == (1, 12) and _abi.recon_plan_info(p4)[1:] == (4, 3)
+    assert _abi.recon_plan_info(p1)[1:3] == (1, 12) and _abi.recon_plan_info(p4)[1:3] == (4, 3)
     assert _abi.recon_workspace_size(p4) > _abi.recon_workspace_size(p1)
     _abi.recon_destroy(p1)
     _abi.recon_destroy(p4)

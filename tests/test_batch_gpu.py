@@ -90,6 +90,15 @@ def test_batch_matches_single_runs(dir_block):
         r.close()
 
 
+def _same(q, toms, a, c):
+    """Bitwise for the deterministic tomograms; the density splat and the learned path's
+    power spectrum sum with float atomics, whose order varies from run to run."""
+    kw = toms[q][3]
+    if kw["ramp"] == "density" or kw["filter"] == "mlp":
+        return torch.allclose(a, c, rtol=1e-6, atol=1e-6 * float(c.abs().max()))
+    return torch.equal(a, c)
+
+
 def test_batch_graph_replays_are_identical_to_the_run():
     from paper_2206_09151_gb300.recon import Batch
     toms = _tomograms()
@@ -103,8 +112,8 @@ def test_batch_graph_replays_are_identical_to_the_run():
         v2 = [r.new_volume().fill_(0.5) for r in recons]
         b.run(imgs, v2, graph=True)  # pointers change: captured again, then replayed below
         torch.cuda.synchronize()
-        for a, c in zip(v1, v2):
-            assert torch.equal(a, c)
+        for q, (a, c) in enumerate(zip(v1, v2)):
+            assert _same(q, toms, a, c), q
     v3 = [r.new_volume().fill_(0.5) for r in recons]
     b.run(imgs, v3, graph=True)
     for _ in range(3):
@@ -112,8 +121,8 @@ def test_batch_graph_replays_are_identical_to_the_run():
             v.fill_(0.5)
         b.run(imgs, v3, graph=True)  # same pointers: a replay of the captured graph
         torch.cuda.synchronize()
-        for a, c in zip(v1, v3):
-            assert torch.equal(a, c)
+        for q, (a, c) in enumerate(zip(v1, v3)):
+            assert _same(q, toms, a, c), q
     b.close()
     for r in recons:
         r.close()
@@ -130,5 +139,20 @@ def test_batch_member_matches_oracle():
                   nz_layers=kw["nz_layers"], grid=grid, sigma=kw["sigma"], eps=kw["eps"])
     assert rel_l2(vols[0].cpu().numpy(), ref) <= 1e-5
     b.close()
+    for r in recons:
+        r.close()
+
+
+def test_autotuner_picks_a_measured_candidate():
+    from paper_2206_09151_gb300.autotune import tune_batch_round, tune_dir_block
+    from paper_2206_09151_gb300.recon import Reconstructor
+    toms = _tomograms()
+    rot, nu, grid, kw, img = toms[0]
+    kw = dict(kw)
+    out = tune_dir_block(rot, nu, nu, grid, img, candidates=[10, 35, 70], repeats=2, **kw)
+    assert out["dir_block"] in (10, 35, 70) and set(out["ms"]) == {"10", "35", "70"}
+    recons = [Reconstructor(t[0], t[1], t[1], t[2], **t[3]) for t in toms[:3]]
+    out = tune_batch_round(recons, [t[4] for t in toms[:3]], candidates=(8, 32), repeats=2)
+    assert out["dir_block"] in (8, 32)
     for r in recons:
         r.close()
