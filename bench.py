@@ -270,7 +270,7 @@ def run_ours(args):
     r = Reconstructor(cfg["rot"], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
                       defocus=cfg["defocus"], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"], eps=cfg["eps"],
                       cs=cfg["cs"], stack_dtype=args.stack, dir_block=args.dir_block, stage_block=args.stage_block,
-                      device=dev, **filt_kw)
+                      bp_kernel=args.bp_kernel, device=dev, **filt_kw)
     vol = r.new_volume()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -362,7 +362,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": args.stack, "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload] + (f" [first {D} directions only]" if args.dirs else ""),
                        "stack": args.stack, "filter": args.filter, "dir_block": db,
-                       "stage_block": r.stage_block,
+                       "stage_block": r.stage_block, "bp_kernel": args.bp_kernel,
                        "blocks": nb, "padded_fft": r.padded, "updates_per_step": U,
                        "l2": "flushed between timed steps (256 MiB write outside the timed span)",
                        "parallelism": f"replicas x{world}"},
@@ -409,6 +409,8 @@ def main():
                     help="mlp: the learned regulariser (seeded untrained weights; speed and parity)")
     ap.add_argument("--dir-block", type=int, default=0)
     ap.add_argument("--stage-block", type=int, default=0, help="directions per FFT/filter sub-block, 0 = auto")
+    ap.add_argument("--bp-kernel", choices=["auto", "direct", "staged"], default="auto",
+                    help="single-axis backprojection variant")
     ap.add_argument("--dirs", type=int, default=None, help="first N directions only (small profiling cases)")
     ap.add_argument("--cpu-dirs", type=int, default=3)
     ap.add_argument("--ref-dirs", type=int, default=1)

@@ -74,6 +74,10 @@ extern "C" {
 #define RECON_RAMP_DENSITY 1     /* any geometry: W = g / (S(q) + eps_S), S the gridded
                                     sampling density of all views' slices (Sec. 2)        */
 
+#define RECON_BP_AUTO 0          /* the single-axis variant measured faster (DIRECT)     */
+#define RECON_BP_DIRECT 1        /* single-axis: bilinear gathers straight from the stack */
+#define RECON_BP_STAGED 2        /* single-axis: footprint staged in shared memory        */
+
 /* Limits (RECON_E_UNSUPPORTED_SIZE beyond them). */
 #define RECON_MAX_IMAGE 1024     /* nu, nv <= 1024, so P <= 2048                        */
 #define RECON_MAX_LAYERS 96      /* 1 <= nz_layers <= 96                                */
@@ -107,6 +111,10 @@ typedef struct {
                       the Poisson floor (nsr M)^2 per DFT coefficient of the SNR feature   */
   int stage_block; /* directions per FFT/filter sub-block (their spectra and per-layer
                       intermediates sized for it), 0 = the whole direction block           */
+  int bp_kernel;   /* RECON_BP_*: single-axis backprojection variant (gathers straight from
+                      the stack, or each direction's footprint staged in shared memory);
+                      AUTO picks the measured-faster one on sm_103a; other geometries
+                      always use the general kernel                                         */
 } recon_options;
 
 /* Fills *opts with defaults: sigma 0, eps 0.1 (the value of Sec. 3), cs 0, Tikhonov

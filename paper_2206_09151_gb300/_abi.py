@@ -30,6 +30,7 @@ RECON_STACK_F32 = 0
 RECON_STACK_BF16 = 1
 RECON_RAMP_SINGLE_AXIS = 0
 RECON_RAMP_DENSITY = 1
+RECON_BP_AUTO, RECON_BP_DIRECT, RECON_BP_STAGED = 0, 1, 2
 RECON_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
@@ -47,7 +48,7 @@ class ReconOptions(ctypes.Structure):
                 ("filter", ctypes.c_int), ("input_mode", ctypes.c_int), ("stack_dtype", ctypes.c_int),
                 ("ramp_mode", ctypes.c_int), ("accumulate", ctypes.c_int), ("dir_block", ctypes.c_int),
                 ("mlp_weights", ctypes.POINTER(ctypes.c_float)), ("nsr", ctypes.c_double),
-                ("stage_block", ctypes.c_int)]
+                ("stage_block", ctypes.c_int), ("bp_kernel", ctypes.c_int)]
 
 
 class ReconTrainCfg(ctypes.Structure):

@@ -137,6 +137,19 @@ __global__ void __launch_bounds__(kTX* kTY) k_backproject(const DirParams* __res
 // along y: per direction it forms u and the layer once, then walks kJ detector rows with
 // two taps each (four when b_off is a half-integer), accumulating in registers.
 constexpr int kAX = 32, kAZ = 8, kJ = 16;
+// A warp of the single-axis kernels covers kLaneWX (i) x 32 / kLaneWX (k) voxel columns:
+// a compact footprint spans fewer depth layers and detector columns than a line of 32
+// along i, so each of its row gathers touches fewer cache lines.
+constexpr int kLaneWX = 8;
+static_assert(32 % kLaneWX == 0 && kAX % kLaneWX == 0 && kAZ % (32 / kLaneWX) == 0 &&
+                  (kAX / kLaneWX) * (kAZ / (32 / kLaneWX)) * 32 == kAX * kAZ,
+              "the warps must tile the 32 x 8 voxel columns");
+__device__ __forceinline__ void axis_lane(int t, int& tx, int& tz) {
+  constexpr int WZ = 32 / kLaneWX, BX = kAX / kLaneWX;  // warp extent in k; warps along i
+  const int w = t >> 5, l = t & 31;
+  tx = (w % BX) * kLaneWX + (l % kLaneWX);
+  tz = (w / BX) * WZ + l / kLaneWX;
+}
 
 struct AxisDir {  // per (tile, direction), 32 bytes in shared memory
   float fa;       // fractional tile-origin u coordinate minus 0.5
@@ -161,7 +174,8 @@ __device__ __forceinline__ void bp_axis_tile(int bx, int by, int bz, const DirPa
                                              int dir_count, float* __restrict__ vol, int accumulate,
                                              AxisDir* s_ax) {
   const int i0 = bx * kAX, k0 = by * kAZ, j0 = bz * kJ;
-  const int tx = threadIdx.x % kAX, tz = threadIdx.x / kAX;
+  int tx, tz;
+  axis_lane(threadIdx.x, tx, tz);
   for (int d = threadIdx.x; d < dir_count; d += blockDim.x) {
     const DirParams& p = dirs[dir_begin + d];
     const double a = fma(p.a[0], (double)i0, fma(p.a[2], (double)k0, p.a[3]));  // p.a[1] = 0
@@ -264,6 +278,217 @@ cudaError_t launch_axis(const BackprojConst& c, const DirParams* dirs, const voi
 }
 
 // ---------------------------------------------------------------------------------
+// Staged single-axis backprojection.  Per (tile, direction) the stack entries the tile
+// can touch form a box of layers x (16 or 17) detector rows x a column range (exact: the
+// per-thread u coordinate is a chain of FMAs, monotone in the thread indices, so its
+// extremes are at the tile corners; the layer is an exact integer sum).  The box of the
+// next direction is copied into shared memory with cp.async while the current one is
+// consumed (double buffering), so the gathers read shared memory and the copies hide the
+// L2/DRAM latency.  A direction whose box exceeds a buffer is read from global memory.
+constexpr int kStageBytes = 16 * 1024;
+
+struct AxisBox {  // per (tile, direction), 16 bytes in shared memory
+  int L0, nL;     // first layer, layers
+  int c0, W;      // first pair column, width (W = 0: read from global memory)
+};
+static_assert(sizeof(AxisBox) == 16, "AxisBox layout");
+
+__device__ __forceinline__ void cp_async(float2* dst, const float2* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async(__nv_bfloat162* dst, const __nv_bfloat162* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+__device__ __forceinline__ float2 smem_pair(const float2* p) { return *p; }
+__device__ __forceinline__ float2 smem_pair(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
+template <typename ST>
+__device__ __forceinline__ ST zero_pair();
+template <>
+__device__ __forceinline__ float2 zero_pair<float2>() { return make_float2(0.f, 0.f); }
+template <>
+__device__ __forceinline__ __nv_bfloat162 zero_pair<__nv_bfloat162>() { return __floats2bfloat162_rn(0.f, 0.f); }
+
+// pair column a thread reads for u coordinate ap (the clamped tap + 1), see bp_axis_tile
+__device__ __forceinline__ int pair_col(float ap, int ia, int nu) {
+  const float ta = fminf(fmaxf(ap, (float)(-1 - ia)), (float)(nu - 1 - ia)) + kMagic;
+  return __float_as_int(ta) - kMagicBits + ia + 1;
+}
+
+template <typename ST, bool TWO_ROWS>
+__global__ void __launch_bounds__(kAX* kAZ) k_backproject_axis_staged(const DirParams* __restrict__ dirs,
+                                                                       const ST* __restrict__ stack, BackprojConst c,
+                                                                       int dir_begin, int dir_count,
+                                                                       float* __restrict__ vol, int accumulate) {
+  constexpr int NR = kJ + (TWO_ROWS ? 1 : 0);
+  constexpr int CAP = kStageBytes / (int)sizeof(ST);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ST* buf0 = (ST*)smem_raw;
+  ST* buf1 = buf0 + CAP;
+  AxisDir* s_ax = (AxisDir*)(smem_raw + 2 * kStageBytes);
+  AxisBox* s_box = (AxisBox*)(s_ax + dir_count);
+  const int i0 = blockIdx.x * kAX, k0 = blockIdx.y * kAZ, j0 = blockIdx.z * kJ;
+  int tx, tz;
+  axis_lane(threadIdx.x, tx, tz);
+  const int row0 = j0 + c.b_int;  // detector row of this tile's first voxel row
+  const int last_layer = c.nz_layers - 1;
+  for (int d = threadIdx.x; d < dir_count; d += blockDim.x) {
+    const DirParams& p = dirs[dir_begin + d];
+    const double a = fma(p.a[0], (double)i0, fma(p.a[2], (double)k0, p.a[3]));  // p.a[1] = 0
+    const double fla = floor(a);
+    AxisDir ad;
+    ad.fa = (float)(a - fla) - 0.5f;
+    ad.ia = (int)fla;
+    ad.t = (uint32_t)p.t[0] + (uint32_t)p.t[1] * (uint32_t)i0 + (uint32_t)p.t[3] * (uint32_t)k0;  // Tj = 0
+    ad.af0 = p.af[0];
+    ad.af2 = p.af[2];
+    ad.ti = (uint32_t)p.t[1];
+    ad.tk = (uint32_t)p.t[3];
+    ad.pad = 0;
+    s_ax[d] = ad;
+    // the box: extremes of the pair column and of the layer over the corners of the part
+    // of the tile inside the volume (threads outside it are clamped into the box)
+    const int ex = min(kAX, c.nx - i0) - 1, ez = min(kAZ, c.nz - k0) - 1;
+    int cmin = 1 << 30, cmax = -(1 << 30), lmin = 1 << 30, lmax = -(1 << 30);
+    for (int cx = 0; cx < 2; ++cx)
+      for (int cz = 0; cz < 2; ++cz) {
+        const int ux = cx ? ex : 0, uz = cz ? ez : 0;
+        const int pc = pair_col(fmaf(ad.af0, (float)ux, fmaf(ad.af2, (float)uz, ad.fa)), ad.ia, c.nu);
+        const int layer =
+            min(max((int32_t)(ad.t + ad.ti * (uint32_t)ux + ad.tk * (uint32_t)uz) >> 24, 0), last_layer);
+        cmin = min(cmin, pc);
+        cmax = max(cmax, pc);
+        lmin = min(lmin, layer);
+        lmax = max(lmax, layer);
+      }
+    AxisBox bx;
+    bx.L0 = lmin;
+    bx.nL = lmax - lmin + 1;
+    bx.c0 = cmin;
+    bx.W = cmax - cmin + 1;
+    if (bx.nL * NR * bx.W > CAP) bx.W = 0;  // too large: read from global memory
+    s_box[d] = bx;
+  }
+  __syncthreads();
+
+  // copy the box of direction d into `buf` (rows outside the stack become zero)
+  auto issue = [&](int d, ST* buf) {
+    const AxisBox bx = s_box[d];
+    if (bx.W > 0) {
+      // warp w copies box rows w, w + 8, ...; its lanes stride over the columns
+      const ST* base = stack + (size_t)d * c.nz_layers * c.layer_elems + bx.c0;
+      const int lane = threadIdx.x & 31;
+      for (int br = threadIdx.x >> 5; br < bx.nL * NR; br += kAZ) {
+        const int l = br / NR, r = br - l * NR;  // NR is a compile-time constant
+        const int R = row0 + 1 + r;              // padded row
+        ST* dst = buf + br * bx.W;
+        if (R >= 0 && R <= c.nv + 1) {
+          const ST* src = base + (size_t)(bx.L0 + l) * c.layer_elems + (size_t)R * c.su;
+          for (int col = lane; col < bx.W; col += 32) cp_async(dst + col, src + col);
+        } else {
+          for (int col = lane; col < bx.W; col += 32) dst[col] = zero_pair<ST>();
+        }
+      }
+    }
+    cp_commit();
+  };
+
+  float acc[kJ];
+#pragma unroll
+  for (int q = 0; q < kJ; ++q) acc[q] = 0.f;
+  const bool rows_inside = row0 >= -1 && row0 + kJ - 1 + (TWO_ROWS ? 1 : 0) <= c.nv;
+  const float ftx = (float)tx, ftz = (float)tz;
+  const float fb = c.b_frac;
+  if (dir_count > 0) issue(0, buf0);
+  for (int d = 0; d < dir_count; ++d) {
+    ST* cur = (d & 1) ? buf1 : buf0;
+    if (d + 1 < dir_count) {
+      issue(d + 1, (d & 1) ? buf0 : buf1);
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
+    }
+    __syncthreads();  // the box of d is in `cur` for every thread
+    const AxisDir ad = s_ax[d];
+    const AxisBox bx = s_box[d];
+    const float ap = fmaf(ad.af0, ftx, fmaf(ad.af2, ftz, ad.fa));
+    const int layer = min(max((int32_t)(ad.t + ad.ti * (uint32_t)tx + ad.tk * (uint32_t)tz) >> 24, 0), last_layer);
+    const float ta = fminf(fmaxf(ap, (float)(-1 - ad.ia)), (float)(c.nu - 1 - ad.ia)) + kMagic;
+    const int ra = __float_as_int(ta) - kMagicBits;
+    const float fa = __saturatef(ap - (ta - kMagic) + 0.5f);
+    if (bx.W > 0) {
+      const int bl = min(max(layer - bx.L0, 0), bx.nL - 1);
+      const int bc = min(max(ra + ad.ia + 1 - bx.c0, 0), bx.W - 1);
+      const ST* sp = cur + (bl * NR) * bx.W + bc;
+      if (TWO_ROWS) {
+        float2 v = smem_pair(sp);
+        float prev = fmaf(fa, v.y - v.x, v.x);
+#pragma unroll
+        for (int q = 0; q < kJ; ++q) {
+          v = smem_pair(sp + (q + 1) * bx.W);
+          const float next = fmaf(fa, v.y - v.x, v.x);
+          acc[q] += fmaf(fb, next - prev, prev);
+          prev = next;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < kJ; ++q) {
+          const float2 v = smem_pair(sp + q * bx.W);
+          acc[q] += fmaf(fa, v.y - v.x, v.x);
+        }
+      }
+    } else {  // box too large for a buffer: gathers from global memory (as bp_axis_tile)
+      const ST* p = stack + ((size_t)d * c.nz_layers + layer) * c.layer_elems + (ptrdiff_t)(row0 + 1) * c.su +
+                    (ra + ad.ia + 1);
+#pragma unroll
+      for (int q = 0; q < kJ; ++q) {
+        const int r = row0 + q;
+        const float lo = (rows_inside || (r >= -1 && r <= c.nv)) ? lerp_row(p + q * c.su, fa) : 0.f;
+        if (TWO_ROWS) {
+          const float hi = (rows_inside || (r + 1 >= -1 && r + 1 <= c.nv)) ? lerp_row(p + (q + 1) * c.su, fa) : 0.f;
+          acc[q] += fmaf(fb, hi - lo, lo);
+        } else {
+          acc[q] += lo;
+        }
+      }
+    }
+    __syncthreads();  // everyone is done with `cur` before it is refilled
+  }
+
+  const int i = i0 + tx, k = k0 + tz;
+  if (i >= c.nx || k >= c.nz) return;
+#pragma unroll
+  for (int q = 0; q < kJ; ++q) {
+    const int j = j0 + q;
+    if (j < c.ny) {
+      float* v = vol + ((size_t)k * c.ny + j) * c.nx + i;
+      *v = accumulate ? *v + acc[q] : acc[q];
+    }
+  }
+}
+
+template <typename ST, bool TWO_ROWS>
+cudaError_t launch_axis_staged(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
+                               int dir_count, float* volume, int accumulate, cudaStream_t stream) {
+  dim3 grid((c.nx + kAX - 1) / kAX, (c.nz + kAZ - 1) / kAZ, (c.ny + kJ - 1) / kJ);
+  const size_t smem = 2 * (size_t)kStageBytes + (size_t)dir_count * (sizeof(AxisDir) + sizeof(AxisBox));
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_backproject_axis_staged<ST, TWO_ROWS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_backproject_axis_staged<ST, TWO_ROWS><<<grid, kAX * kAZ, smem, stream>>>(dirs, (const ST*)stack, c, dir_begin,
+                                                                             dir_count, volume, accumulate);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
 // Persistent backprojection over many tomograms: CTAs take (tomogram, tile) items from
 // one atomic counter until the items run out; each item runs the tile body of its
 // tomogram's kind.  No CTA waits on another, so the loop always ends.
@@ -323,13 +548,23 @@ __global__ void __launch_bounds__(256) k_backproject_persistent(const BatchBp* _
 cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
                                int dir_count, float* volume, int accumulate, cudaStream_t stream) {
   if (dir_count <= 0 || c.nx <= 0 || c.ny <= 0 || c.nz <= 0) return cudaSuccess;
-  if (c.axis_y) {
+  if (c.axis_y && !c.staged) {
     const bool two = c.b_frac != 0.f;
     if (c.stack_bf16)
       return two ? launch_axis<__nv_bfloat162, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream)
                  : launch_axis<__nv_bfloat162, false>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream);
     return two ? launch_axis<float2, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream)
                : launch_axis<float2, false>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream);
+  }
+  if (c.axis_y) {
+    const bool two = c.b_frac != 0.f;
+    if (c.stack_bf16)
+      return two ? launch_axis_staged<__nv_bfloat162, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate,
+                                                            stream)
+                 : launch_axis_staged<__nv_bfloat162, false>(c, dirs, stack, dir_begin, dir_count, volume, accumulate,
+                                                             stream);
+    return two ? launch_axis_staged<float2, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream)
+               : launch_axis_staged<float2, false>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream);
   }
   dim3 grid((c.nx + kTX - 1) / kTX, (c.ny + kTY - 1) / kTY, (c.nz + kTZ - 1) / kTZ);
   const size_t smem = (size_t)dir_count * sizeof(TileDir);

@@ -88,6 +88,7 @@ void recon_default_options(recon_options* o) {
   o->mlp_weights = nullptr;
   o->nsr = 0.0;
   o->stage_block = 0;
+  o->bp_kernel = RECON_BP_AUTO;
 }
 
 const char* recon_error_string(int code) {
@@ -148,6 +149,8 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
     return fail(RECON_E_INVALID_ARG, "recon_plan: non-finite sigma, eps or cs");
   if (o.dir_block < 0) return fail(RECON_E_INVALID_ARG, "recon_plan: dir_block < 0");
   if (o.stage_block < 0) return fail(RECON_E_INVALID_ARG, "recon_plan: stage_block < 0");
+  if (o.bp_kernel < RECON_BP_AUTO || o.bp_kernel > RECON_BP_STAGED)
+    return fail(RECON_E_INVALID_ARG, "recon_plan: unknown bp_kernel");
 
   recon_plan_s* p = new (std::nothrow) recon_plan_s();
   if (!p) return fail(RECON_E_NO_MEMORY, "recon_plan: out of host memory");
@@ -374,6 +377,7 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
     cb.b_int = (int)fl;
     cb.b_frac = (float)(boff - fl);
   }
+  cb.staged = o.bp_kernel == RECON_BP_STAGED;
 
   const size_t elem = ca.stack_bf16 ? 4 : 8;  // one tap pair
   p->stack_dir_bytes = (size_t)nz_layers * ca.layer_elems * elem;
@@ -892,7 +896,9 @@ extern "C" int recon_mlp_train(const recon_train_cfg* cfg, float* weights, float
   const float* x2 = (const float*)(b + p->off_x2);
   cudaError_t e = cudaMemcpyAsync(theta, weights, sizeof(float) * recon::kMlpParams, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(pow, 0, sizeof(float) * (size_t)N * p->lc.n_bins, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(g, 0, sizeof(float) * recon::kMlpParams * 3, s);  // grad, m1, m2
+  // grad, m1 and m2 (separate 256-byte aligned arrays: the padding between them is not cleared)
+  for (float* a : {g, m1, m2})
+    if (e == cudaSuccess) e = cudaMemsetAsync(a, 0, sizeof(float) * recon::kMlpParams, s);
   // spectra of the images (and their radial power) and of the layer targets
   if (e == cudaSuccess) e = recon::launch_rows_fwd(p->ca, S, w.twp, cfg->images, 0, N, s);
   if (e == cudaSuccess) e = recon::launch_cols_forward(p->ca, p->lc, S, G, pow, w.twp, N, s);

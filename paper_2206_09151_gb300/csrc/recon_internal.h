@@ -110,6 +110,7 @@ struct BackprojConst {
   int axis_y;
   int b_int;      // floor(b_off)
   float b_frac;   // b_off - floor(b_off), 0 or 1/2
+  int staged;     // single-axis kernel with shared-memory staging of each footprint
 };
 
 cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,

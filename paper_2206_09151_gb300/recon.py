@@ -13,6 +13,7 @@ _FILTERS = {"off": _abi.RECON_FILTER_OFF, "tikhonov": _abi.RECON_FILTER_TIKHONOV
 _INPUTS = {"intensity": _abi.RECON_INPUT_INTENSITY, "contrast": _abi.RECON_INPUT_CONTRAST}
 _STACKS = {"f32": _abi.RECON_STACK_F32, "bf16": _abi.RECON_STACK_BF16}
 _RAMPS = {"single_axis": _abi.RECON_RAMP_SINGLE_AXIS, "density": _abi.RECON_RAMP_DENSITY}
+_BP_KERNELS = {"auto": _abi.RECON_BP_AUTO, "direct": _abi.RECON_BP_DIRECT, "staged": _abi.RECON_BP_STAGED}
 
 
 class Reconstructor:
@@ -26,7 +27,7 @@ class Reconstructor:
                  sigma: float = 0.0, eps: float = 0.1, cs: float = 0.0, filter: str = "tikhonov",
                  input_mode: str = "intensity", stack_dtype: str = "f32", accumulate: bool = False,
                  dir_block: int = 0, ramp: str = "single_axis", mlp_weights=None, nsr: float = 0.0,
-                 stage_block: int = 0, device=None, allocate: bool = True):
+                 stage_block: int = 0, bp_kernel: str = "auto", device=None, allocate: bool = True):
         o = _abi.recon_default_options()
         o.sigma, o.eps, o.cs = float(sigma), float(eps), float(cs)
         o.filter, o.input_mode, o.stack_dtype = _FILTERS[filter], _INPUTS[input_mode], _STACKS[stack_dtype]
@@ -34,6 +35,7 @@ class Reconstructor:
         o.ramp_mode = _RAMPS[ramp]
         o.nsr = float(nsr)
         o.stage_block = int(stage_block)
+        o.bp_kernel = _BP_KERNELS[bp_kernel]
         self._weights = None
         if mlp_weights is not None:
             self._weights = np.ascontiguousarray(mlp_weights, dtype=np.float32)

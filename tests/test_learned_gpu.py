@@ -117,3 +117,24 @@ def test_training_gains_over_the_fixed_tikhonov_eps():
     mean = {k: float(np.mean(v)) for k, v in errs.items()}
     print("held-out rel-L2 to the phantoms:", mean, "training loss", float(loss[0]), "->", float(loss[-1]))
     assert mean["learned"] < 0.95 * mean["eps=0.1"]
+
+
+def test_training_does_not_depend_on_the_workspace_contents():
+    """Adam's moments and the gradient accumulators start from zero whatever the workspace
+    held: a few steps on a workspace that held NaN bytes give the losses of one that held
+    zeros (up to the order of the float atomics)."""
+    from paper_2206_09151_gb300.recon import train_mlp
+    n, nzl = 32, 2
+    img, tgt, rot, R, grid = _train_set(2, 2, n, nzl, seed=21, photons=1e4)
+    w = _weights(22).astype(np.float32)
+    out = {}
+    for fill in (0x00, 0xFF):  # 0xFF bytes are NaNs in float32
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+        junk = torch.full((64 << 20,), fill, dtype=torch.uint8, device="cuda")
+        del junk  # the caching allocator hands these bytes to the training workspace
+        _, loss, _ = train_mlp(w, torch.from_numpy(img).cuda(), torch.from_numpy(tgt).cuda(), rot, R, grid,
+                               nz_layers=nzl, nsr=1e-2, steps=5, lr=1e-3, **PHYS)
+        out[fill] = np.asarray(loss, np.float64)
+    assert np.all(np.isfinite(out[0xFF])), out[0xFF]
+    np.testing.assert_allclose(out[0xFF], out[0x00], rtol=1e-5)

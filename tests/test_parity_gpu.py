@@ -82,10 +82,11 @@ def test_stage_a_layer_stack_matches_oracle(case):
 
 
 # ---------------------------------------------------------------- stage B
-def _stage_b_case(grid, nu, nv, nzl, D, seed, start=0.1, span=math.pi, axis=None):
+def _stage_b_case(grid, nu, nv, nzl, D, seed, start=0.1, span=math.pi, axis=None, bp_kernel="auto"):
     rng = np.random.default_rng(seed)
     rot = ph.single_axis_rotations(D, span=span, start=start, axis=axis)
-    r = make(rot, nu, nv, grid, lam=1e-10, delta=1e-9, defocus=np.zeros(D), nz_layers=nzl, dir_block=D)
+    r = make(rot, nu, nv, grid, lam=1e-10, delta=1e-9, defocus=np.zeros(D), nz_layers=nzl, dir_block=D,
+             bp_kernel=bp_kernel)
     stacks = rng.standard_normal((D, nzl, nv, nu)).astype(np.float32)
     padded = np.zeros((D, nzl, nv + 2, nu + 2), np.float32)
     padded[:, :, 1:-1, 1:-1] = stacks
@@ -113,9 +114,12 @@ def _stage_b_case(grid, nu, nv, nzl, D, seed, start=0.1, span=math.pi, axis=None
     ((1, 1, 1), 1, 1, 1, 2, None),
     ((37, 20, 9), 41, 23, 5, 7, (0.3, 1.0, -0.2)),   # tilted axis: general kernel
     ((48, 40, 56), 64, 64, 6, 30, (0.0, 1.0, 0.5)),
-], ids=["y-half", "y-64", "y-tall", "y-rows-outside", "y-rows-outside-half", "y-1", "tilted", "tilted-2"])
-def test_stage_b_backprojection_matches_oracle(grid, nu, nv, nzl, D, axis):
-    got, ref = _stage_b_case(grid, nu, nv, nzl, D, seed=sum(grid) + D, axis=axis)
+    ((64, 64, 64), 64, 64, 96, 12, None),       # thin layers: staged boxes overflow to direct loads
+], ids=["y-half", "y-64", "y-tall", "y-rows-outside", "y-rows-outside-half", "y-1", "tilted", "tilted-2",
+        "y-thin-layers"])
+@pytest.mark.parametrize("bp_kernel", ["direct", "staged"])
+def test_stage_b_backprojection_matches_oracle(grid, nu, nv, nzl, D, axis, bp_kernel):
+    got, ref = _stage_b_case(grid, nu, nv, nzl, D, seed=sum(grid) + D, axis=axis, bp_kernel=bp_kernel)
     assert rel_l2(got, ref) <= TOL_F32
     # any layer or tap decided differently would show as an O(1) error at that voxel
     assert np.max(np.abs(got - ref)) <= 1e-4 * max(np.max(np.abs(ref)), 1.0)
@@ -164,6 +168,16 @@ def test_small_workload_bf16_stack(small):
     cfg, img, ref = small
     got = _gpu_recon(cfg, img, stack_dtype="bf16")
     assert rel_l2(got, ref) <= TOL_BF16, rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("stack_dtype", ["f32", "bf16"])
+def test_small_workload_staged_backprojection_equals_direct(small, stack_dtype):
+    """Both single-axis kernels gather the same taps and add in the same order: the
+    staged one (footprints copied to shared memory) gives the direct one's bits."""
+    cfg, img, ref = small
+    a = _gpu_recon(cfg, img, stack_dtype=stack_dtype, bp_kernel="direct")
+    b = _gpu_recon(cfg, img, stack_dtype=stack_dtype, bp_kernel="staged")
+    assert np.array_equal(a, b)
 
 
 def test_accumulate_adds_and_empty_scan_clears():
