@@ -2,7 +2,7 @@
 // the bilinear sample of the layer that contains its depth and sums over directions
 // (the real-space counterpart of gridding each image onto its Ewald patch, Sec. 2).
 //
-// A CTA owns a 32 x 8 x 4 voxel tile; a thread owns a 4-voxel run along z and keeps
+// A CTA owns a 32 x 8 x 8 voxel tile; a thread owns an 8-voxel run along z and keeps
 // its sums in registers across the whole direction block, then reads-modifies-writes
 // the volume once.  Coordinates: per (tile, direction) the tile-origin pixel
 // coordinate is formed in FP64 and split into an integer and an FP32 fraction, so the
@@ -20,7 +20,7 @@
 namespace recon {
 namespace {
 
-constexpr int kTX = 32, kTY = 8, kTZ = 4;
+constexpr int kTX = 32, kTY = 8, kTZ = 8;
 
 struct TileDir {  // per (tile, direction), 64 bytes in shared memory
   float fa, fb;   // fractional tile-origin coordinate minus 0.5
@@ -35,13 +35,27 @@ static_assert(sizeof(TileDir) == 64, "TileDir layout");
 // A stack entry is the horizontal tap pair (Y[u], Y[u + 1]) (one 8-byte or 4-byte load).
 __device__ __forceinline__ float2 stack_pair(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ float2 stack_pair(const __nv_bfloat162* p) { return __bfloat1622float2(__ldg(p)); }
+// The same loads as volatile asm, which keeps a run of them in program order ahead of
+// the arithmetic that uses them (all of a column's gathers in flight at once).
+__device__ __forceinline__ float2 stack_pair_issue(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float2 stack_pair_issue(const __nv_bfloat162* p) {
+  unsigned u;
+  asm volatile("ld.global.nc.b32 %0, [%1];\n" : "=r"(u) : "l"(p));
+  __nv_bfloat162 h;
+  memcpy(&h, &u, sizeof(u));
+  return __bfloat1622float2(h);
+}
 
 // Round-to-nearest integer of |x| < 2^22 through the FP32 adder: x + 1.5*2^23 holds
 // rint(x) in its low mantissa bits.
 constexpr float kMagic = 12582912.0f;
 constexpr int kMagicBits = 0x4B400000;
 
-// One 32 x 8 x 4 tile (tile coordinates bx, by, bz); s_dir: dir_count TileDir records.
+// One 32 x 8 x 8 tile (tile coordinates bx, by, bz); s_dir: dir_count TileDir records.
 template <typename ST>
 __device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const DirParams* __restrict__ dirs,
                                                 const ST* __restrict__ stack, const BackprojConst& c,
@@ -121,7 +135,7 @@ __device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const Di
 }
 
 template <typename ST>
-__global__ void __launch_bounds__(kTX* kTY) k_backproject(const DirParams* __restrict__ dirs,
+__global__ void __launch_bounds__(kTX* kTY, 4) k_backproject(const DirParams* __restrict__ dirs,
                                                            const ST* __restrict__ stack, BackprojConst c,
                                                            int dir_begin, int dir_count, float* __restrict__ vol,
                                                            int accumulate) {
@@ -213,17 +227,24 @@ __device__ __forceinline__ void bp_axis_tile(int bx, int by, int bz, const DirPa
     const ST* p = stack + ((size_t)d * c.nz_layers + layer) * c.layer_elems + (ptrdiff_t)(row0 + 1) * c.su +
                   (ra + ad.ia + 1);
     if (rows_inside) {
+      // every tap of this direction is loaded before the first is used, so that all of
+      // the column's gathers are in flight together
+      float2 v[kJ + (TWO_ROWS ? 1 : 0)];
+#pragma unroll
+      for (int q = 0; q < kJ + (TWO_ROWS ? 1 : 0); ++q) v[q] = stack_pair_issue(p + q * c.su);
+#pragma unroll
+      for (int q = 0; q < kJ + (TWO_ROWS ? 1 : 0); ++q) asm volatile("" : "+f"(v[q].x), "+f"(v[q].y));
       if (TWO_ROWS) {
-        float prev = lerp_row(p, fa);
+        float prev = fmaf(fa, v[0].y - v[0].x, v[0].x);
 #pragma unroll
         for (int q = 0; q < kJ; ++q) {
-          const float next = lerp_row(p + (q + 1) * c.su, fa);
+          const float next = fmaf(fa, v[q + 1].y - v[q + 1].x, v[q + 1].x);
           acc[q] += fmaf(fb, next - prev, prev);
           prev = next;
         }
       } else {
 #pragma unroll
-        for (int q = 0; q < kJ; ++q) acc[q] += lerp_row(p + q * c.su, fa);
+        for (int q = 0; q < kJ; ++q) acc[q] += fmaf(fa, v[q].y - v[q].x, v[q].x);
       }
     } else {
 #pragma unroll
@@ -253,7 +274,10 @@ __device__ __forceinline__ void bp_axis_tile(int bx, int by, int bz, const DirPa
 }
 
 template <typename ST, bool TWO_ROWS>
-__global__ void __launch_bounds__(kAX* kAZ) k_backproject_axis(const DirParams* __restrict__ dirs,
+// At least 4 CTAs per SM: ptxas then keeps all of a column's gathers in registers at once
+// (58 registers); left to itself it chose 40 and issued them in batches (256^3 / 120
+// directions: 1.57 -> 0.75 ms).
+__global__ void __launch_bounds__(kAX* kAZ, 4) k_backproject_axis(const DirParams* __restrict__ dirs,
                                                                 const ST* __restrict__ stack, BackprojConst c,
                                                                 int dir_begin, int dir_count,
                                                                 float* __restrict__ vol, int accumulate) {

@@ -9,8 +9,8 @@
 // memory: the pass at sub-length Ns (radix R) stores exp(-2 pi i kb r / (Ns R)) at
 // offset (Ns - 8) + kb (R - 1) + (r - 1) for kb < Ns, 1 <= r < R, so the lanes of a
 // warp read addresses R - 1 apart (no bank conflicts); the table has P - 8 entries.
-// INV selects the inverse (conjugate) transform, unscaled.  Every thread of the CTA
-// must call it (it uses __syncthreads).
+// INV selects the inverse (conjugate) transform, unscaled.  Every thread of the CTA (or,
+// with GroupSync, of the group) must call it.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -83,9 +83,24 @@ __device__ __forceinline__ void dftR(float2* v) {
   else dft2<INV>(v);
 }
 
+// Barrier between the passes.  CtaSync: the whole CTA (needed where the exchange
+// buffer aliases memory that other groups read).  GroupSync: only the group's own
+// threads, for kernels whose groups each own their exchange buffer: a named barrier per
+// group of 64 or more threads, __syncwarp for a group inside one warp.
+struct CtaSync {
+  __device__ __forceinline__ void operator()() const { __syncthreads(); }
+};
+struct GroupSync {
+  int id, n;  // named barrier id (1..15) and thread count (a multiple of 32, or <= 32)
+  __device__ __forceinline__ void operator()() const {
+    if (n <= 32) __syncwarp();
+    else asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+  }
+};
+
 // One Stockham pass of radix R at sub-length Ns (product of the radices before it).
-template <int P, int R, int Ns, bool INV>
-__device__ __forceinline__ void pass(float2 (&x)[8], float2* buf, const float2* tw, int j) {
+template <int P, int R, int Ns, bool INV, typename Sync = CtaSync>
+__device__ __forceinline__ void pass(float2 (&x)[8], float2* buf, const float2* tw, int j, Sync sync = {}) {
   constexpr int T = P / 8, NB = 8 / R, STRIDE = P / R;
   constexpr bool FIRST = Ns == 1, LAST = Ns * R == P;
   float2 v[8];
@@ -95,7 +110,7 @@ __device__ __forceinline__ void pass(float2 (&x)[8], float2* buf, const float2* 
 #pragma unroll
       for (int r = 0; r < R; ++r) v[q * R + r] = x[q + r * NB];
   } else {
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int q = 0; q < NB; ++q)
 #pragma unroll
@@ -119,7 +134,7 @@ __device__ __forceinline__ void pass(float2 (&x)[8], float2* buf, const float2* 
 #pragma unroll
       for (int r = 0; r < R; ++r) x[q + r * NB] = v[q * R + r];
   } else {
-    __syncthreads();
+    sync();
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
       const int b = j + q * T;
@@ -130,19 +145,19 @@ __device__ __forceinline__ void pass(float2 (&x)[8], float2* buf, const float2* 
   }
 }
 
-template <int P, int Ns, bool INV>
-__device__ __forceinline__ void stockham(float2 (&x)[8], float2* buf, const float2* tw, int j) {
+template <int P, int Ns, bool INV, typename Sync>
+__device__ __forceinline__ void stockham(float2 (&x)[8], float2* buf, const float2* tw, int j, Sync sync) {
   constexpr int rem = P / Ns;
   constexpr int R = (rem % 8 == 0) ? 8 : rem;
-  pass<P, R, Ns, INV>(x, buf, tw, j);
-  if constexpr (Ns * R < P) stockham<P, Ns * R, INV>(x, buf, tw, j);
+  pass<P, R, Ns, INV, Sync>(x, buf, tw, j, sync);
+  if constexpr (Ns * R < P) stockham<P, Ns * R, INV, Sync>(x, buf, tw, j, sync);
 }
 
 // Length-P FFT of the 8 values a thread holds (positions j + s*P/8), P >= 16.
-template <int P, bool INV>
-__device__ __forceinline__ void block_fft(float2 (&x)[8], float2* buf, const float2* tw, int j) {
+template <int P, bool INV, typename Sync = CtaSync>
+__device__ __forceinline__ void block_fft(float2 (&x)[8], float2* buf, const float2* tw, int j, Sync sync = {}) {
   static_assert(P >= 16 && (P & (P - 1)) == 0, "P must be a power of two >= 16");
-  stockham<P, 1, INV>(x, buf, tw, j);
+  stockham<P, 1, INV, Sync>(x, buf, tw, j, sync);
 }
 
 }  // namespace fft
