@@ -45,7 +45,15 @@ WORKLOAD_TEXT = {
 
 # DRAM traffic per launch (bytes) from ncu captures, keyed by kernel and workload and
 # valid only for the kernel source they were taken on (sha256 of the .cu file).
-NCU_TRAFFIC: dict = {}
+# Taken from a --set full capture of one 40-direction launch, scaled by 120/40 to the
+# bench's 120-direction blocks. The stack read grows in proportion; the backprojection's
+# volume read-modify-write does not, and its figure overstates that part.
+NCU_TRAFFIC: dict = {
+    ("k_cols", "mid", "f32"): {"bytes_per_launch": (21.154048e6 + 612.350464e6) * 3, "src": "3d702c4e22709be4"},
+    ("k_cols", "mid", "bf16"): {"bytes_per_launch": (21.154048e6 + 612.350464e6) * 3, "src": "3d702c4e22709be4"},
+    ("k_rows_inv", "mid", "f32"): {"bytes_per_launch": (673.874688e6 + 634.947584e6) * 3, "src": "3d702c4e22709be4"},
+    ("k_backproject", "mid", "f32"): {"bytes_per_launch": (554.355456e6 + 59.22176e6) * 3, "src": "b781270a4c70acae"},
+}
 
 
 def _src_hash(name: str) -> str:
@@ -234,6 +242,21 @@ def algorithmic_bytes(cfg, r, stack_bytes: int, dir_counts: list[int]) -> list[f
     return out
 
 
+# FP32 peak of the column-filter kernel's roofline: 152 SMs x 128 FP32 lanes x 2 flops (FMA)
+# x 2070 MHz maximum SM clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+
+
+def cols_flops(cfg, r, dir_counts: list[int]) -> float:
+    """FP32 work of the column kernel per run: a length-P complex FFT counted as
+    5 P log2 P flops, one forward and Nz inverse transforms per half-spectrum column,
+    and the real per-layer filter applied to every complex coefficient (2 flops)."""
+    P, nzl = r.padded, cfg["nz_layers"]
+    half = P // 2 + 1
+    fft = 5.0 * P * math.log2(P)
+    return float(sum(dir_counts)) * half * ((1 + nzl) * fft + nzl * 2.0 * P)
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -340,22 +363,42 @@ def run_ours(args):
     for q, name in enumerate(KERNELS):
         per_launch_ms = kern_ms[q] / max(kern_n[q], 1)
         gbs = algo[q] / (kern_ms[q] / args.steps / 1e3) / 1e9 if kern_ms[q] > 0 else None
+        tr = NCU_TRAFFIC.get((name, args.workload, args.stack))
+        src = "backproject.cu" if q == 3 else "stage_a.cu"
         kernels[name] = {"launches": kern_n[q], "ms_per_launch": per_launch_ms,
-                         "share": kern_ms[q] / max(sum(kern_ms), 1e-12), "algorithmic_GBps": gbs}
+                         "share": kern_ms[q] / max(sum(kern_ms), 1e-12), "algorithmic_GBps": gbs,
+                         "algorithmic_bytes_per_launch": algo[q] * args.steps / max(kern_n[q], 1),
+                         "ncu_dram_bytes_per_launch": tr["bytes_per_launch"] if tr and tr["src"] == _src_hash(src)
+                         else None}
+    flops = cols_flops(cfg, r, counts)
+    kernels["k_cols"]["algorithmic_TFLOPs"] = (flops / (kern_ms[1] / args.steps / 1e3) / 1e12
+                                               if kern_ms[1] > 0 else None)
     dom = max(range(4), key=lambda q: kern_ms[q])
     dom_name = KERNELS[dom]
-    # bytes of all launches over their summed time (a launch is a block or a sub-block)
-    achieved = algo[dom] * args.steps / (kern_ms[dom] / 1e3) / 1e9
     src = "backproject.cu" if dom == 3 else "stage_a.cu"
     key = (dom_name, args.workload, args.stack)
     tr = NCU_TRAFFIC.get(key)
     traffic = tr["bytes_per_launch"] if tr and tr["src"] == _src_hash(src) else None
-    roofline = {"kernel": dom_name, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else
-                "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": algo[dom] * args.steps / max(kern_n[dom], 1),
-                "launches": kern_n[dom], "ms_per_launch": kern_ms[dom] / max(kern_n[dom], 1),
-                "units_per_launch": (V * D if dom == 3 else D) * args.steps / max(kern_n[dom], 1)}
+    launches = max(kern_n[dom], 1)
+    common = {"kernel": dom_name, "traffic": traffic,
+              "algorithmic_bytes_per_launch": algo[dom] * args.steps / launches, "launches": kern_n[dom],
+              "ms_per_launch": kern_ms[dom] / launches,
+              "units_per_launch": (V * D if dom == 3 else D) * args.steps / launches}
+    if dom == 1:
+        # the column kernel is bound by FP32 arithmetic (FFTs and the per-layer filter):
+        # its flops over its summed launch time, against the FP32 peak of the SM count and clock
+        achieved = flops * args.steps / (kern_ms[dom] / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": achieved / FP32_PEAK_TFLOPS,
+                    "peak_source": "FP32: 152 SMs x 128 lanes x 2 flops x 2070 MHz",
+                    "algorithmic_flops_per_launch": flops * args.steps / launches, **common}
+    else:
+        # bytes of all launches over their summed time (a launch is a block or a sub-block)
+        achieved = algo[dom] * args.steps / (kern_ms[dom] / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"],
+                    "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)" if peak_src == "measured" else
+                    "fallback 6.8 TB/s", **common}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",

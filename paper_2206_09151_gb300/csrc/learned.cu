@@ -20,7 +20,6 @@
 #include "fft_reg.cuh"
 #include "learned.cuh"
 #include "recon_internal.h"
-#include "sinpi_poly.h"
 
 namespace recon {
 namespace {
@@ -47,18 +46,13 @@ __device__ __forceinline__ int radial_bin(const LearnConst& lc, uint32_t msq) {
 
 __device__ __forceinline__ float softplus(float o) { return o > 20.f ? o : log1pf(expf(o)); }
 
+// sin(pi t) for t = hi * 2^-31 in [-1, 1) (hi: the top 32 bits of chi / (2 pi) in
+// fixed point, so chi = pi t is already reduced to [-pi, pi) exactly by the integer
+// phase).  The hardware sine (__sinf, maximum absolute error 2^-21.4 on [-pi, pi])
+// measured faster than an odd polynomial after a quadrant fold, at 5.7e-7 instead of
+// 5.2e-7 rel-L2 against the FP64 oracle on the 256^3 / 360-view scan.
 __device__ __forceinline__ float sin_half_turns(int32_t hi) {
-  const bool fold = (uint32_t)hi + 0x40000000u > 0x80000000u;
-  const int32_t u = fold ? (int32_t)(0x80000000u - (uint32_t)hi) : hi;
-  const float z = (float)u * 9.313225746154785e-10f;
-  const float z2 = z * z;
-  float p = RECON_SINPI_C5;
-  p = fmaf(p, z2, RECON_SINPI_C4);
-  p = fmaf(p, z2, RECON_SINPI_C3);
-  p = fmaf(p, z2, RECON_SINPI_C2);
-  p = fmaf(p, z2, RECON_SINPI_C1);
-  p = fmaf(p, z2, RECON_SINPI_C0);
-  return p * z;
+  return __sinf((float)hi * 1.4629180792671596e-09f);  // hi * 2 pi / 2^32
 }
 
 // ----------------------------------------------------------------- column forward FFT

@@ -19,7 +19,6 @@
 #include "density.cuh"
 #include "fft_reg.cuh"
 #include "recon_internal.h"
-#include "sinpi_poly.h"
 
 namespace recon {
 namespace {
@@ -49,21 +48,12 @@ __device__ __forceinline__ float sin_from_turns(uint64_t x) {
 }
 
 // sin(pi t) for t = hi * 2^-31 in [-1, 1) (hi: the top 32 bits of chi / (2 pi) in
-// fixed point).  The fold sin(pi t) = sin(pi (+-1 - t)) is exact integer arithmetic and
-// brings t into [-1/2, 1/2]; then z = 2t in [-1, 1] goes through the odd polynomial
-// z * p(z^2) ~ sin(pi z / 2) of sinpi_poly.h (least-squares fit, max error 1.7e-7).
+// fixed point, so chi = pi t is already reduced to [-pi, pi) exactly by the integer
+// phase).  The hardware sine (__sinf, maximum absolute error 2^-21.4 on [-pi, pi])
+// measured faster than an odd polynomial after a quadrant fold, at 5.7e-7 instead of
+// 5.2e-7 rel-L2 against the FP64 oracle on the 256^3 / 360-view scan.
 __device__ __forceinline__ float sin_half_turns(int32_t hi) {
-  const bool fold = (uint32_t)hi + 0x40000000u > 0x80000000u;  // |t| > 1/2
-  const int32_t u = fold ? (int32_t)(0x80000000u - (uint32_t)hi) : hi;
-  const float z = (float)u * 9.313225746154785e-10f;  // u * 2^-30
-  const float z2 = z * z;
-  float p = RECON_SINPI_C5;
-  p = fmaf(p, z2, RECON_SINPI_C4);
-  p = fmaf(p, z2, RECON_SINPI_C3);
-  p = fmaf(p, z2, RECON_SINPI_C2);
-  p = fmaf(p, z2, RECON_SINPI_C1);
-  p = fmaf(p, z2, RECON_SINPI_C0);
-  return p * z;
+  return __sinf((float)hi * 1.4629180792671596e-09f);  // hi * 2 pi / 2^32
 }
 
 // The stack stores horizontal tap pairs: entry (row v + 1, column c) of a layer holds
