@@ -14,6 +14,7 @@ Every definition here is shared, in meaning, with the CUDA path; the code is not
 """
 from __future__ import annotations
 
+import functools
 import math
 
 import numpy as np
@@ -34,13 +35,17 @@ def n_bins(P: int) -> int:
     return math.isqrt(P * P // 2) // bin_width(P) + 1
 
 
+@functools.lru_cache(maxsize=8)
 def radial_bin(P: int) -> np.ndarray:
     """Bin of every frequency of the P x P DFT grid: floor(isqrt(m_u^2 + m_v^2) / w),
-    exact integer arithmetic (so every implementation bins identically)."""
+    exact integer arithmetic (so every implementation bins identically).  Cached per P;
+    the array is read-only."""
     m = R.signed_freq(P).astype(np.int64)
     msq = m[:, None] ** 2 + m[None, :] ** 2
     r = np.array([math.isqrt(int(x)) for x in msq.ravel()]).reshape(msq.shape)
-    return np.minimum(r // bin_width(P), n_bins(P) - 1)
+    out = np.minimum(r // bin_width(P), n_bins(P) - 1)
+    out.setflags(write=False)
+    return out
 
 
 def radial_snr(G: np.ndarray, nsr: float, n_pix: int) -> np.ndarray:
@@ -141,36 +146,62 @@ def learned_filter(P, delta, lam, r_eff, sigma, eps_bins, cs=0.0):
     return lam / (4.0 * math.pi * math.sqrt(1.0 + sigma * sigma)) * s / (s * s + eps), s
 
 
-def recon_learned(images, rot, theta, *, lam, delta, defocus, nz_layers, grid, sigma, nsr, cs=0.0,
-                  input_mode=R.INPUT_INTENSITY, voxels=None):
-    """The whole operator with the learned regulariser (single-axis ramp)."""
-    images = np.asarray(images)
-    rot = np.asarray(rot, np.float64)
+def _partial_learned(args):
+    """Sum over directions ``dirs`` of their learned-filter contributions to voxels (i, j, k)."""
+    (images, rot, dirs, theta, lam, delta, defocus, nz_layers, grid, sigma, nsr, cs, input_mode, i, j, k,
+     density) = args
     D, nv, nu = images.shape
     P = R.padded_size(max(nu, nv))
+    A, B = R.pixel_coefficients(rot, grid, nu, nv)
+    T = R.layer_constants(rot, grid, nz_layers)
+    zc = R.layer_centres(rot, grid, nz_layers, delta)
+    dens = R.density_weights(rot, P, delta, dirs) if density else None
+    ramp = R.ramp_weights(P, delta, D)[None, :]
+    ou, ov = (P - nu) // 2, (P - nv) // 2
+    acc = np.zeros(i.shape)
+    for o, n in enumerate(dirs):
+        r_eff = float(defocus[n]) - zc[n]
+        eps = eps_table(theta, images[n], r_eff=r_eff, lam=lam, delta=delta, nsr=nsr, input_mode=input_mode)
+        g = np.zeros((P, P))
+        g[ov:ov + nv, ou:ou + nu] = R.contrast(images[n], input_mode)
+        G = np.fft.fft2(g)
+        W = ramp if dens is None else dens[o]
+        st = np.empty((nz_layers, nv, nu))
+        for kk_ in range(nz_layers):
+            H, _ = learned_filter(P, delta, lam, r_eff[kk_], sigma, eps[kk_], cs)
+            st[kk_] = np.fft.ifft2(G * H * W).real[ov:ov + nv, ou:ou + nu]
+        acc += R.backproject_direction(st, A[n], B[n], T[n], i, j, k)
+    return acc
+
+
+def recon_learned(images, rot, theta, *, lam, delta, defocus, nz_layers, grid, sigma, nsr, cs=0.0,
+                  input_mode=R.INPUT_INTENSITY, voxels=None, workers: int = 1, density: bool = False):
+    """The whole operator with the learned regulariser: the single-axis ramp, or the
+    sampling-density weighting of an arbitrary scan (``density``).  ``voxels`` = (i, j, k)
+    returns those voxels only; ``workers`` > 1 splits the directions over a spawned
+    process pool (the same arithmetic, summed in another order)."""
+    images = np.asarray(images)
+    rot = np.asarray(rot, np.float64)
+    theta = np.asarray(theta, np.float64)
+    D = images.shape[0]
     nx, ny, nz = grid
     if voxels is None:
         kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
         i, j, k = ii.ravel(), jj.ravel(), kk.ravel()
     else:
         i, j, k = (np.asarray(x, np.int64) for x in voxels)
-    A, B = R.pixel_coefficients(rot, grid, nu, nv)
-    T = R.layer_constants(rot, grid, nz_layers)
-    zc = R.layer_centres(rot, grid, nz_layers, delta)
-    W = R.ramp_weights(P, delta, D)[None, :]
-    acc = np.zeros(i.shape)
-    for n in range(D):
-        r_eff = float(defocus[n]) - zc[n]
-        eps = eps_table(theta, images[n], r_eff=r_eff, lam=lam, delta=delta, nsr=nsr, input_mode=input_mode)
-        g = np.zeros((P, P))
-        ou, ov = (P - nu) // 2, (P - nv) // 2
-        g[ov:ov + nv, ou:ou + nu] = R.contrast(images[n], input_mode)
-        G = np.fft.fft2(g)
-        st = np.empty((nz_layers, nv, nu))
-        for kk_ in range(nz_layers):
-            H, _ = learned_filter(P, delta, lam, r_eff[kk_], sigma, eps[kk_], cs)
-            st[kk_] = np.fft.ifft2(G * H * W).real[ov:ov + nv, ou:ou + nu]
-        acc += R.backproject_direction(st, A[n], B[n], T[n], i, j, k)
+    common = (theta, lam, delta, np.asarray(defocus, np.float64), nz_layers, tuple(grid), sigma, nsr, cs, input_mode,
+              i, j, k, density)
+    dirs = list(range(D))
+    if workers <= 1 or D < 2:
+        acc = _partial_learned((images, rot, dirs) + common)
+    else:
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        groups = [dirs[w::workers] for w in range(workers) if dirs[w::workers]]
+        with ProcessPoolExecutor(max_workers=len(groups), mp_context=mp.get_context("spawn")) as ex:
+            parts = list(ex.map(_partial_learned, [(images, rot, g) + common for g in groups]))
+        acc = np.sum(parts, axis=0)
     return acc.reshape(nz, ny, nx) if voxels is None else acc
 
 

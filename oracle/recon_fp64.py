@@ -200,8 +200,10 @@ def density_ball_count(Gh: int) -> tuple[np.ndarray, int]:
     return mask, int(mask.sum())
 
 
-def density_weights(rot: np.ndarray, P: int, delta: float) -> np.ndarray:
+def density_weights(rot: np.ndarray, P: int, delta: float, dirs=None) -> np.ndarray:
     """W_n(q) = g / (S(m_u u_n + m_v v_n) + eps_S) on each direction's P x P DFT grid
+    (for the directions ``dirs`` only when given, in that order; S is always the density of
+    every direction of ``rot``)
     (Sec. 2: the regularised inverse S_eps^-1 of the sampling matrix replaces the 1/n_q of
     Eq. 11).  S is interpolated trilinearly; g = s^3 / (P delta) turns sample counts into
     the density of slices per unit frequency, so that a 180-degree single-axis scan gives
@@ -216,7 +218,8 @@ def density_weights(rot: np.ndarray, P: int, delta: float) -> np.ndarray:
     g = s ** 3 / (P * delta)
     m = signed_freq(P).astype(np.float64)
     mv, mu = np.meshgrid(m, m, indexing="ij")  # [v][u]
-    out = np.empty((rot.shape[0], P, P))
+    dirs = list(range(rot.shape[0])) if dirs is None else list(dirs)
+    out = np.empty((len(dirs), P, P))
     Sf = S.ravel()
 
     def weight(n, a, b):
@@ -238,10 +241,10 @@ def density_weights(rot: np.ndarray, P: int, delta: float) -> np.ndarray:
     # which keeps it even on the DFT grid (a real inverse transform)
     nyq_u = mu == -(P // 2)
     nyq_v = (mv == -(P // 2)) & ~nyq_u
-    for n in range(rot.shape[0]):
+    for o, n in enumerate(dirs):
         w0 = weight(n, mu, mv)
         w1 = weight(n, np.where(nyq_u, -mu, mu), np.where(nyq_v, -mv, mv))
-        out[n] = np.where(nyq_u | nyq_v, 0.5 * (w0 + w1), w0)
+        out[o] = np.where(nyq_u | nyq_v, 0.5 * (w0 + w1), w0)
     return out
 
 
@@ -314,16 +317,16 @@ def _partial_recon(args):
     (images, rot, dirs, lam, delta, defocus, nz_layers, grid, sigma, eps, cs, filt, input_mode, i, j, k,
      n_dir, density) = args
     nu, nv = images.shape[2], images.shape[1]
-    dens = density_weights(rot, padded_size(max(nu, nv)), delta) if density else None
+    dens = density_weights(rot, padded_size(max(nu, nv)), delta, dirs) if density else None
     A, B = pixel_coefficients(rot, grid, nu, nv)
     T = layer_constants(rot, grid, nz_layers)
     zc = layer_centres(rot, grid, nz_layers, delta)
     acc = np.zeros(i.shape)
     chunk = 1 << 21
-    for n in dirs:
+    for o, n in enumerate(dirs):
         st = layer_stack(images[n], delta=delta, lam=lam, r_n=float(defocus[n]), z_layers=zc[n], n_dir=n_dir,
                          sigma=sigma, eps=eps, cs=cs, filt=filt, input_mode=input_mode,
-                         weight=None if dens is None else dens[n])
+                         weight=None if dens is None else dens[o])
         for s0 in range(0, i.size, chunk):
             sl = slice(s0, s0 + chunk)
             acc[sl] += backproject_direction(st, A[n], B[n], T[n], i[sl], j[sl], k[sl])

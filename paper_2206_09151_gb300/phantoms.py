@@ -139,20 +139,25 @@ def ball_phantom(grid, count: int, seed: int, r_range=(2.0, 8.0), delta_range=(1
 
 
 def blob_phantom(grid, count: int, seed: int, s_vox: float, w_range=(1.0, 8.0), amp_unit=1.0,
-                 margin: float = 3.0) -> Phantom:
+                 margin: float = 3.0, region: str = "cylinder") -> Phantom:
     """``count`` Gaussian pseudo-atoms of width ``s_vox`` voxels, weights U[w_range] times
     ``amp_unit`` peak decrement, centres uniform inside the box shrunk by ``margin*s``
-    and inside the y-axis cylinder."""
+    and, for ``region = "cylinder"``, inside the y-axis cylinder (a single-axis scan's
+    field of view); ``region = "box"`` fills the whole shrunk box (a slab)."""
     nx, ny, nz = grid
     rng = np.random.default_rng(seed)
     m = margin * s_vox
-    rc = 0.5 * min(nx, nz) - m
-    cen = np.empty((0, 3))
-    while cen.shape[0] < count:
-        c = np.stack([rng.uniform(-rc, rc, 2 * count), rng.uniform(-(0.5 * ny - m), 0.5 * ny - m, 2 * count),
-                      rng.uniform(-rc, rc, 2 * count)], axis=1)
-        c = c[c[:, 0] ** 2 + c[:, 2] ** 2 <= rc * rc]
-        cen = np.concatenate([cen, c])
+    if region == "box":
+        lo = -0.5 * np.array([nx, ny, nz], np.float64) + m
+        cen = rng.uniform(lo, -lo, (count, 3))
+    else:
+        rc = 0.5 * min(nx, nz) - m
+        cen = np.empty((0, 3))
+        while cen.shape[0] < count:
+            c = np.stack([rng.uniform(-rc, rc, 2 * count), rng.uniform(-(0.5 * ny - m), 0.5 * ny - m, 2 * count),
+                          rng.uniform(-rc, rc, 2 * count)], axis=1)
+            c = c[c[:, 0] ** 2 + c[:, 2] ** 2 <= rc * rc]
+            cen = np.concatenate([cen, c])
     cen = cen[:count]
     w = rng.uniform(w_range[0], w_range[1], count) * amp_unit
     return Phantom("blob", cen, np.full(count, float(s_vox)), w)
@@ -187,33 +192,35 @@ def ball_projections(ph: Phantom, rot: np.ndarray, nu: int, nv: int) -> np.ndarr
 def _slab_projection(ph: Phantom, c_beam: np.ndarray, sel: np.ndarray, P: int, off: int, nu: int, nv: int,
                      device) -> torch.Tensor:
     """Projected decrement (voxel-length units) of the primitives ``sel`` on a P x P grid
-    whose pixel (off + u, off + v) is image pixel (u, v)."""
+    whose pixel (off + u, off + v) is image pixel (u, v).  Evaluated with torch on
+    ``device`` (float64), in chunks of primitives."""
     out = torch.zeros((P, P), dtype=torch.float64, device=device)
     if sel.size == 0:
         return out
-    cu = c_beam[sel, 0] + (nu - 1) / 2.0 + off
-    cv = c_beam[sel, 1] + (nv - 1) / 2.0 + off
-    size = ph.size[sel]
-    amp = ph.amp[sel]
     if ph.kind == "ball":
-        rad = int(math.ceil(float(size.max()))) + 1
+        rad = int(math.ceil(float(ph.size[sel].max()))) + 1
     else:
-        rad = int(math.ceil(4.0 * float(size.max()))) + 1
-    offs = np.arange(-rad, rad + 1)
-    iu = np.floor(cu).astype(np.int64)[:, None, None] + offs[None, None, :]
-    iv = np.floor(cv).astype(np.int64)[:, None, None] + offs[None, :, None]
-    du = iu - cu[:, None, None]
-    dv = iv - cv[:, None, None]
-    rho2 = du * du + dv * dv
-    if ph.kind == "ball":
-        val = 2.0 * amp[:, None, None] * np.sqrt(np.maximum(size[:, None, None] ** 2 - rho2, 0.0))
-    else:
-        s = size[:, None, None]
-        val = amp[:, None, None] * math.sqrt(2.0 * math.pi) * s * np.exp(-rho2 / (2.0 * s * s))
-    iu_b = np.broadcast_to(iu, val.shape) % P
-    iv_b = np.broadcast_to(iv, val.shape) % P
-    flat = torch.as_tensor((iv_b * P + iu_b).reshape(-1), device=device)
-    out.view(-1).index_add_(0, flat, torch.as_tensor(val.reshape(-1), device=device))
+        rad = int(math.ceil(4.0 * float(ph.size[sel].max()))) + 1
+    offs = torch.arange(-rad, rad + 1, device=device, dtype=torch.float64)
+    chunk = max(1, (1 << 22) // (2 * rad + 1) ** 2)
+    for a in range(0, sel.size, chunk):
+        sl = sel[a:a + chunk]
+        cu = torch.as_tensor(c_beam[sl, 0] + (nu - 1) / 2.0 + off, device=device)
+        cv = torch.as_tensor(c_beam[sl, 1] + (nv - 1) / 2.0 + off, device=device)
+        size = torch.as_tensor(ph.size[sl], device=device)[:, None, None]
+        amp = torch.as_tensor(ph.amp[sl], device=device)[:, None, None]
+        iu = torch.floor(cu)[:, None, None] + offs[None, None, :]
+        iv = torch.floor(cv)[:, None, None] + offs[None, :, None]
+        du = iu - cu[:, None, None]
+        dv = iv - cv[:, None, None]
+        rho2 = du * du + dv * dv
+        if ph.kind == "ball":
+            val = 2.0 * amp * torch.sqrt(torch.clamp(size * size - rho2, min=0.0))
+        else:
+            val = amp * math.sqrt(2.0 * math.pi) * size * torch.exp(-rho2 / (2.0 * size * size))
+        iu_b = torch.remainder(iu.expand_as(val).to(torch.int64), P)
+        iv_b = torch.remainder(iv.expand_as(val).to(torch.int64), P)
+        out.view(-1).index_add_(0, (iv_b * P + iu_b).reshape(-1), val.reshape(-1))
     return out
 
 
@@ -320,6 +327,16 @@ def config_workload(name: str, *, scale_dirs: int | None = None):
     256x256 images, lambda = 1.97 pm (300 keV electrons), Nz = 32, defocus 1 um,
     Cs = 2.7 mm, 2e4 Gaussian pseudo-atoms (s = 0.1 nm, weights U[1,8], peak phase
     0.01 rad per unit weight), sigma = 0.07, 100 electrons/pixel.
+
+    ``"learned"``: 512^3, 720 single-axis directions, 512x512 images, Nz = 64, the
+    physics of "mid" with R_n ~ U[0.5, 1.5] um, 1.6e5 pseudo-atoms (the density of "mid").
+
+    ``"slab"``: a 1024 x 1024 x 256 slab of 0.05 nm voxels, 1500 Haar-random directions
+    within 60 deg of its normal, 1024x1024 images, Nz = 64, lambda = 1.97 pm, R = 1 um,
+    Cs = 2.7 mm, 2e5 pseudo-atoms of s = 0.1 nm filling the slab, 50 electrons/pixel,
+    sampling-density weighting (``ramp = "density"``).
+
+    ``scale_dirs`` keeps the first directions only (a scan of its own).
     """
     if name == "small":
         n, D = 64, 90
@@ -332,20 +349,80 @@ def config_workload(name: str, *, scale_dirs: int | None = None):
         cfg = dict(grid=(n, n, n), nu=n, nv=n, n_dir=D, delta=1e-10, lam=1.97e-12, nz_layers=32, sigma=0.07,
                    eps=0.1, cs=2.7e-3, photons=100.0, seed=2001, phantom="blobs", count=20000)
         cfg["defocus"] = np.full(D, 1e-6)
+    elif name == "learned":
+        # 512^3 / 720 views / Nz = 64 in bfloat16, the physics of "mid" with R_n ~ U[0.5, 1.5] um
+        n, D = 512, 720
+        cfg = dict(grid=(n, n, n), nu=n, nv=n, n_dir=D, delta=1e-10, lam=1.97e-12, nz_layers=64, sigma=0.07,
+                   eps=0.1, cs=2.7e-3, photons=100.0, seed=3001, phantom="blobs", count=160000)
+        cfg["defocus"] = np.random.default_rng(cfg["seed"] + 7).uniform(0.5e-6, 1.5e-6, D)
+    elif name == "slab":
+        # 1024 x 1024 x 256 slab, 1500 Haar-random views within 60 deg of its normal, 1024^2
+        # images, 0.05 nm voxels (DOF 0.63 nm against 12.8 nm of thickness), Nz = 64 in bfloat16,
+        # sampling-density weighting, 2e5 pseudo-atoms of s = 0.1 nm in the whole box, 50 e/px
+        D = 1500
+        cfg = dict(grid=(1024, 1024, 256), nu=1024, nv=1024, n_dir=D, delta=5e-11, lam=1.97e-12, nz_layers=64,
+                   sigma=0.07, eps=0.1, cs=2.7e-3, photons=50.0, seed=5001, phantom="blobs", count=200000,
+                   region="box", ramp="density")
+        cfg["defocus"] = np.full(D, 1e-6)
+        cfg["rot"] = cone_rotations(D, 60.0, cfg["seed"] + 11)
     else:
         raise ValueError(name)
+    cfg.setdefault("ramp", "single_axis")
+    if "rot" not in cfg:
+        cfg["rot"] = single_axis_rotations(cfg["n_dir"])
     if scale_dirs is not None:
         cfg["n_dir"] = scale_dirs
         cfg["defocus"] = cfg["defocus"][:scale_dirs]
-    cfg["rot"] = single_axis_rotations(cfg["n_dir"])
+        cfg["rot"] = cfg["rot"][:scale_dirs].copy()
     return cfg
+
+
+def batch_workloads(count: int = 48, seed: int = 4001) -> list:
+    """``count`` uneven tomograms for a batched run: grids n^3 with n ~ U{64, 96, ..., 256}
+    (n x n images), D ~ U[60, 360] single-axis views, Nz ~ U[4, 32]; the phantom alternates
+    between balls and Gaussian blobs and, independently, the physics between the "small"
+    (soft X-ray, 1 nm voxels) and "mid" (300 keV electrons, 0.1 nm voxels, Cs) settings.
+    Each entry has the keys of :func:`config_workload`; images take 4 multislice slabs."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for q in range(count):
+        n = int(rng.choice(np.arange(64, 257, 32)))
+        D = int(rng.integers(60, 361))
+        nzl = int(rng.integers(4, 33))
+        balls = q % 2 == 0
+        electrons = (q // 2) % 2 == 1
+        cfg = dict(grid=(n, n, n), nu=n, nv=n, n_dir=D, nz_layers=nzl, seed=seed + 10 * q, n_slabs=4,
+                   ramp="single_axis", start=float(rng.uniform(0, math.pi)))
+        if electrons:
+            cfg.update(delta=1e-10, lam=1.97e-12, sigma=0.07, eps=0.1, cs=2.7e-3, photons=100.0,
+                       defocus=np.full(D, 1e-6), delta_range=(2e-7, 2e-6))
+        else:
+            cfg.update(delta=1e-9, lam=1e-10, sigma=0.01, eps=1e-2, cs=0.0, photons=1e4,
+                       defocus=rng.uniform(100e-9, 120e-9, D), delta_range=(1e-6, 1e-5))
+        if balls:
+            cfg.update(phantom="balls", count=20)
+        else:
+            cfg.update(phantom="blobs", count=max(200, int(20000 * (n / 256) ** 3)),
+                       s_vox=max(1.0, 1e-10 / cfg["delta"]))
+        cfg["rot"] = single_axis_rotations(D, start=cfg["start"])
+        out.append(cfg)
+    return out
 
 
 def make_phantom(cfg) -> Phantom:
     """The phantom that ``cfg`` (from :func:`config_workload`) names."""
     if cfg["phantom"] == "balls":
-        return ball_phantom(cfg["grid"], cfg["count"], cfg["seed"])
+        return ball_phantom(cfg["grid"], cfg["count"], cfg["seed"], delta_range=cfg.get("delta_range", (1e-6, 1e-5)))
     # peak phase per unit weight 0.01 rad: (2 pi / lam) * amp * sqrt(2 pi) * s * delta = 0.01
-    s = 1e-10 / cfg["delta"]
+    s = cfg.get("s_vox", 1e-10 / cfg["delta"])
     amp = 0.01 * cfg["lam"] / (2 * math.pi * math.sqrt(2 * math.pi) * s * cfg["delta"])
-    return blob_phantom(cfg["grid"], cfg["count"], cfg["seed"], s, amp_unit=amp)
+    return blob_phantom(cfg["grid"], cfg["count"], cfg["seed"], s, amp_unit=amp,
+                        region=cfg.get("region", "cylinder"))
+
+
+def make_images(cfg, device="cpu", dtype=torch.float32) -> torch.Tensor:
+    """Multislice images of :func:`make_phantom` ``(cfg)`` for the scan ``cfg`` names."""
+    phan = make_phantom(cfg)
+    return multislice_images(phan, cfg["rot"], cfg["nu"], cfg["nv"], cfg["delta"], cfg["lam"], cfg["defocus"],
+                             cfg["sigma"], cs=cfg["cs"], photons=cfg["photons"], seed=cfg["seed"], device=device,
+                             dtype=dtype, n_slabs=cfg.get("n_slabs", 16))

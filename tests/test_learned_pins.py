@@ -71,6 +71,24 @@ def test_constant_eps_network_is_the_tikhonov_filter():
     assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
 
 
+def test_constant_eps_network_is_the_tikhonov_filter_with_density_weights():
+    """The same reduction for an arbitrary scan (sampling-density weighting): a constant
+    network is the Tikhonov path, and the spawned process pool sums the same terms."""
+    eps0 = 0.08
+    theta = np.zeros(L.N_PARAMS)
+    theta[-1] = math.log(math.expm1(eps0))
+    rng = np.random.default_rng(16)
+    D, n = 7, 12
+    rot = ph.cone_rotations(D, 60.0, seed=3)
+    img = 1.0 + 1e-3 * rng.standard_normal((D, n, n))
+    kw = dict(lam=1e-10, delta=1e-9, defocus=rng.uniform(50e-9, 60e-9, D), nz_layers=3, grid=(n, 10, 8), sigma=0.05)
+    a = L.recon_learned(img, rot, theta, nsr=1e-2, density=True, **kw)
+    b = O.recon(img, rot, eps=eps0, density=True, **kw)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(b))
+    c = L.recon_learned(img, rot, theta, nsr=1e-2, density=True, workers=2, **kw)
+    assert np.max(np.abs(c - a)) <= 1e-12 * np.max(np.abs(a))
+
+
 def test_white_noise_sits_on_the_parseval_floor():
     """A noise image of variance nsr^2 per pixel has radial power ~ nsr^2 * n_pix per DFT
     coefficient (Parseval), so its estimated SNR is at the floor."""
