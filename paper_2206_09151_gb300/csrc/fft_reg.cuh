@@ -3,9 +3,9 @@
 // Each of the T = P/8 threads of a group holds 8 complex values, element s of thread j
 // being position j + s*T of the sequence, both on input and on output (natural order).
 // The passes use radix 8 while the remaining length allows, then one radix-2 or
-// radix-4 pass; between passes the values go through a padded shared-memory buffer
-// (index i stored at i + i/16, which keeps the 64-bit accesses of a half-warp on
-// distinct banks for these patterns).  Twiddles come from a per-pass table in shared
+// radix-4 pass; between passes the values go through a shared-memory buffer with a
+// swizzled index (padded(): every pass's 64-bit accesses keep each half-warp on 16
+// distinct bank pairs).  Twiddles come from a per-pass table in shared
 // memory: the pass at sub-length Ns (radix R) stores exp(-2 pi i kb r / (Ns R)) at
 // offset (Ns - 8) + kb (R - 1) + (r - 1) for kb < Ns, 1 <= r < R, so the lanes of a
 // warp read addresses R - 1 apart (no bank conflicts); the table has P - 8 entries.
@@ -29,8 +29,14 @@ __device__ __forceinline__ float2 mul_mi(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
 
-__host__ __device__ constexpr int padded(int i) { return i + (i >> 4); }
-__host__ __device__ constexpr int buffer_len(int P) { return P + P / 16 + 1; }
+// Exchange-buffer index of element i: bits 0-3 XORed with bits 3-6, a permutation of
+// every aligned block of 128 (so of [0, P) for P >= 16) under which the 64-bit writes and
+// reads of every pass keep each half-warp on 16 distinct bank pairs.
+__host__ __device__ constexpr int padded(int i) { return i ^ ((i >> 3) & 15); }
+// Stride between the buffers of the `groups` FFT groups of a CTA: P + 16/groups (one
+// entry for 16 or more groups) staggers the groups over the banks, so a fill that writes
+// the groups' columns side by side does not conflict either.
+__host__ __device__ constexpr int buffer_len(int P, int groups) { return P + (groups >= 16 ? 1 : 16 / groups); }
 // entries of the per-pass twiddle table for length P (P >= 16)
 __host__ __device__ constexpr int pass_table_len(int P) { return P - 8; }
 

@@ -60,7 +60,7 @@ template <int P>
 __global__ void __launch_bounds__(kThreads) k_cols_forward(const float2* __restrict__ S, float2* __restrict__ G_out,
                                                             float* __restrict__ pow, const float2* __restrict__ twg,
                                                             StageAConst c, LearnConst lc) {
-  constexpr int TT = P / 8, CB = groups<P>(), L = fft::buffer_len(P), NT = fft::pass_table_len(P);
+  constexpr int TT = P / 8, CB = groups<P>(), L = fft::buffer_len(P, CB), NT = fft::pass_table_len(P);
   __shared__ float2 tw[NT];
   __shared__ float2 buf_all[CB * L];
   __shared__ float hist[kMaxBins];

@@ -73,7 +73,7 @@ template <int P>
 __global__ void __launch_bounds__(kThreads) k_rows_fwd(const float* __restrict__ images, float2* __restrict__ S,
                                                         const float2* __restrict__ twg, StageAConst c,
                                                         int dir_begin) {
-  constexpr int TT = P / 8, G = groups_per_cta<P>(), L = fft::buffer_len(P), NT = fft::pass_table_len(P);
+  constexpr int TT = P / 8, G = groups_per_cta<P>(), L = fft::buffer_len(P, G), NT = fft::pass_table_len(P);
   __shared__ float2 tw[NT];
   __shared__ float2 buf_all[G * L];
   const int g = threadIdx.x / TT, j = threadIdx.x % TT;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_cols(const float2* __restrict__
                                                     const double* __restrict__ band_sum,
                                                     const float* __restrict__ eps_tab, int n_bins, int bin_width,
                                                     StageAConst c, int dir_begin) {
-  constexpr int TT = P / 8, CB = groups_per_cta<P>(), L = fft::buffer_len(P), NT = fft::pass_table_len(P);
+  constexpr int TT = P / 8, CB = groups_per_cta<P>(), L = fft::buffer_len(P, CB), NT = fft::pass_table_len(P);
   __shared__ float2 tw[NT];
   __shared__ float2 buf_all[CB * L];
   const int g = threadIdx.x / TT, j = threadIdx.x % TT;
@@ -234,9 +234,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_cols(const float2* __restrict__
 template <int P, typename PairT>
 __global__ void __launch_bounds__(kThreads) k_rows_inv(const float2* __restrict__ T, PairT* __restrict__ stack,
                                                         const float2* __restrict__ twg, StageAConst c) {
-  constexpr int TT = P / 8, G = groups_per_cta<P>(), L = fft::buffer_len(P), H = P / 2 + 1;
-  constexpr int TILE = 2 * G * H, BUF = G * L, NT = fft::pass_table_len(P);
-  constexpr int FILL = (TILE + kThreads - 1) / kThreads;
+  constexpr int TT = P / 8, G = groups_per_cta<P>(), L = fft::buffer_len(P, G), H = P / 2 + 1;
+  // tile row stride HS = 8/G (mod 16) float2: a half-warp of the coalesced fill below
+  // (2G rows x 8/G consecutive columns) then writes 16 distinct bank pairs; with G >= 8 a
+  // half-warp fills one column and the odd stride H already does
+  constexpr int HS = G >= 8 ? H : H + ((8 / G - H % 16) % 16 + 16) % 16;
+  constexpr int TILE = 2 * G * HS, BUF = G * L, NT = fft::pass_table_len(P);
+  constexpr int USED = 2 * G * H;  // tile entries that hold spectrum values
+  constexpr int FILL = (USED + kThreads - 1) / kThreads;
   __shared__ float2 tw[NT];
   // the half-spectrum tile is read once, before the FFT's first exchange: the
   // exchange buffer reuses its memory
@@ -255,18 +260,18 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(const float2* __restrict_
       const int idx = threadIdx.x + it * kThreads;
       const int vv = idx % (2 * G), cc = idx / (2 * G);
       const int v = vbase + vv;
-      tmp[it] = (idx < TILE && v < c.nv) ? Tk[(size_t)cc * c.nv + v] : make_float2(0.f, 0.f);
+      tmp[it] = (idx < USED && v < c.nv) ? Tk[(size_t)cc * c.nv + v] : make_float2(0.f, 0.f);
     }
 #pragma unroll
     for (int it = 0; it < FILL; ++it) {
       const int idx = threadIdx.x + it * kThreads;
-      if (idx < TILE) tile[(idx % (2 * G)) * H + idx / (2 * G)] = tmp[it];
+      if (idx < USED) tile[(idx % (2 * G)) * HS + idx / (2 * G)] = tmp[it];
     }
   }
   __syncthreads();
   const int v0 = vbase + 2 * g;
-  const float2* X1 = tile + (2 * g) * H;
-  const float2* X2 = X1 + H;
+  const float2* X1 = tile + (2 * g) * HS;
+  const float2* X2 = X1 + HS;
   float2 x[8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
