@@ -41,7 +41,17 @@ WORKLOAD_TEXT = {
     "small": ("small plain method: 64^3 grid (1 nm voxels), 90 single-axis directions over 180 deg, 64x64 "
               "float32 images, lambda 0.1 nm, Nz=8 depth layers, R_n ~ U[100,120] nm, sigma 0.01, eps 0.01; "
               "20 uniform balls (r U[2,8] vox, delta U[1e-6,1e-5]); multislice images, 1e4 photons/px"),
+    "learned": ("learned-filter scan: 512^3 grid (0.1 nm voxels), 720 single-axis directions over 180 deg, "
+                "512x512 float32 images, lambda 1.97 pm, Nz=64 layers, R_n ~ U[0.5,1.5] um, Cs 2.7 mm, sigma "
+                "0.07, eps 0.1; 1.6e5 Gaussian pseudo-atoms; 100 e/px (--filter mlp: seeded network)"),
+    "slab": ("arbitrary geometry, large slab: 1024x1024x256 grid (0.05 nm voxels), 1500 Haar-random directions "
+             "within 60 deg of the slab normal, 1024x1024 float32 images, lambda 1.97 pm, Nz=64 layers, R 1 um, "
+             "Cs 2.7 mm, sampling-density weighting; 2e5 Gaussian pseudo-atoms filling the slab; 50 e/px"),
+    "batch": ("batched: 48 tomograms of uneven sizes (64^3-256^3 grids, 64^2-256^2 images, 60-360 single-axis "
+              "directions, Nz 4-32), balls and blobs, soft X-ray and electron physics, one graph replay"),
 }
+# stack precision each workload is specified with
+DEFAULT_STACK = {"mid": "f32", "small": "f32", "learned": "bf16", "slab": "bf16", "batch": "bf16"}
 
 # DRAM traffic per launch (bytes) from ncu captures, keyed by kernel and workload and
 # valid only for the kernel source they were taken on (sha256 of the .cu file).
@@ -148,18 +158,31 @@ def make_images(cfg, device):
     import torch
 
     from paper_2206_09151_gb300 import phantoms as ph
-    phan = ph.make_phantom(cfg)
-    return ph.multislice_images(phan, cfg["rot"], cfg["nu"], cfg["nv"], cfg["delta"], cfg["lam"], cfg["defocus"],
-                                cfg["sigma"], cs=cfg["cs"], photons=cfg["photons"], seed=cfg["seed"], device=device,
-                                dtype=torch.float32)
+    return ph.make_images(cfg, device=device, dtype=torch.float32)
 
 
-def oracle_sample(cfg, images_np, dirs, mlp=None):
-    """FP64 oracle on the directions ``dirs`` alone (a D = len(dirs) scan), full volume;
-    ``mlp`` = (weights, nsr) selects the learned regulariser."""
+# volumes above this many voxels are compared with the oracle on a random voxel sample
+FULL_VOLUME_LIMIT = 1 << 24
+
+
+def sample_voxels(cfg):
+    """None (the full volume) for volumes up to 2^24 voxels, else 2^18 seeded random voxels."""
+    V = int(np.prod(cfg["grid"]))
+    if V <= FULL_VOLUME_LIMIT:
+        return None
+    rng = np.random.default_rng(cfg["seed"] + 99)
+    nx, ny, nz = cfg["grid"]
+    n = 1 << 18
+    return rng.integers(0, nx, n), rng.integers(0, ny, n), rng.integers(0, nz, n)
+
+
+def oracle_sample(cfg, images_np, dirs, mlp=None, voxels=None):
+    """FP64 oracle on the directions ``dirs`` alone (a D = len(dirs) scan), at ``voxels`` or
+    over the full volume; ``mlp`` = (weights, nsr) selects the learned regulariser."""
     import oracle as O
     kw = dict(lam=cfg["lam"], delta=cfg["delta"], defocus=cfg["defocus"][dirs], nz_layers=cfg["nz_layers"],
-              grid=cfg["grid"], sigma=cfg["sigma"], cs=cfg["cs"])
+              grid=cfg["grid"], sigma=cfg["sigma"], cs=cfg["cs"], voxels=voxels,
+              density=cfg.get("ramp", "single_axis") == "density")
     if mlp is not None:
         return O.learned.recon_learned(images_np[dirs], cfg["rot"][dirs], mlp[0].astype(np.float64), nsr=mlp[1],
                                        **kw)
@@ -172,8 +195,13 @@ def run_reference(args):
     if rank != 0:
         return 0
     import torch
-    cfg = workload(args.workload)
-    V = int(np.prod(cfg["grid"]))
+    if args.workload == "batch":  # the oracle on one member of the batch
+        from paper_2206_09151_gb300 import phantoms as ph
+        cfg = ph.batch_workloads()[0]
+    else:
+        cfg = workload(args.workload)
+    vox = sample_voxels(cfg)
+    V = int(np.prod(cfg["grid"])) if vox is None else vox[0].size
     D = cfg["n_dir"]
     per_step = max(1, args.ref_dirs)
     plan = [[((s * per_step + q) * 97) % D for q in range(per_step)] for s in range(args.warmup + args.steps)]
@@ -184,13 +212,15 @@ def run_reference(args):
     times = []
     for s, dirs in enumerate(plan):
         t0 = time.perf_counter()
-        oracle_sample(cfg, images, dirs)
+        oracle_sample(cfg, images, dirs, voxels=vox)
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt)
     t = sum(times) / len(times)
     value = V * per_step / t
-    sample = f"{per_step} direction(s) per step over the full {cfg['grid'][0]}^3 volume, FP64 numpy, 1 thread"
+    where = "the full volume" if vox is None else f"{V} random voxels"
+    sample = (f"{per_step} direction(s) per step over {where} of the {'x'.join(map(str, cfg['grid']))} grid"
+              + (" (first tomogram of the batch)" if args.workload == "batch" else "") + ", FP64 numpy, 1 thread")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -293,7 +323,7 @@ def run_ours(args):
     r = Reconstructor(cfg["rot"], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
                       defocus=cfg["defocus"], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"], eps=cfg["eps"],
                       cs=cfg["cs"], stack_dtype=args.stack, dir_block=args.dir_block, stage_block=args.stage_block,
-                      bp_kernel=args.bp_kernel, device=dev, **filt_kw)
+                      bp_kernel=args.bp_kernel, ramp=cfg["ramp"], device=dev, **filt_kw)
     vol = r.new_volume()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -418,23 +448,137 @@ def run_ours(args):
         # sample reconstructed on the GPU: the stated accuracy and the CPU rate
         sel = [int(x) for x in np.linspace(0, D - 1, args.cpu_dirs).round()]
         img_np = images.cpu().numpy()
+        vox = sample_voxels(cfg)
         t0 = time.perf_counter()
-        ref = oracle_sample(cfg, img_np, sel, mlp)
+        ref = oracle_sample(cfg, img_np, sel, mlp, vox)
         dt = time.perf_counter() - t0
         rs = Reconstructor(cfg["rot"][sel], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
                            defocus=cfg["defocus"][sel], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"],
-                           eps=cfg["eps"], cs=cfg["cs"], stack_dtype=args.stack, device=dev, **filt_kw)
-        got = rs.run(images[sel].contiguous()).cpu().numpy()
+                           eps=cfg["eps"], cs=cfg["cs"], stack_dtype=args.stack, ramp=cfg["ramp"], device=dev,
+                           **filt_kw)
+        got = rs.run(images[sel].contiguous())
         rs.close()
+        if vox is None:
+            got = got.cpu().numpy()
+            n_vox, where = V, "the full volume"
+        else:
+            got = got[tuple(torch.as_tensor(x, device=dev) for x in vox[::-1])].cpu().numpy()
+            n_vox, where = vox[0].size, f"{vox[0].size} random voxels"
         rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-        sample = f"{len(sel)} of {D} directions over the full volume ({len(sel) * V:.3e} updates), FP64 numpy"
-        line["cpu_baseline"] = {"value": len(sel) * V / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+        sample = f"{len(sel)} of {D} directions over {where} ({len(sel) * n_vox:.3e} updates), FP64 numpy"
+        line["cpu_baseline"] = {"value": len(sel) * n_vox / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                                 "sample": sample, "seconds": dt}
         line["accuracy"] = {"rel_l2_vs_fp64_oracle": rel, "sample": sample,
                             "target": 1e-5 if args.stack == "f32" else 3e-3}
     if rank == 0:
         print(json.dumps(line))
     r.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_batch(args):
+    """48 uneven tomograms (``phantoms.batch_workloads``) reconstructed together: stage A per
+    tomogram and one persistent backprojection per round, the whole step captured once as a
+    CUDA graph and replayed.  ``value`` is the voxel x direction updates of all 48 per second."""
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2206_09151_gb300 import phantoms as ph
+    from paper_2206_09151_gb300.build import build
+    from paper_2206_09151_gb300.recon import Batch, Reconstructor
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    cfgs = ph.batch_workloads(seed=4001 + 100 * rank)
+    images = [make_images(c, dev) for c in cfgs]
+    recons = [Reconstructor(c["rot"], c["nu"], c["nv"], c["grid"], lam=c["lam"], delta=c["delta"],
+                            defocus=c["defocus"], nz_layers=c["nz_layers"], sigma=c["sigma"], eps=c["eps"],
+                            cs=c["cs"], stack_dtype=args.stack, device=dev, allocate=False) for c in cfgs]
+    b = Batch(recons, dir_block=args.dir_block)
+    vols = [r.new_volume() for r in recons]
+    U = sum(int(np.prod(c["grid"])) * c["n_dir"] for c in cfgs)
+    dbb = args.dir_block if args.dir_block > 0 else 32
+    rounds = max((c["n_dir"] + dbb - 1) // dbb for c in cfgs)
+    # kernels per replay: per round, stage A (3 launches) for every tomogram still active,
+    # and one persistent backprojection
+    launches = sum(3 * sum(1 for c in cfgs if rr * dbb < c["n_dir"]) + 1 for rr in range(rounds))
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        b.run(images, vols, graph=True)  # the first run captures, the others replay
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_index(local))
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    step_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run(images, vols, graph=True)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    total_ms = max_over_ranks(sum(step_ms), dev)
+    value = aggregate_rate(U, args.steps, world, total_ms)
+    # end to end: pinned host images in, volumes out, every step, around the same replay
+    host_img = [im.cpu().pin_memory() for im in images]
+    host_vol = [torch.empty(v.shape, dtype=torch.float32).pin_memory() for v in vols]
+    e2e_ms = []
+    for st in range(args.warmup + args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for d, h in zip(images, host_img):
+            d.copy_(h, non_blocking=True)
+        b.run(images, vols, graph=True)
+        for h, v in zip(host_vol, vols):
+            h.copy_(v, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if st >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_value = aggregate_rate(U, args.steps, world, max_over_ranks(sum(e2e_ms), dev))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.stack, "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT["batch"], "tomograms": len(cfgs), "round_directions": dbb,
+                       "rounds": rounds, "updates_per_step": U, "stack": args.stack,
+                       "l2": "flushed between timed steps (256 MiB write outside the timed span)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": sum(im.numel() * 4 for im in images),
+                    "d2h_bytes_per_step": sum(v.numel() * 4 for v in vols)},
+            "gpu_launches": launches * args.steps,
+            "roofline": None,
+            "roofline_note": "the graph replay has no per-kernel events; the kernels are those of the single "
+                             "runs, whose rooflines the mid workload reports",
+            "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line))
+    b.close()
+    for r in recons:
+        r.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -447,7 +591,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=list(WORKLOAD_TEXT), default="mid")
-    ap.add_argument("--stack", choices=["f32", "bf16"], default="f32")
+    ap.add_argument("--stack", choices=["f32", "bf16"], default=None,
+                    help="layer-stack precision (default: the workload's, f32 for mid/small, bf16 otherwise)")
     ap.add_argument("--filter", choices=["tikhonov", "mlp"], default="tikhonov",
                     help="mlp: the learned regulariser (seeded untrained weights; speed and parity)")
     ap.add_argument("--dir-block", type=int, default=0)
@@ -455,13 +600,20 @@ def main():
     ap.add_argument("--bp-kernel", choices=["auto", "direct", "staged"], default="auto",
                     help="single-axis backprojection variant")
     ap.add_argument("--dirs", type=int, default=None, help="first N directions only (small profiling cases)")
-    ap.add_argument("--cpu-dirs", type=int, default=3)
+    ap.add_argument("--cpu-dirs", type=int, default=None, help="oracle directions of the CPU baseline "
+                    "(default 3, 1 for the 512^3 and slab workloads)")
     ap.add_argument("--ref-dirs", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
+    if args.stack is None:
+        args.stack = DEFAULT_STACK[args.workload]
+    if args.cpu_dirs is None:
+        args.cpu_dirs = 1 if args.workload in ("learned", "slab") else 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
     return run_ours(args)
 
 

@@ -55,6 +55,38 @@ __device__ __forceinline__ float2 stack_pair_issue(const __nv_bfloat162* p) {
 constexpr float kMagic = 12582912.0f;
 constexpr int kMagicBits = 0x4B400000;
 
+// One direction's samples for a thread's run of kTZ voxels along z.  CLAMP: the taps are
+// clamped to the zero border and the weights saturated (any tile); without it the tile
+// is known to lie inside the detector and the layer range.
+template <typename ST, bool CLAMP>
+__device__ __forceinline__ void generic_run(const TileDir& td, const ST* __restrict__ base, const BackprojConst& c,
+                                            float ftx, float fty, int tx, int ty, float (&acc)[kTZ]) {
+  float ap = fmaf(td.af0, ftx, fmaf(td.af1, fty, td.fa));
+  float bp = fmaf(td.bf0, ftx, fmaf(td.bf1, fty, td.fb));
+  uint32_t t = td.t + td.ti * (uint32_t)tx + td.tj * (uint32_t)ty;
+  const float loa = (float)(-1 - td.ia), hia = (float)(c.nu - 1 - td.ia);
+  const float lob = (float)(-1 - td.ib), hib = (float)(c.nv - 1 - td.ib);
+  const int last_layer = c.nz_layers - 1;
+#pragma unroll
+  for (int z = 0; z < kTZ; ++z) {
+    const int layer = CLAMP ? min(max((int32_t)t >> 24, 0), last_layer) : (int32_t)t >> 24;
+    const float ta = (CLAMP ? fminf(fmaxf(ap, loa), hia) : ap) + kMagic;
+    const float tb = (CLAMP ? fminf(fmaxf(bp, lob), hib) : bp) + kMagic;
+    const int ra = __float_as_int(ta) - kMagicBits;
+    const int rb = __float_as_int(tb) - kMagicBits;
+    const float fa = CLAMP ? __saturatef(ap - (ta - kMagic) + 0.5f) : ap - (ta - kMagic) + 0.5f;
+    const float fb = CLAMP ? __saturatef(bp - (tb - kMagic) + 0.5f) : bp - (tb - kMagic) + 0.5f;
+    const ST* p = base + (size_t)layer * c.layer_elems + (ptrdiff_t)rb * c.su + ra;
+    const float2 r0 = stack_pair(p), r1 = stack_pair(p + c.su);
+    const float top = fmaf(fa, r0.y - r0.x, r0.x);
+    const float bot = fmaf(fa, r1.y - r1.x, r1.x);
+    acc[z] += fmaf(fb, bot - top, top);
+    ap += td.af2;
+    bp += td.bf2;
+    t += td.tk;
+  }
+}
+
 // One 32 x 8 x 8 tile (tile coordinates bx, by, bz); s_dir: dir_count TileDir records.
 template <typename ST>
 __device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const DirParams* __restrict__ dirs,
@@ -84,7 +116,25 @@ __device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const Di
     td.ti = (uint32_t)p.t[1];
     td.tj = (uint32_t)p.t[2];
     td.tk = (uint32_t)p.t[3];
-    td.pad[0] = td.pad[1] = 0;
+    // Whole tile (every thread, also those past the volume edge) inside the detector by a
+    // margin far above the FP32 in-tile error, and inside the layer range: then the clamps
+    // and the saturation below cannot change anything and are skipped (same bits).
+    // An affine map over the tile box takes its extremes at the corners.
+    double amin = a, amax = a, bmin = b, bmax = b;
+    long long tmin = (long long)p.t[0] + (long long)p.t[1] * i0 + (long long)p.t[2] * j0 + (long long)p.t[3] * k0;
+    long long tmax = tmin;
+    const int ext[3] = {kTX - 1, kTY - 1, kTZ - 1};
+    for (int q = 0; q < 3; ++q) {
+      const double da = p.a[q] * ext[q], db = p.b[q] * ext[q];
+      const long long dt = (long long)p.t[q + 1] * ext[q];
+      (da < 0 ? amin : amax) += da;
+      (db < 0 ? bmin : bmax) += db;
+      (dt < 0 ? tmin : tmax) += dt;
+    }
+    constexpr double kMargin = 1e-3;  // pixels
+    td.pad[0] = amin >= -0.5 + kMargin && amax <= c.nu - 0.5 - kMargin && bmin >= -0.5 + kMargin &&
+                bmax <= c.nv - 0.5 - kMargin && tmin >= 0 && tmax < ((long long)c.nz_layers << 24);
+    td.pad[1] = 0;
     s_dir[d] = td;
   }
   __syncthreads();
@@ -93,33 +143,11 @@ __device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const Di
 #pragma unroll
   for (int z = 0; z < kTZ; ++z) acc[z] = 0.f;
   const float ftx = (float)tx, fty = (float)ty;
-  const int last_layer = c.nz_layers - 1;
   for (int d = 0; d < dir_count; ++d) {
     const TileDir& td = s_dir[d];
-    float ap = fmaf(td.af0, ftx, fmaf(td.af1, fty, td.fa));
-    float bp = fmaf(td.bf0, ftx, fmaf(td.bf1, fty, td.fb));
-    uint32_t t = td.t + td.ti * (uint32_t)tx + td.tj * (uint32_t)ty;
-    const float loa = (float)(-1 - td.ia), hia = (float)(c.nu - 1 - td.ia);
-    const float lob = (float)(-1 - td.ib), hib = (float)(c.nv - 1 - td.ib);
     const ST* base = stack + (size_t)d * c.nz_layers * c.layer_elems + (ptrdiff_t)(td.ib + 1) * c.su + (td.ia + 1);
-#pragma unroll
-    for (int z = 0; z < kTZ; ++z) {
-      const int layer = min(max((int32_t)t >> 24, 0), last_layer);
-      const float ta = fminf(fmaxf(ap, loa), hia) + kMagic;
-      const float tb = fminf(fmaxf(bp, lob), hib) + kMagic;
-      const int ra = __float_as_int(ta) - kMagicBits;
-      const int rb = __float_as_int(tb) - kMagicBits;
-      const float fa = __saturatef(ap - (ta - kMagic) + 0.5f);
-      const float fb = __saturatef(bp - (tb - kMagic) + 0.5f);
-      const ST* p = base + (size_t)layer * c.layer_elems + (ptrdiff_t)rb * c.su + ra;
-      const float2 r0 = stack_pair(p), r1 = stack_pair(p + c.su);
-      const float top = fmaf(fa, r0.y - r0.x, r0.x);
-      const float bot = fmaf(fa, r1.y - r1.x, r1.x);
-      acc[z] += fmaf(fb, bot - top, top);
-      ap += td.af2;
-      bp += td.bf2;
-      t += td.tk;
-    }
+    if (td.pad[0]) generic_run<ST, false>(td, base, c, ftx, fty, tx, ty, acc);
+    else generic_run<ST, true>(td, base, c, ftx, fty, tx, ty, acc);
   }
 
   const int i = i0 + tx, j = j0 + ty;
@@ -274,10 +302,11 @@ __device__ __forceinline__ void bp_axis_tile(int bx, int by, int bz, const DirPa
 }
 
 template <typename ST, bool TWO_ROWS>
-// At least 4 CTAs per SM: ptxas then keeps all of a column's gathers in registers at once
-// (58 registers); left to itself it chose 40 and issued them in batches (256^3 / 120
-// directions: 1.57 -> 0.75 ms).
-__global__ void __launch_bounds__(kAX* kAZ, 4) k_backproject_axis(const DirParams* __restrict__ dirs,
+// At least 4 CTAs per SM (float32 pairs): ptxas then keeps all of a column's gathers in
+// registers at once (58 registers); left to itself it chose 40 and issued them in batches
+// (256^3 / 120 directions: 1.57 -> 0.75 ms).  The bfloat16 variant, bound by issue (it
+// unpacks every pair), runs best at 5 (0.84 -> 0.80 ms).
+__global__ void __launch_bounds__(kAX* kAZ, sizeof(ST) == 4 ? 5 : 4) k_backproject_axis(const DirParams* __restrict__ dirs,
                                                                 const ST* __restrict__ stack, BackprojConst c,
                                                                 int dir_begin, int dir_count,
                                                                 float* __restrict__ vol, int accumulate) {

@@ -381,13 +381,26 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
 
   const size_t elem = ca.stack_bf16 ? 4 : 8;  // one tap pair
   p->stack_dir_bytes = (size_t)nz_layers * ca.layer_elems * elem;
-  const size_t per_dir = (size_t)p->nv * p->half * 8 * (1 + (size_t)nz_layers) + p->stack_dir_bytes;
+  // S and T of one direction (the stage-A intermediates)
+  const size_t inter_dir = (size_t)p->nv * p->half * 8 * (1 + (size_t)nz_layers);
+  const size_t per_dir = inter_dir + p->stack_dir_bytes;
+  // Where one direction's intermediates are large (big images, many layers), stage A runs
+  // in sub-blocks whose intermediates fit 1 GiB by default, and the rest of the budget
+  // holds stacks: a larger direction block means fewer volume read-modify-writes and tile
+  // set-ups in the backprojection (1024^2 images, Nz = 64: 13 instead of 5 directions).
+  const bool big_dir = inter_dir > ((size_t)64 << 20);
+  int auto_sub = 0;
+  if (big_dir && o.stage_block == 0) auto_sub = (int)std::max<size_t>(1, ((size_t)1 << 30) / inter_dir);
   int db = o.dir_block;
   if (db == 0) {
     // as many directions per block as a 4 GiB stage budget holds (fewer volume
     // read-modify-writes), then balanced so that the blocks are of equal size
     const size_t budget = (size_t)4 << 30;
-    db = (int)(budget / per_dir);
+    if (auto_sub > 0) {
+      const size_t used = (size_t)auto_sub * inter_dir;
+      db = used < budget ? (int)std::min<size_t>((budget - used) / p->stack_dir_bytes, 1024) : 1;
+    } else
+      db = (int)(budget / per_dir);
     if (db < 1) db = 1;
     if (db > 1024) db = 1024;
     if (D > 0) {
@@ -400,9 +413,10 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   if (db < 1) db = 1;
   p->db = db;
   p->n_blocks = D > 0 ? (D + db - 1) / db : 0;
-  {  // stage-A sub-blocks (option; measured slower than whole blocks at 256^2 / Nz = 32,
-     // where launch gaps outweigh the L2 residency of the intermediates)
-    int sub = o.stage_block > 0 ? o.stage_block : db;
+  {  // stage-A sub-blocks: an option where one direction's intermediates are small (measured
+     // slower than whole blocks at 256^2 / Nz = 32, where launch gaps outweigh the L2
+     // residency of the intermediates), the default where they are large (above)
+    int sub = o.stage_block > 0 ? o.stage_block : (auto_sub > 0 ? auto_sub : db);
     if (sub < 1) sub = 1;
     if (sub > db) sub = db;
     ca.sub_block = P >= 16 ? sub : db;  // the radix-2 path (tiny images) runs whole blocks
