@@ -59,10 +59,10 @@ DEFAULT_STACK = {"mid": "f32", "small": "f32", "learned": "bf16", "slab": "bf16"
 # bench's 120-direction blocks. The stack read grows in proportion; the backprojection's
 # volume read-modify-write does not, and its figure overstates that part.
 NCU_TRAFFIC: dict = {
-    ("k_cols", "mid", "f32"): {"bytes_per_launch": (21.154048e6 + 612.350464e6) * 3, "src": "3d702c4e22709be4"},
-    ("k_cols", "mid", "bf16"): {"bytes_per_launch": (21.154048e6 + 612.350464e6) * 3, "src": "3d702c4e22709be4"},
-    ("k_rows_inv", "mid", "f32"): {"bytes_per_launch": (673.874688e6 + 634.947584e6) * 3, "src": "3d702c4e22709be4"},
-    ("k_backproject", "mid", "f32"): {"bytes_per_launch": (554.355456e6 + 59.22176e6) * 3, "src": "b781270a4c70acae"},
+    ("k_cols", "mid", "f32"): {"bytes_per_launch": (21.221632e6 + 612.414976e6) * 3, "src": "ec137d50e974a37c"},
+    ("k_cols", "mid", "bf16"): {"bytes_per_launch": (21.221632e6 + 612.414976e6) * 3, "src": "ec137d50e974a37c"},
+    ("k_rows_inv", "mid", "f32"): {"bytes_per_launch": (673.772544e6 + 633.649408e6) * 3, "src": "ec137d50e974a37c"},
+    ("k_backproject", "mid", "f32"): {"bytes_per_launch": (612.013312e6 + 59.375872e6) * 3, "src": "1a3990d52f176c1c"},
 }
 
 
