@@ -20,7 +20,13 @@
 namespace recon {
 namespace {
 
-constexpr int kTX = 32, kTY = 8, kTZ = 8;
+constexpr int kTX = kGenTile[0], kTY = kGenTile[1], kTZ = kGenTile[2];
+
+// Integer pixel (floor) and FP32 fraction of a coordinate in 2^-40 pixel units.
+__device__ __forceinline__ int pix_floor(long long x) { return (int)(x >> kPixFracBits); }
+__device__ __forceinline__ float pix_frac(long long x) {
+  return (float)((x & ((1LL << kPixFracBits) - 1)) >> (kPixFracBits - 24)) * 0x1p-24f;  // exact
+}
 
 struct TileDir {  // per (tile, direction), 64 bytes in shared memory
   float fa, fb;   // fractional tile-origin coordinate minus 0.5
@@ -97,14 +103,14 @@ __device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const Di
   const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
   for (int d = threadIdx.x; d < dir_count; d += blockDim.x) {
     const DirParams& p = dirs[dir_begin + d];
-    const double a = fma(p.a[0], (double)i0, fma(p.a[1], (double)j0, fma(p.a[2], (double)k0, p.a[3])));
-    const double b = fma(p.b[0], (double)i0, fma(p.b[1], (double)j0, fma(p.b[2], (double)k0, p.b[3])));
-    const double fla = floor(a), flb = floor(b);
+    // tile origin on the detector: exact integer sums in 2^-40 pixel
+    const long long a = p.a[3] + p.a[0] * i0 + p.a[1] * j0 + p.a[2] * k0;
+    const long long b = p.b[3] + p.b[0] * i0 + p.b[1] * j0 + p.b[2] * k0;
     TileDir td;
-    td.ia = (int)fla;
-    td.ib = (int)flb;
-    td.fa = (float)(a - fla) - 0.5f;
-    td.fb = (float)(b - flb) - 0.5f;
+    td.ia = pix_floor(a);
+    td.ib = pix_floor(b);
+    td.fa = pix_frac(a) - 0.5f;
+    td.fb = pix_frac(b) - 0.5f;
     td.t = (uint32_t)p.t[0] + (uint32_t)p.t[1] * (uint32_t)i0 + (uint32_t)p.t[2] * (uint32_t)j0 +
            (uint32_t)p.t[3] * (uint32_t)k0;
     td.af0 = p.af[0];
@@ -117,23 +123,18 @@ __device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const Di
     td.tj = (uint32_t)p.t[2];
     td.tk = (uint32_t)p.t[3];
     // Whole tile (every thread, also those past the volume edge) inside the detector by a
-    // margin far above the FP32 in-tile error, and inside the layer range: then the clamps
-    // and the saturation below cannot change anything and are skipped (same bits).
-    // An affine map over the tile box takes its extremes at the corners.
-    double amin = a, amax = a, bmin = b, bmax = b;
-    long long tmin = (long long)p.t[0] + (long long)p.t[1] * i0 + (long long)p.t[2] * j0 + (long long)p.t[3] * k0;
-    long long tmax = tmin;
-    const int ext[3] = {kTX - 1, kTY - 1, kTZ - 1};
-    for (int q = 0; q < 3; ++q) {
-      const double da = p.a[q] * ext[q], db = p.b[q] * ext[q];
-      const long long dt = (long long)p.t[q + 1] * ext[q];
-      (da < 0 ? amin : amax) += da;
-      (db < 0 ? bmin : bmax) += db;
-      (dt < 0 ? tmin : tmax) += dt;
-    }
-    constexpr double kMargin = 1e-3;  // pixels
-    td.pad[0] = amin >= -0.5 + kMargin && amax <= c.nu - 0.5 - kMargin && bmin >= -0.5 + kMargin &&
-                bmax <= c.nv - 0.5 - kMargin && tmin >= 0 && tmax < ((long long)c.nz_layers << 24);
+    // margin (1e-3 pixel) far above the FP32 in-tile error, and inside the layer range: then
+    // the clamps and the saturation below cannot change anything and are skipped (same
+    // bits).  The extremes of the affine maps over the tile (at its corners) come with the
+    // direction, in 2^-16 pixel, rounded outwards.
+    const long long a16 = a >> (kPixFracBits - 16), b16 = b >> (kPixFracBits - 16);
+    const long long t = (long long)p.t[0] + (long long)p.t[1] * i0 + (long long)p.t[2] * j0 + (long long)p.t[3] * k0;
+    constexpr long long kMargin16 = 66;  // 1e-3 pixel in 2^-16 pixel
+    const long long lo16 = -32768 + kMargin16;
+    td.pad[0] = p.ab_ext[0] != INT32_MIN && p.t_ext[0] != INT32_MIN && a16 + p.ab_ext[0] >= lo16 &&
+                a16 + p.ab_ext[1] + 1 <= (long long)c.nu * 65536 - 32768 - kMargin16 && b16 + p.ab_ext[2] >= lo16 &&
+                b16 + p.ab_ext[3] + 1 <= (long long)c.nv * 65536 - 32768 - kMargin16 && t + p.t_ext[0] >= 0 &&
+                t + p.t_ext[1] < ((long long)c.nz_layers << 24);
     td.pad[1] = 0;
     s_dir[d] = td;
   }
@@ -220,11 +221,10 @@ __device__ __forceinline__ void bp_axis_tile(int bx, int by, int bz, const DirPa
   axis_lane(threadIdx.x, tx, tz);
   for (int d = threadIdx.x; d < dir_count; d += blockDim.x) {
     const DirParams& p = dirs[dir_begin + d];
-    const double a = fma(p.a[0], (double)i0, fma(p.a[2], (double)k0, p.a[3]));  // p.a[1] = 0
-    const double fla = floor(a);
+    const long long a = p.a[3] + p.a[0] * i0 + p.a[2] * k0;  // p.a[1] = 0; 2^-40 pixel
     AxisDir ad;
-    ad.fa = (float)(a - fla) - 0.5f;
-    ad.ia = (int)fla;
+    ad.fa = pix_frac(a) - 0.5f;
+    ad.ia = pix_floor(a);
     ad.t = (uint32_t)p.t[0] + (uint32_t)p.t[1] * (uint32_t)i0 + (uint32_t)p.t[3] * (uint32_t)k0;  // Tj = 0
     ad.af0 = p.af[0];
     ad.af2 = p.af[2];
@@ -393,11 +393,10 @@ __global__ void __launch_bounds__(kAX* kAZ) k_backproject_axis_staged(const DirP
   const int last_layer = c.nz_layers - 1;
   for (int d = threadIdx.x; d < dir_count; d += blockDim.x) {
     const DirParams& p = dirs[dir_begin + d];
-    const double a = fma(p.a[0], (double)i0, fma(p.a[2], (double)k0, p.a[3]));  // p.a[1] = 0
-    const double fla = floor(a);
+    const long long a = p.a[3] + p.a[0] * i0 + p.a[2] * k0;  // p.a[1] = 0; 2^-40 pixel
     AxisDir ad;
-    ad.fa = (float)(a - fla) - 0.5f;
-    ad.ia = (int)fla;
+    ad.fa = pix_frac(a) - 0.5f;
+    ad.ia = pix_floor(a);
     ad.t = (uint32_t)p.t[0] + (uint32_t)p.t[1] * (uint32_t)i0 + (uint32_t)p.t[3] * (uint32_t)k0;  // Tj = 0
     ad.af0 = p.af[0];
     ad.af2 = p.af[2];

@@ -6,6 +6,7 @@
 #include "recon.h"
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -208,14 +209,17 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
       }
       recon::DirParams& d = p->dirs[n];
       std::memset(&d, 0, sizeof(d));
+      const double pix = std::ldexp(1.0, recon::kPixFracBits);
+      const double a3 = 0.5 * (p->nu - 1) - ((R[0] * cx + R[1] * cy) + R[2] * cz);
+      const double b3 = 0.5 * (p->nv - 1) - ((R[3] * cx + R[4] * cy) + R[5] * cz);
       for (int q = 0; q < 3; ++q) {
-        d.a[q] = R[q];
-        d.b[q] = R[3 + q];
+        d.a[q] = std::llrint(R[q] * pix);
+        d.b[q] = std::llrint(R[3 + q] * pix);
         d.af[q] = (float)R[q];
         d.bf[q] = (float)R[3 + q];
       }
-      d.a[3] = 0.5 * (p->nu - 1) - ((R[0] * cx + R[1] * cy) + R[2] * cz);
-      d.b[3] = 0.5 * (p->nv - 1) - ((R[3] * cx + R[4] * cy) + R[5] * cz);
+      d.a[3] = std::llrint(a3 * pix);
+      d.b[3] = std::llrint(b3 * pix);
       // Depth layers: Nz equal slabs over the bounding-box extent along the beam.
       // Exact operation order (defines the fixed-point layer decision):
       const double ext = (std::fabs(R[6]) * (double)p->nx + std::fabs(R[7]) * (double)p->ny) +
@@ -229,6 +233,28 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
       d.t[1] = (int32_t)std::rint(ti * one);
       d.t[2] = (int32_t)std::rint(tj * one);
       d.t[3] = (int32_t)std::rint(tk * one);
+      {  // extremes over a general-kernel tile, relative to its origin (outward rounding)
+        double lo[2] = {0.0, 0.0}, hi[2] = {0.0, 0.0};
+        long long tlo = 0, thi = 0;
+        for (int q = 0; q < 3; ++q) {
+          const int e = recon::kGenTile[q] - 1;
+          for (int w = 0; w < 2; ++w) {
+            const double v = R[3 * w + q] * e;
+            (v < 0 ? lo[w] : hi[w]) += v;
+          }
+          const long long tv = (long long)d.t[q + 1] * e;
+          (tv < 0 ? tlo : thi) += tv;
+        }
+        const double u16 = 65536.0;
+        const double ext16[4] = {std::floor(lo[0] * u16) - 1, std::ceil(hi[0] * u16) + 1,
+                                 std::floor(lo[1] * u16) - 1, std::ceil(hi[1] * u16) + 1};
+        bool fits = tlo >= INT32_MIN / 2 && thi <= INT32_MAX / 2;
+        for (int q = 0; q < 4; ++q) fits = fits && std::fabs(ext16[q]) < 1e9;
+        for (int q = 0; q < 4; ++q) d.ab_ext[q] = fits ? (int32_t)ext16[q] : 0;
+        d.t_ext[0] = fits ? (int32_t)tlo : 0;
+        d.t_ext[1] = fits ? (int32_t)thi : 0;
+        if (!fits) d.ab_ext[0] = d.t_ext[0] = INT32_MIN;
+      }
       // Per-layer CTF phase constant: chi = pi * [lambda (R_n - z_k) / (P delta)^2] * m^2 + ...
       const double extm = ext * delta;
       for (int k = 0; k < nz_layers; ++k) {

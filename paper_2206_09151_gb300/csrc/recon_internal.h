@@ -10,14 +10,26 @@ struct recon_plan_s;
 
 namespace recon {
 
-// Per-direction constants, built by the plan in FP64 (one 128-byte record per direction).
+// Voxel tile of the general-geometry backprojection (i, j, k extents).
+constexpr int kGenTile[3] = {32, 8, 8};
+// Fixed-point scale of the detector coordinates in DirParams: 2^-40 pixel.
+constexpr int kPixFracBits = 40;
+
+// Per-direction constants, built by the plan from FP64 (one 128-byte record per direction).
 struct DirParams {
-  double a[4];      // detector u pixel: a(i,j,k) = a[0] i + a[1] j + a[2] k + a[3]
-  double b[4];      // detector v pixel, same form
+  // detector u pixel a(i,j,k) = a[0] i + a[1] j + a[2] k + a[3] and v pixel b(i,j,k), each
+  // coefficient rounded to 2^-40 pixel: a tile origin is an exact integer sum (error below
+  // 1e-8 pixel at any grid size), formed without FP64 arithmetic on the device
+  int64_t a[4];
+  int64_t b[4];
   float af[3];      // FP32 copies of the steps a[0..2]
   float bf[3];      // FP32 copies of the steps b[0..2]
   int32_t t[4];     // depth in 2^-24 layer units: T0, Ti, Tj, Tk (exact integer sum)
-  int32_t pad[6];
+  // extremes of a and b over a general-kernel tile relative to its origin, in 2^-16 pixel
+  // (min a, max a, min b, max b, rounded outwards), and of t (min, max); INT32_MIN in
+  // ab_ext[0] or t_ext[0] marks a direction whose extremes do not fit (no fast path)
+  int32_t ab_ext[4];
+  int32_t t_ext[2];
 };
 static_assert(sizeof(DirParams) == 128, "DirParams must stay 128 bytes");
 
