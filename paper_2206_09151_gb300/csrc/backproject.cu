@@ -5,9 +5,9 @@
 // A CTA owns a 32 x 8 x 8 voxel tile; a thread owns an 8-voxel run along z and keeps
 // its sums in registers across the whole direction block, then reads-modifies-writes
 // the volume once.  Coordinates: per (tile, direction) the tile-origin pixel
-// coordinate is formed in FP64 and split into an integer and an FP32 fraction, so the
-// FP32 arithmetic inside the tile works on small numbers (error ~1e-6 pixel at any
-// detector size).  The depth coordinate is an exact 2^-24 fixed-point integer sum, so
+// coordinate is an exact integer sum of 2^-40-pixel fixed-point coefficients, split into
+// an integer and an FP32 fraction, so the FP32 arithmetic inside the tile works on small
+// numbers (error ~1e-6 pixel at any detector size).  The depth coordinate is an exact 2^-24 fixed-point integer sum, so
 // the layer decision does not depend on the traversal order.  Out-of-detector taps
 // read the stack's zero border (rows -1 and nv, pairs holding the columns -1 and nu):
 // the integer tap is clamped to [-1, n-1] and the weight saturated to [0, 1], which
