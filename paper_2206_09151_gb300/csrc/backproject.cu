@@ -41,21 +41,6 @@ static_assert(sizeof(TileDir) == 64, "TileDir layout");
 // A stack entry is the horizontal tap pair (Y[u], Y[u + 1]) (one 8-byte or 4-byte load).
 __device__ __forceinline__ float2 stack_pair(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ float2 stack_pair(const __nv_bfloat162* p) { return __bfloat1622float2(__ldg(p)); }
-// The same loads as volatile asm, which keeps a run of them in program order ahead of
-// the arithmetic that uses them (all of a column's gathers in flight at once).
-__device__ __forceinline__ float2 stack_pair_issue(const float2* p) {
-  float2 v;
-  asm volatile("ld.global.nc.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "l"(p));
-  return v;
-}
-__device__ __forceinline__ float2 stack_pair_issue(const __nv_bfloat162* p) {
-  unsigned u;
-  asm volatile("ld.global.nc.b32 %0, [%1];\n" : "=r"(u) : "l"(p));
-  __nv_bfloat162 h;
-  memcpy(&h, &u, sizeof(u));
-  return __bfloat1622float2(h);
-}
-
 // Round-to-nearest integer of |x| < 2^22 through the FP32 adder: x + 1.5*2^23 holds
 // rint(x) in its low mantissa bits.
 constexpr float kMagic = 12582912.0f;
@@ -255,13 +240,11 @@ __device__ __forceinline__ void bp_axis_tile(int bx, int by, int bz, const DirPa
     const ST* p = stack + ((size_t)d * c.nz_layers + layer) * c.layer_elems + (ptrdiff_t)(row0 + 1) * c.su +
                   (ra + ad.ia + 1);
     if (rows_inside) {
-      // every tap of this direction is loaded before the first is used, so that all of
-      // the column's gathers are in flight together
+      // every tap of this direction is loaded before the first is used; with the kernel's
+      // launch bounds the registers hold them all, so the column's gathers are in flight together
       float2 v[kJ + (TWO_ROWS ? 1 : 0)];
 #pragma unroll
-      for (int q = 0; q < kJ + (TWO_ROWS ? 1 : 0); ++q) v[q] = stack_pair_issue(p + q * c.su);
-#pragma unroll
-      for (int q = 0; q < kJ + (TWO_ROWS ? 1 : 0); ++q) asm volatile("" : "+f"(v[q].x), "+f"(v[q].y));
+      for (int q = 0; q < kJ + (TWO_ROWS ? 1 : 0); ++q) v[q] = stack_pair(p + q * c.su);
       if (TWO_ROWS) {
         float prev = fmaf(fa, v[0].y - v[0].x, v[0].x);
 #pragma unroll
