@@ -62,7 +62,7 @@ NCU_TRAFFIC: dict = {
     ("k_cols", "mid", "f32"): {"bytes_per_launch": (21.221632e6 + 612.414976e6) * 3, "src": "ec137d50e974a37c"},
     ("k_cols", "mid", "bf16"): {"bytes_per_launch": (21.221632e6 + 612.414976e6) * 3, "src": "ec137d50e974a37c"},
     ("k_rows_inv", "mid", "f32"): {"bytes_per_launch": (673.772544e6 + 633.649408e6) * 3, "src": "ec137d50e974a37c"},
-    ("k_backproject", "mid", "f32"): {"bytes_per_launch": (612.292096e6 + 59.760128e6) * 3, "src": "0ba0dcd69f54c26c"},
+    ("k_backproject", "mid", "f32"): {"bytes_per_launch": (612.676608e6 + 59.275520e6) * 3, "src": "40408219a6e58e02"},
 }
 
 
