@@ -236,6 +236,41 @@ def test_fbp_of_closed_form_ball_radon_recovers_delta():
     assert np.sqrt(np.mean(vals[outer & (np.hypot(i - 31.5, k - 31.5) < 28)] ** 2)) < 2e-2
 
 
+def test_filter_off_single_layer_is_textbook_fbp_slice_by_slice():
+    """Nz = 1, filter off, a single-axis scan about y: the operator is parallel-beam FBP of
+    each detector row (Eq. 15), written here independently: the band-limited Ram-Lak kernel
+    convolved in real space over every shift the row needs (no DFT), scaled by pi/D and the
+    pitch, then linear interpolation along the detector u axis of each view, zero outside."""
+    rng = np.random.default_rng(21)
+    D, nu, nx, ny, nz, delta = 16, 24, 20, 5, 17, 0.5
+    rot = ph.single_axis_rotations(D, start=0.2)
+    proj = rng.standard_normal((D, ny, nu))  # projection input, nv = ny: row v is slice j
+    vol = O.recon(proj, rot, lam=1.0, delta=delta, defocus=np.zeros(D), nz_layers=1, grid=(nx, ny, nz),
+                  filt=O.FILTER_OFF, input_mode=O.INPUT_CONTRAST)
+    shifts = np.arange(-(nu - 1), nu)
+    h = np.where(shifts == 0, 1 / (4 * delta ** 2),
+                 np.where(shifts % 2 != 0, -1 / (shifts.astype(float) ** 2 * np.pi ** 2 * delta ** 2), 0.0))
+    ref = np.zeros((nz, ny, nx))
+    for n in range(D):
+        # q[v, u] = (pi / D) * delta * sum_u' p[v, u'] h[u - u']
+        q = np.zeros((ny, nu))
+        for u in range(nu):
+            for up in range(nu):
+                q[:, u] += proj[n, :, up] * h[u - up + nu - 1]
+        q *= np.pi / D * delta
+        ux = rot[n, 0]  # the view's detector u axis in the volume frame
+        for k in range(nz):
+            for i in range(nx):
+                r = np.array([i - (nx - 1) / 2, 0.0, k - (nz - 1) / 2])
+                u = ux[0] * r[0] + ux[2] * r[2] + (nu - 1) / 2  # ux[1] = 0 about y
+                u0 = int(np.floor(u))
+                f = u - u0
+                left = q[:, u0] if 0 <= u0 < nu else 0.0
+                right = q[:, u0 + 1] if 0 <= u0 + 1 < nu else 0.0
+                ref[k, :, i] += (1 - f) * left + f * right
+    assert np.max(np.abs(vol - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
 # ---------------------------------------------------------------- invariants
 def _small_case(seed=4, D=12, grid=(10, 9, 8), nu=12, nv=11):
     rng = np.random.default_rng(seed)
