@@ -59,9 +59,9 @@ DEFAULT_STACK = {"mid": "f32", "small": "f32", "learned": "bf16", "slab": "bf16"
 # bench's 120-direction blocks. The stack read grows in proportion; the backprojection's
 # volume read-modify-write does not, and its figure overstates that part.
 NCU_TRAFFIC: dict = {
-    ("k_cols", "mid", "f32"): {"bytes_per_launch": (21.221632e6 + 612.414976e6) * 3, "src": "ec137d50e974a37c"},
-    ("k_cols", "mid", "bf16"): {"bytes_per_launch": (21.221632e6 + 612.414976e6) * 3, "src": "ec137d50e974a37c"},
-    ("k_rows_inv", "mid", "f32"): {"bytes_per_launch": (673.772544e6 + 633.649408e6) * 3, "src": "ec137d50e974a37c"},
+    ("k_cols", "mid", "f32"): {"bytes_per_launch": (21.393664e6 + 612.677376e6) * 3, "src": "d48e06ae03fad5cf"},
+    ("k_cols", "mid", "bf16"): {"bytes_per_launch": (21.393664e6 + 612.677376e6) * 3, "src": "d48e06ae03fad5cf"},
+    ("k_rows_inv", "mid", "f32"): {"bytes_per_launch": (673.865728e6 + 633.4848e6) * 3, "src": "d48e06ae03fad5cf"},
     ("k_backproject", "mid", "f32"): {"bytes_per_launch": (612.676608e6 + 59.275520e6) * 3, "src": "40408219a6e58e02"},
 }
 

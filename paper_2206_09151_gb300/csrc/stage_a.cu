@@ -170,6 +170,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_cols(const float2* __restrict__
   } else {
     wgt[0] = ramp[colc];
   }
+  // with a filter, the weight carries the filter's prefactor lambda / (4 pi sqrt(1+sigma^2))
+  if constexpr (FILT != 0) {
+#pragma unroll
+    for (int s = 0; s < (DENS ? 8 : 1); ++s) wgt[s] *= c.pref;
+  }
   // chi/(2 pi) in 2^-32 turns needs only the top 32 bits of the 64-bit fixed-point
   // sum: the per-layer product uA_k * m is formed as hi(uA) * m + umulhi(lo(uA), m), and
   // the layer-independent part uC * m^2 - uW once per element (dropped low-word carries
@@ -215,7 +220,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_cols(const float2* __restrict__
         float e;
         if constexpr (FILT == 2) e = __ldg(eps_k + bin[s]);  // learned eps
         else e = c.eps;                                      // Tikhonov eps
-        f *= c.pref * __fdividef(sn, fmaf(sn, sn, e));       // real part of the Eq. 11 bracket
+        f *= __fdividef(sn, fmaf(sn, sn, e));                // real part of the Eq. 11 bracket
       }
       x[s] = make_float2(xg[s].x * f, xg[s].y * f);
     }
