@@ -394,3 +394,24 @@ def test_density_weighted_fbp_of_a_ball_from_random_directions():
     inner = rr < 0.8 * 8
     assert abs(vol[inner].mean() - 1.0) < 0.03
     assert np.sqrt(np.mean((vol[inner] - 1.0) ** 2)) < 0.04
+
+
+def test_process_pool_sums_the_same_terms():
+    """The spawned pool (used for the full-size parity cases) splits the directions over
+    workers: the same terms summed in another order."""
+    rot, img, kw = _small_case(seed=9, D=10)
+    i = np.arange(10) % kw["grid"][0]
+    j = (np.arange(10) * 3) % kw["grid"][1]
+    k = (np.arange(10) * 7) % kw["grid"][2]
+    a = O.recon(img, rot, voxels=(i, j, k), density=True, **kw)
+    b = O.recon(img, rot, voxels=(i, j, k), density=True, workers=3, **kw)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
+
+
+def test_batch_workloads_span_the_stated_ranges():
+    cfgs = ph.batch_workloads()
+    assert len(cfgs) == 48
+    assert all(64 <= c["grid"][0] <= 256 and c["grid"][0] % 32 == 0 and c["nu"] == c["grid"][0] for c in cfgs)
+    assert all(60 <= c["n_dir"] <= 360 and 4 <= c["nz_layers"] <= 32 for c in cfgs)
+    assert {c["phantom"] for c in cfgs} == {"balls", "blobs"} and len({c["lam"] for c in cfgs}) == 2
+    assert all(c["rot"].shape == (c["n_dir"], 3, 3) and len(c["defocus"]) == c["n_dir"] for c in cfgs)
