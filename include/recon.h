@@ -54,6 +54,9 @@ extern "C" {
 #define RECON_E_CUDA (-3)             /* a CUDA runtime call or a launch failed        */
 #define RECON_E_WORKSPACE (-4)        /* workspace too small or not 256-byte aligned    */
 #define RECON_E_NO_MEMORY (-5)        /* host allocation failed                         */
+#define RECON_E_NONFINITE (-6)        /* an image holds NaN or Inf (checked only when the
+                                         plan's check_finite option is set)             */
+#define RECON_E_NO_WEIGHTS (-7)       /* RECON_FILTER_MLP without its network parameters */
 
 /* ---------------------------------------------------------------- option values */
 #define RECON_FILTER_OFF 0       /* H = 1: ramp-filtered backprojection of g (Eq. 15)   */
@@ -115,11 +118,15 @@ typedef struct {
                       the stack, or each direction's footprint staged in shared memory);
                       AUTO picks the measured-faster one on sm_103a; other geometries
                       always use the general kernel                                         */
+  int check_finite; /* 1: recon_run (and recon_run_noalloc) first scans the images for NaN / Inf on the GPU, waits
+                       for the scan (the call then synchronises its stream) and returns
+                       RECON_E_NONFINITE without touching the volume if it finds any; 0: no
+                       scan (a NaN then propagates into the voxels it reaches)             */
 } recon_options;
 
 /* Fills *opts with defaults: sigma 0, eps 0.1 (the value of Sec. 3), cs 0, Tikhonov
  * filter, intensity input, float32 stack, single-axis ramp, overwrite, automatic
- * block.  No error (opts NULL is ignored). */
+ * block, no finiteness scan.  No error (opts NULL is ignored). */
 void recon_default_options(recon_options* opts);
 
 /* Builds a plan (host memory only; no CUDA call, no device allocation).
@@ -129,7 +136,8 @@ void recon_default_options(recon_options* opts);
  *   opts      NULL = recon_default_options
  * The per-direction FP64 tables are computed here: layer depths z_k and defocus
  * R_n - z_k (Eq. 5), the CTF phase constants (Eq. 7, Eq. 11), the ramp (Sec. 2).
- * Returns INVALID_ARG / UNSUPPORTED_SIZE / NO_MEMORY on failure, *out untouched. */
+ * Returns INVALID_ARG / UNSUPPORTED_SIZE / NO_MEMORY on failure (NO_WEIGHTS for
+ * RECON_FILTER_MLP with mlp_weights NULL), *out untouched. */
 int recon_plan(const recon_geometry* geom, double lambda, double delta, const double* defocus, int nz_layers,
                const recon_grid* grid, const recon_options* opts, recon_plan_t* out);
 
@@ -187,6 +195,21 @@ int recon_batch_destroy(recon_batch_t batch); /* NULL is a no-op */
 int recon_run_batch_workspace_size(int n, const recon_plan_t* plans, size_t* bytes);
 int recon_run_batch(int n, const recon_plan_t* plans, const float* const* images, float* const* volumes,
                     void* workspace, size_t ws_bytes, void* stream);
+
+/* Depth of field (Sec. 1): DOF = delta^2 / (2 lambda).  Layers thinner than the DOF
+ * keep every voxel within its layer's focus; a thicker layer is the plan-time warning of
+ * a shallow-DOF scan under too few layers.
+ *   recon_plan_dof      *pitch_max = the largest layer pitch h_n = T_n / Nz over the
+ *                       directions (T_n the bounding-box extent along beam n, metres),
+ *                       *dof = Delta^2 / (2 lambda); either pointer may be NULL.
+ *   recon_plan_warning  "" when pitch_max <= dof, else a message with both figures (the
+ *                       string lives as long as the plan).
+ *   recon_layers_for_dof  the smallest Nz (capped at RECON_MAX_LAYERS) whose layer pitch
+ *                       is <= DOF for every direction of `geom` over `grid` (1 when the
+ *                       scan has no direction). */
+int recon_plan_dof(recon_plan_t plan, double* pitch_max, double* dof);
+const char* recon_plan_warning(recon_plan_t plan);
+int recon_layers_for_dof(const recon_geometry* geom, const recon_grid* grid, double lambda, double delta, int* nz);
 
 /* Plan facts: padded FFT size P, directions per block, number of blocks, directions per
  * FFT/filter sub-block (any pointer may be NULL). */
@@ -250,9 +273,11 @@ int recon_profile_read(recon_plan_t plan, double* ms, int* launches);
  *   Limit: a plan whose table head plus one direction's scratch exceeds
  *   RECON_NOALLOC_SCRATCH_BYTES is refused with RECON_E_UNSUPPORTED_SIZE and a message
  *   giving both sizes.
- *   Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call before any
- *   stream capture.
+ *   Set-up: every call looks up the array's device address (cudaGetSymbolAddress) on
+ *   the current device, so the address stays right after a cudaDeviceReset.
+ *   Streams: the call copies the plan tables from pageable host memory with
+ *   cudaMemcpyAsync, which stream capture rejects, so it must not be called while
+ *   `stream` is being captured into a CUDA graph.
  *   Sharing: all calls share the one array and it keeps the last call's contents;
  *   nothing in it needs to start at zero (every kernel writes what it later reads), but
  *   two calls that overlap on the GPU (other streams, other threads) race on it.

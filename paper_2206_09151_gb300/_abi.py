@@ -19,6 +19,8 @@ RECON_E_UNSUPPORTED_SIZE = -2
 RECON_E_CUDA = -3
 RECON_E_WORKSPACE = -4
 RECON_E_NO_MEMORY = -5
+RECON_E_NONFINITE = -6
+RECON_E_NO_WEIGHTS = -7
 
 RECON_FILTER_OFF = 0
 RECON_FILTER_TIKHONOV = 1
@@ -32,6 +34,7 @@ RECON_RAMP_SINGLE_AXIS = 0
 RECON_RAMP_DENSITY = 1
 RECON_BP_AUTO, RECON_BP_DIRECT, RECON_BP_STAGED = 0, 1, 2
 RECON_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
+RECON_MAX_LAYERS = 96
 
 
 class ReconGrid(ctypes.Structure):
@@ -48,7 +51,7 @@ class ReconOptions(ctypes.Structure):
                 ("filter", ctypes.c_int), ("input_mode", ctypes.c_int), ("stack_dtype", ctypes.c_int),
                 ("ramp_mode", ctypes.c_int), ("accumulate", ctypes.c_int), ("dir_block", ctypes.c_int),
                 ("mlp_weights", ctypes.POINTER(ctypes.c_float)), ("nsr", ctypes.c_double),
-                ("stage_block", ctypes.c_int), ("bp_kernel", ctypes.c_int)]
+                ("stage_block", ctypes.c_int), ("bp_kernel", ctypes.c_int), ("check_finite", ctypes.c_int)]
 
 
 class ReconTrainCfg(ctypes.Structure):
@@ -90,6 +93,11 @@ def load_library(path: str = LIB_PATH):
     L.recon_backproject.argtypes = [vp, vp, ip, ip, vp, ip, vp, sz, vp]
     L.recon_plan_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.recon_run_noalloc.argtypes = [vp, vp, vp, vp]
+    L.recon_plan_dof.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.recon_plan_warning.argtypes = [vp]
+    L.recon_plan_warning.restype = ctypes.c_char_p
+    L.recon_layers_for_dof.argtypes = [ctypes.POINTER(ReconGeometry), ctypes.POINTER(ReconGrid), ctypes.c_double,
+                                       ctypes.c_double, ctypes.POINTER(ip)]
     L.recon_mlp_train_workspace_size.argtypes = [ctypes.POINTER(ReconTrainCfg), ctypes.POINTER(sz)]
     L.recon_mlp_train.argtypes = [ctypes.POINTER(ReconTrainCfg), ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_float), vp, sz, vp]
@@ -113,7 +121,7 @@ def load_library(path: str = LIB_PATH):
                  "recon_plan_info", "recon_sync", "recon_destroy", "recon_profile_enable", "recon_profile_read",
                  "recon_run_noalloc", "recon_mlp_train_workspace_size", "recon_mlp_train", "recon_batch_create",
                  "recon_batch_workspace_size", "recon_batch_run", "recon_batch_run_graph", "recon_batch_destroy",
-                 "recon_run_batch_workspace_size", "recon_run_batch"):
+                 "recon_run_batch_workspace_size", "recon_run_batch", "recon_plan_dof", "recon_layers_for_dof"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -198,6 +206,28 @@ def recon_plan_info(plan) -> tuple[int, int, int, int]:
     _check(load_library().recon_plan_info(plan, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
            "recon_plan_info")
     return a.value, b.value, c.value, d.value
+
+
+def recon_plan_dof(plan) -> tuple[float, float]:
+    """(largest layer pitch over the directions, depth of field Delta^2 / (2 lambda)), metres."""
+    h, d = ctypes.c_double(), ctypes.c_double()
+    _check(load_library().recon_plan_dof(plan, ctypes.byref(h), ctypes.byref(d)), "recon_plan_dof")
+    return h.value, d.value
+
+
+def recon_plan_warning(plan) -> str:
+    return load_library().recon_plan_warning(plan).decode()
+
+
+def recon_layers_for_dof(rot: np.ndarray, grid, lam: float, delta: float) -> int:
+    """Smallest Nz whose layers are no thicker than the depth of field for every direction."""
+    rot = np.ascontiguousarray(rot, dtype=np.float64).reshape(-1, 3, 3)
+    geom = ReconGeometry(rot.shape[0], 1, 1, rot.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    g = ReconGrid(*grid)
+    nz = ctypes.c_int()
+    _check(load_library().recon_layers_for_dof(ctypes.byref(geom), ctypes.byref(g), lam, delta, ctypes.byref(nz)),
+           "recon_layers_for_dof")
+    return nz.value
 
 
 def recon_run(plan, images_ptr: int, volume_ptr: int, ws_ptr: int, ws_bytes: int, stream: int):

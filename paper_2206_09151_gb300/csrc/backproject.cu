@@ -654,9 +654,7 @@ cudaError_t launch_backproject_persistent(const BatchBp* desc_dev, int n_desc, u
         cudaFuncSetAttribute(k_backproject_persistent, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  int dev = 0, sms = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = device_sm_count();
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backproject_persistent, 256, smem);
   if (per_sm < 1) per_sm = 1;

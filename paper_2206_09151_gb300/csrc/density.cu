@@ -69,7 +69,7 @@ cudaError_t launch_density_setup(const DensityConst& dc, const DirParams* dirs, 
     const int n = dc.n_samples1 * dc.n_samples1;
     k_density_splat<<<dim3((n + 255) / 256, n_dir), 256, 0, stream>>>(dirs, dc, P, S);
   }
-  k_density_band_sum<<<152 * 4, 256, 0, stream>>>(S, dc, band_sum);
+  k_density_band_sum<<<device_sm_count() * 4, 256, 0, stream>>>(S, dc, band_sum);
   return cudaGetLastError();
 }
 

@@ -12,11 +12,11 @@
 //
 // The host cannot use the array's name as a device address (in host code it names a
 // host-side shadow; a kernel handed that would fault or silently touch the wrong
-// memory), so the device address is looked up once per device with
-// cudaGetSymbolAddress while that device is current, and that pointer is what the
-// kernels receive.
-#include <mutex>
-
+// memory), so every call looks up the device address with cudaGetSymbolAddress while
+// the caller's device is current, and that pointer is what the kernels receive.  The
+// lookup allocates nothing and is cheap; doing it on every call (rather than caching it
+// per device) keeps the address right after a cudaDeviceReset or a primary-context
+// re-creation, which can reload the module at a new address.
 #include "recon.h"
 #include "recon_internal.h"
 
@@ -24,32 +24,14 @@ namespace {
 
 static __device__ __align__(256) unsigned char g_scratch[RECON_NOALLOC_SCRATCH_BYTES];
 
-constexpr int kMaxDevices = 256;
-std::mutex g_mutex;
-void* g_scratch_ptr[kMaxDevices] = {};
-
 }  // namespace
 
 extern "C" int recon_run_noalloc(recon_plan_t plan, const float* images, float* volume, void* stream) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    recon::set_last_error("recon_run_noalloc: cudaGetDevice failed or device index out of range");
-    return RECON_E_CUDA;
-  }
   void* ptr = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_ptr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_scratch);
-      if (e != cudaSuccess || !p) {
-        recon::set_last_error("recon_run_noalloc: cudaGetSymbolAddress of the static scratch failed");
-        return RECON_E_CUDA;
-      }
-      g_scratch_ptr[dev] = p;
-    }
-    ptr = g_scratch_ptr[dev];
+  const cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
+  if (e != cudaSuccess || !ptr) {
+    recon::set_last_error("recon_run_noalloc: cudaGetSymbolAddress of the static scratch failed");
+    return RECON_E_CUDA;
   }
   return recon::run_in_scratch(plan, images, volume, static_cast<char*>(ptr), RECON_NOALLOC_SCRATCH_BYTES,
                                (cudaStream_t)stream);

@@ -63,6 +63,9 @@ struct recon_plan_s {
   size_t off_dirs, off_uA, off_ramp, off_tw, off_twp, off_dens, off_dsum, off_theta, off_cnt, off_x2, off_S, off_T,
       off_stack, off_pow, off_eps, ws_bytes, table_bytes;
   size_t stack_dir_bytes;
+  size_t off_flag;                 // device counter of the finiteness scan
+  double pitch_max = 0.0, dof = 0.0;  // largest layer pitch and Delta^2 / (2 lambda), metres
+  std::string warning;             // plan-time warning ("" if none)
   // optional profiling: one event after every launch (see recon::EventRecorder)
   bool profile = false;
   std::vector<cudaEvent_t> events;
@@ -90,6 +93,7 @@ void recon_default_options(recon_options* o) {
   o->nsr = 0.0;
   o->stage_block = 0;
   o->bp_kernel = RECON_BP_AUTO;
+  o->check_finite = 0;
 }
 
 const char* recon_error_string(int code) {
@@ -100,6 +104,8 @@ const char* recon_error_string(int code) {
     case RECON_E_CUDA: return "CUDA error";
     case RECON_E_WORKSPACE: return "workspace too small or misaligned";
     case RECON_E_NO_MEMORY: return "host allocation failed";
+    case RECON_E_NONFINITE: return "an image holds NaN or Inf";
+    case RECON_E_NO_WEIGHTS: return "the learned filter has no network parameters";
     default: return "unknown status";
   }
 }
@@ -132,8 +138,11 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   if (opts) o = *opts;
   if (o.filter != RECON_FILTER_OFF && o.filter != RECON_FILTER_TIKHONOV && o.filter != RECON_FILTER_MLP)
     return fail(RECON_E_INVALID_ARG, "recon_plan: unknown filter");
-  if (o.filter == RECON_FILTER_MLP && !training && (!o.mlp_weights || !(o.nsr > 0.0) || !std::isfinite(o.nsr)))
-    return fail(RECON_E_INVALID_ARG, "recon_plan: the learned filter needs mlp_weights and nsr > 0");
+  if (o.filter == RECON_FILTER_MLP && !training && !o.mlp_weights)
+    return fail(RECON_E_NO_WEIGHTS, "recon_plan: the learned filter needs mlp_weights (RECON_MLP_PARAMS floats)");
+  if (o.filter == RECON_FILTER_MLP && !training && (!(o.nsr > 0.0) || !std::isfinite(o.nsr)))
+    return fail(RECON_E_INVALID_ARG, "recon_plan: the learned filter needs nsr > 0");
+  if (o.check_finite != 0 && o.check_finite != 1) return fail(RECON_E_INVALID_ARG, "recon_plan: check_finite must be 0 or 1");
   if (o.input_mode != RECON_INPUT_INTENSITY && o.input_mode != RECON_INPUT_CONTRAST)
     return fail(RECON_E_INVALID_ARG, "recon_plan: unknown input_mode");
   if (o.stack_dtype != RECON_STACK_F32 && o.stack_dtype != RECON_STACK_BF16)
@@ -257,11 +266,23 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
       }
       // Per-layer CTF phase constant: chi = pi * [lambda (R_n - z_k) / (P delta)^2] * m^2 + ...
       const double extm = ext * delta;
+      if (extm / nz_layers > p->pitch_max) p->pitch_max = extm / nz_layers;
       for (int k = 0; k < nz_layers; ++k) {
         const double zk = -0.5 * extm + (k + 0.5) * (extm / nz_layers);
         const double Ak = lambda * (defocus[n] - zk) / (PD * PD);
         p->uA[(size_t)n * nz_layers + k] = half_turns_fixed(Ak);
       }
+    }
+    // Depth of field (Sec. 1): a layer thicker than Delta^2 / (2 lambda) holds voxels out of
+    // its own focus; reported as a warning, not an error.
+    p->dof = delta * delta / (2.0 * lambda);
+    if (p->pitch_max > p->dof) {
+      char msg[256];
+      std::snprintf(msg, sizeof msg,
+                    "layer pitch %.4g m exceeds the depth of field Delta^2/(2 lambda) = %.4g m: "
+                    "recon_layers_for_dof gives the Nz that resolves it",
+                    p->pitch_max, p->dof);
+      p->warning = msg;
     }
     // Ramp: (pi/D) delta DFT_P[Ram-Lak](m), m = 0..P/2, with the 1/P^2 of the inverse DFT.
     p->ramp.assign(p->half, 0.0f);
@@ -469,6 +490,8 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   off = align256(off + sizeof(float) * p->cnt.size());
   p->off_x2 = off;
   off = align256(off + sizeof(float) * p->x2.size());
+  p->off_flag = off;
+  off = align256(off + sizeof(unsigned int));
   p->table_bytes = off;
   p->off_S = off;
   off = align256(off + (size_t)ca.sub_block * p->nv * p->half * 8);
@@ -516,6 +539,35 @@ int recon_plan_info(recon_plan_t p, int* padded, int* dir_block, int* n_blocks, 
 
 int recon_destroy(recon_plan_t p) {
   delete p;
+  return RECON_OK;
+}
+
+int recon_plan_dof(recon_plan_t p, double* pitch_max, double* dof) {
+  if (!p) return fail(RECON_E_INVALID_ARG, "recon_plan_dof: null plan");
+  if (pitch_max) *pitch_max = p->pitch_max;
+  if (dof) *dof = p->dof;
+  return RECON_OK;
+}
+
+const char* recon_plan_warning(recon_plan_t p) { return p ? p->warning.c_str() : ""; }
+
+int recon_layers_for_dof(const recon_geometry* geom, const recon_grid* grid, double lambda, double delta, int* nz) {
+  if (!geom || !grid || !nz) return fail(RECON_E_INVALID_ARG, "recon_layers_for_dof: null argument");
+  if (geom->n_dir < 0 || (geom->n_dir > 0 && !geom->rot))
+    return fail(RECON_E_INVALID_ARG, "recon_layers_for_dof: bad geometry");
+  if (!(lambda > 0.0) || !(delta > 0.0) || !std::isfinite(lambda) || !std::isfinite(delta))
+    return fail(RECON_E_INVALID_ARG, "recon_layers_for_dof: lambda and delta must be > 0");
+  if (grid->nx < 0 || grid->ny < 0 || grid->nz < 0) return fail(RECON_E_INVALID_ARG, "recon_layers_for_dof: grid < 0");
+  // Nz >= T_n / DOF for every direction: T_n in voxels times delta over Delta^2 / (2 lambda)
+  const double dof = delta * delta / (2.0 * lambda);
+  double need = 1.0;
+  for (int n = 0; n < geom->n_dir; ++n) {
+    const double* R = geom->rot + 9 * (size_t)n;
+    const double ext = ((std::fabs(R[6]) * grid->nx + std::fabs(R[7]) * grid->ny) + std::fabs(R[8]) * grid->nz) * delta;
+    if (!std::isfinite(ext)) return fail(RECON_E_INVALID_ARG, "recon_layers_for_dof: non-finite rotation");
+    need = std::max(need, std::ceil(ext / dof * (1.0 - 1e-12)));
+  }
+  *nz = need > RECON_MAX_LAYERS ? RECON_MAX_LAYERS : (int)need;
   return RECON_OK;
 }
 
@@ -580,6 +632,22 @@ int upload_tables(recon_plan_t p, const recon::Workspace& w, cudaStream_t s) {
   return RECON_OK;
 }
 
+// Optional finiteness scan of the images: counts NaN / Inf on the GPU, waits for the
+// count and refuses the run if it is not zero.
+int scan_finite(recon_plan_t p, const float* images, unsigned int* d_count, cudaStream_t s, const char* who) {
+  const size_t n = (size_t)p->D * p->nu * p->nv;
+  cudaError_t e = cudaMemsetAsync(d_count, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = recon::launch_count_nonfinite(images, n, d_count, s);
+  unsigned int h_count = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h_count, d_count, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, (std::string(who) + ": finiteness scan").c_str());
+  if (h_count != 0)
+    return fail(RECON_E_NONFINITE, std::string(who) + ": " + std::to_string(h_count) +
+                                       " image values are NaN or Inf; nothing was reconstructed");
+  return RECON_OK;
+}
+
 // Learned regulariser, between the row FFTs and the column kernel of each block: radial
 // power spectrum of every image (column FFTs), then the eps table of the block.
 struct MlpHookCtx {
@@ -622,6 +690,10 @@ int recon_run(recon_plan_t p, const float* images, float* volume, void* workspac
   }
   int rc = check_ws(p, workspace, ws_bytes, "recon_run");
   if (rc) return rc;
+  if (p->opt.check_finite) {
+    rc = scan_finite(p, images, (unsigned int*)((char*)workspace + p->off_flag), s, "recon_run");
+    if (rc) return rc;
+  }
   const recon::Workspace w = carve(p, workspace);
   rc = upload_tables(p, w, s);
   if (rc) return rc;
@@ -774,6 +846,10 @@ int run_in_scratch(recon_plan_t p, const float* images, float* volume, char* scr
       if (e != cudaSuccess) return cuda_fail(e, "recon_run_noalloc: clearing the volume");
     }
     return RECON_OK;
+  }
+  if (p->opt.check_finite) {
+    const int rc = scan_finite(p, images, (unsigned int*)(scratch + p->off_flag), s, "recon_run_noalloc");
+    if (rc) return rc;
   }
   size_t db = 1;
   while ((int)db < p->db && need(db + 1) <= scratch_bytes) ++db;

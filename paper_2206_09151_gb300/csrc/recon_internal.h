@@ -10,6 +10,14 @@ struct recon_plan_s;
 
 namespace recon {
 
+// Streaming multiprocessors of the current device (launch sizing); 1 if the query fails.
+inline int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 1;
+  return sms;
+}
+
 // Voxel tile of the general-geometry backprojection (i, j, k extents).
 constexpr int kGenTile[3] = {32, 8, 8};
 // Fixed-point scale of the detector coordinates in DirParams: 2^-40 pixel.
@@ -106,6 +114,8 @@ struct EventRecorder {
 cudaError_t launch_stage_a(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin,
                            int dir_count, cudaStream_t stream, EventRecorder* rec = nullptr,
                            const StageAHook* hook = nullptr);
+// Adds to *count the number of NaN / Inf values among x[0..n).
+cudaError_t launch_count_nonfinite(const float* x, size_t n, unsigned int* count, cudaStream_t stream);
 // The row FFTs alone (S of `count` images starting at image `first`), P >= 16.
 cudaError_t launch_rows_fwd(const StageAConst& c, float2* S, const float2* twp, const float* images, int first,
                             int count, cudaStream_t stream);

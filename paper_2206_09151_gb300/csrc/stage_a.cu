@@ -465,6 +465,15 @@ __global__ void k_small_rows_inv(const float2* __restrict__ T, PairT* __restrict
   }
 }
 
+// ------------------------------------------------------------------ finiteness scan
+__global__ void k_count_nonfinite(const float* __restrict__ x, size_t n, unsigned int* __restrict__ count) {
+  unsigned int bad = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    bad += isfinite(x[i]) ? 0u : 1u;
+  for (int o = 16; o > 0; o >>= 1) bad += __shfl_down_sync(0xffffffffu, bad, o);
+  if ((threadIdx.x & 31) == 0 && bad) atomicAdd(count, bad);
+}
+
 // ------------------------------------------------------------------ launch
 template <int P>
 cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin, int dir_count,
@@ -474,6 +483,7 @@ cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* i
   // column and the row kernels; each sub-block writes its part of the block's stack.
   const int sub = c.sub_block > 0 ? c.sub_block : dir_count;
   const int col_groups = (c.half + G - 1) / G;
+  const int sms = device_sm_count();
   for (int s0 = 0; s0 < dir_count; s0 += sub) {
     const int cnt = min(sub, dir_count - s0);
     const int d0 = dir_begin + s0;
@@ -484,7 +494,7 @@ cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* i
     }
     if (rec) rec->mark(0, stream);
     // layer groups so that about 2 waves of CTAs run even for a small sub-block
-    const int target = 2 * 152 * 4;
+    const int target = 2 * sms * 4;
     int lgroups = (target + col_groups * cnt - 1) / (col_groups * cnt);
     lgroups = max(1, min(lgroups, c.nz_layers / 2 > 0 ? c.nz_layers / 2 : 1));
     const dim3 gc(col_groups, cnt, lgroups);
@@ -554,6 +564,14 @@ cudaError_t launch_stage_a(const StageAConst& c, const Workspace& ws, const floa
     case 2048: return launch_reg<2048>(c, ws, images, dir_begin, dir_count, stream, ev, hook);
     default: return hook ? cudaErrorInvalidValue : launch_small(c, ws, images, dir_begin, dir_count, stream, ev);
   }
+}
+
+cudaError_t launch_count_nonfinite(const float* x, size_t n, unsigned int* count, cudaStream_t stream) {
+  if (n == 0) return cudaSuccess;
+  const size_t want = (n + 255) / 256;
+  const size_t cap = (size_t)device_sm_count() * 8;
+  k_count_nonfinite<<<(unsigned)(want < cap ? want : cap), 256, 0, stream>>>(x, n, count);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rows_fwd(const StageAConst& c, float2* S, const float2* twp, const float* images, int first,

@@ -27,7 +27,8 @@ class Reconstructor:
                  sigma: float = 0.0, eps: float = 0.1, cs: float = 0.0, filter: str = "tikhonov",
                  input_mode: str = "intensity", stack_dtype: str = "f32", accumulate: bool = False,
                  dir_block: int = 0, ramp: str = "single_axis", mlp_weights=None, nsr: float = 0.0,
-                 stage_block: int = 0, bp_kernel: str = "auto", device=None, allocate: bool = True):
+                 stage_block: int = 0, bp_kernel: str = "auto", check_finite: bool = False, device=None,
+                 allocate: bool = True):
         o = _abi.recon_default_options()
         o.sigma, o.eps, o.cs = float(sigma), float(eps), float(cs)
         o.filter, o.input_mode, o.stack_dtype = _FILTERS[filter], _INPUTS[input_mode], _STACKS[stack_dtype]
@@ -36,6 +37,7 @@ class Reconstructor:
         o.nsr = float(nsr)
         o.stage_block = int(stage_block)
         o.bp_kernel = _BP_KERNELS[bp_kernel]
+        o.check_finite = int(bool(check_finite))
         self._weights = None
         if mlp_weights is not None:
             self._weights = np.ascontiguousarray(mlp_weights, dtype=np.float32)

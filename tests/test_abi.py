@@ -85,8 +85,8 @@ def test_block_sizing_follows_the_per_direction_intermediates(lib):
 
 def test_default_options(lib):
     o = _abi.recon_default_options()
-    assert (o.sigma, o.eps, o.cs, o.filter, o.input_mode, o.stack_dtype, o.accumulate, o.dir_block) == \
-        (0.0, 0.1, 0.0, 1, 0, 0, 0, 0)
+    assert (o.sigma, o.eps, o.cs, o.filter, o.input_mode, o.stack_dtype, o.accumulate, o.dir_block,
+            o.check_finite) == (0.0, 0.1, 0.0, 1, 0, 0, 0, 0, 0)
 
 
 @pytest.mark.parametrize("kw,code", [
@@ -140,8 +140,53 @@ def test_null_arguments_are_errors_not_crashes(lib):
 
 
 def test_error_strings(lib):
-    for c in (0, -1, -2, -3, -4, -5):
-        assert _abi.recon_error_string(c)
+    texts = {_abi.recon_error_string(c) for c in (0, -1, -2, -3, -4, -5, -6, -7)}
+    assert len(texts) == 8 and "unknown status" not in texts
+
+
+def test_learned_filter_without_weights_is_its_own_error(lib):
+    o = _abi.recon_default_options()
+    o.filter = _abi.RECON_FILTER_MLP
+    o.nsr = 0.1
+    with pytest.raises(_abi.ReconError) as e:
+        _plan(opts=o)
+    assert e.value.code == _abi.RECON_E_NO_WEIGHTS
+    w = (ctypes.c_float * _abi.RECON_MLP_PARAMS)()
+    o.mlp_weights = ctypes.cast(w, ctypes.POINTER(ctypes.c_float))
+    o.nsr = 0.0
+    with pytest.raises(_abi.ReconError) as e:
+        _plan(opts=o)
+    assert e.value.code == _abi.RECON_E_INVALID_ARG
+
+
+def test_check_finite_option_is_validated(lib):
+    o = _abi.recon_default_options()
+    o.check_finite = 2
+    with pytest.raises(_abi.ReconError) as e:
+        _plan(opts=o)
+    assert e.value.code == _abi.RECON_E_INVALID_ARG
+    o.check_finite = 1
+    _abi.recon_destroy(_plan(opts=o))
+
+
+def test_depth_of_field_report_and_layer_count(lib):
+    """DOF = Delta^2 / (2 lambda) (Sec. 1).  A 64^3 single-axis scan with Delta = 1 nm,
+    lambda = 0.1 nm: DOF = 5 nm; the bounding-box extent along a beam at angle t in the
+    x-z plane is 64 (|cos t| + |sin t|) nm, largest (64 sqrt 2 = 90.5 nm) at 45 degrees."""
+    rot = ph.single_axis_rotations(4)  # 0, 45, 90, 135 degrees
+    grid, lam, delta = (64, 64, 64), 1e-10, 1e-9
+    assert _abi.recon_layers_for_dof(rot, grid, lam, delta) == 19  # ceil(90.51 / 5)
+    assert _abi.recon_layers_for_dof(rot[:1], grid, lam, delta) == 13  # ceil(64 / 5)
+    assert _abi.recon_layers_for_dof(rot, grid, lam, 1e-8) == 2  # 905 nm thick, DOF 500 nm
+    assert _abi.recon_layers_for_dof(rot, grid, lam, 2e-8) == 1  # 1810 nm thick, DOF 2000 nm
+    assert _abi.recon_layers_for_dof(rot, (4096, 4096, 4096), 1e-10, 1e-9) == _abi.RECON_MAX_LAYERS
+    for nz, warn in ((8, True), (19, False)):
+        p = _plan(rot=rot, nu=64, nv=64, defocus=np.full(4, 1e-7), nz_layers=nz, grid=grid)
+        h, dof = _abi.recon_plan_dof(p)
+        assert dof == pytest.approx(5e-9, rel=1e-12)
+        assert h == pytest.approx(64 * np.sqrt(2) * 1e-9 / nz, rel=1e-9)
+        assert (_abi.recon_plan_warning(p) != "") == warn
+        _abi.recon_destroy(p)
 
 
 def test_training_config_is_validated_on_the_host(lib):

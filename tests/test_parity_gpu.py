@@ -200,6 +200,27 @@ def test_accumulate_adds_and_empty_scan_clears():
     e.close()
 
 
+def test_check_finite_refuses_nan_and_inf_images():
+    """check_finite: a NaN or an Inf anywhere in the images is reported as
+    RECON_E_NONFINITE before anything is written; clean images run as usual."""
+    from paper_2206_09151_gb300 import _abi
+    cfg, img = _small_workload(n_dir=6)
+    r = make(cfg["rot"], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
+             defocus=cfg["defocus"], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"], eps=cfg["eps"],
+             check_finite=True)
+    good = r.run(torch.from_numpy(img).cuda()).clone()
+    assert torch.isfinite(good).all()
+    for bad_value, where in ((float("nan"), (5, 63, 0)), (float("inf"), (0, 0, 17))):
+        bad = img.copy()
+        bad[where] = bad_value
+        vol = torch.full_like(good, 7.0)
+        with pytest.raises(_abi.ReconError) as e:
+            r.run(torch.from_numpy(bad).cuda(), vol)
+        assert e.value.code == _abi.RECON_E_NONFINITE
+        assert bool((vol == 7.0).all())
+    r.close()
+
+
 def test_filter_off_is_independent_of_layer_count():
     """Filter off: every layer is the same ramp-filtered image, so Nz = 4 and Nz = 1 give
     bitwise the same volume (conventional FBP, Eq. 15)."""

@@ -5,6 +5,8 @@ in processes whose allocator owns every byte).  It works in the library's static
 device scratch; here it is called twice in a row through the C-ABI and each result is
 checked against recon_run with a caller-provided workspace, within the float32 parity
 tolerance of the other tests.  This file is collected last on purpose."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -47,6 +49,36 @@ def test_noalloc_run_matches_recon_run_twice(n, D, nzl):
     _abi.recon_run(plan, img.data_ptr(), ref.data_ptr(), ws.data_ptr(), ws_bytes, stream)
     for _ in range(2):
         vol = torch.full((nz, ny, nx), float("nan"), device="cuda")
+        _abi.recon_run_noalloc(plan, img.data_ptr(), vol.data_ptr(), stream)
+        _abi.recon_sync(stream)
+        assert torch.isfinite(vol).all()
+        assert rel_l2(vol, ref) <= TOL_F32
+    _abi.recon_destroy(plan)
+
+
+def test_noalloc_learned_filter_bf16_density_matches_recon_run_twice():
+    """The learned regulariser keeps its power spectra and eps table in the static scratch
+    (after the stacks), the bfloat16 stack and the sampling-density grid too: 64^2 images,
+    Nz = 4, 24 directions of a 60-degree cone, against recon_run with its own workspace."""
+    n, D, nzl = 64, 24, 4
+    rot = ph.cone_rotations(D, 60.0, seed=11)
+    rng = np.random.default_rng(5)
+    img = torch.from_numpy((1.0 + 1e-2 * rng.standard_normal((D, n, n))).astype(np.float32)).cuda()
+    w = ph.mlp_init(17).astype(np.float32)
+    opts = _abi.recon_default_options()
+    opts.sigma, opts.filter, opts.nsr = 0.07, _abi.RECON_FILTER_MLP, 0.1
+    opts.stack_dtype, opts.ramp_mode = _abi.RECON_STACK_BF16, _abi.RECON_RAMP_DENSITY
+    opts.dir_block = 5  # several blocks on the caller-owned path
+    opts.mlp_weights = w.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    grid = (n, n, 32)
+    plan = _abi.recon_plan(rot, n, n, 1.97e-12, 1e-10, np.full(D, 1e-6), nzl, grid, opts)
+    ws_bytes = _abi.recon_workspace_size(plan)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    ref = torch.empty((grid[2], grid[1], grid[0]), device="cuda")
+    _abi.recon_run(plan, img.data_ptr(), ref.data_ptr(), ws.data_ptr(), ws_bytes, stream)
+    for _ in range(2):
+        vol = torch.full_like(ref, float("nan"))
         _abi.recon_run_noalloc(plan, img.data_ptr(), vol.data_ptr(), stream)
         _abi.recon_sync(stream)
         assert torch.isfinite(vol).all()
