@@ -176,12 +176,13 @@ def sample_voxels(cfg):
     return rng.integers(0, nx, n), rng.integers(0, ny, n), rng.integers(0, nz, n)
 
 
-def oracle_sample(cfg, images_np, dirs, mlp=None, voxels=None):
+def oracle_sample(cfg, images_np, dirs, mlp=None, voxels=None, workers: int = 1):
     """FP64 oracle on the directions ``dirs`` alone (a D = len(dirs) scan), at ``voxels`` or
-    over the full volume; ``mlp`` = (weights, nsr) selects the learned regulariser."""
+    over the full volume, in ``workers`` processes; ``mlp`` = (weights, nsr) selects the
+    learned regulariser."""
     import oracle as O
     kw = dict(lam=cfg["lam"], delta=cfg["delta"], defocus=cfg["defocus"][dirs], nz_layers=cfg["nz_layers"],
-              grid=cfg["grid"], sigma=cfg["sigma"], cs=cfg["cs"], voxels=voxels,
+              grid=cfg["grid"], sigma=cfg["sigma"], cs=cfg["cs"], voxels=voxels, workers=workers,
               density=cfg.get("ramp", "single_axis") == "density")
     if mlp is not None:
         return O.learned.recon_learned(images_np[dirs], cfg["rot"][dirs], mlp[0].astype(np.float64), nsr=mlp[1],
@@ -190,6 +191,33 @@ def oracle_sample(cfg, images_np, dirs, mlp=None, voxels=None):
 
 
 # ----------------------------------------------------------------------------- reference arm
+def host_cpu() -> tuple[int, str]:
+    """Host cores the oracle's process pool uses, and the CPU model."""
+    cores = os.cpu_count() or 1
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                             timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return cores, model
+
+
+def oracle_timed(cfg, images_np, dirs, workers, mlp=None, voxels=None):
+    """The FP64 oracle on the directions ``dirs`` (a scan of its own) over ``voxels``,
+    spread over ``workers`` spawned processes; returns (result, wall seconds)."""
+    t0 = time.perf_counter()
+    ref = oracle_sample(cfg, images_np, dirs, mlp, voxels, workers)
+    return ref, time.perf_counter() - t0
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -200,32 +228,32 @@ def run_reference(args):
         cfg = ph.batch_workloads()[0]
     else:
         cfg = workload(args.workload)
+    cores, model = host_cpu()
     vox = sample_voxels(cfg)
     V = int(np.prod(cfg["grid"])) if vox is None else vox[0].size
     D = cfg["n_dir"]
-    per_step = max(1, args.ref_dirs)
-    plan = [[((s * per_step + q) * 97) % D for q in range(per_step)] for s in range(args.warmup + args.steps)]
-    need = sorted({d for ds in plan for d in ds})
+    # one direction per step; the warm-up steps and then the timed steps each run as one
+    # batch of directions spread over the host cores
+    order = [(s * 97) % D for s in range(args.warmup + args.steps)]
+    need = sorted(set(order))
     sub = dict(cfg, rot=cfg["rot"][need], defocus=cfg["defocus"][need])
     images = np.zeros((D, cfg["nv"], cfg["nu"]), np.float32)
     images[need] = make_images(sub, "cpu").numpy()  # only the sampled views are simulated
-    times = []
-    for s, dirs in enumerate(plan):
-        t0 = time.perf_counter()
-        oracle_sample(cfg, images, dirs, voxels=vox)
-        dt = time.perf_counter() - t0
-        if s >= args.warmup:
-            times.append(dt)
-    t = sum(times) / len(times)
-    value = V * per_step / t
+    warm, timed = order[:args.warmup], order[args.warmup:]
+    oracle_timed(cfg, images, warm, min(cores, len(warm)), voxels=vox)
+    _, t = oracle_timed(cfg, images, timed, min(cores, len(timed)), voxels=vox)
+    value = V * len(timed) / t
     where = "the full volume" if vox is None else f"{V} random voxels"
-    sample = (f"{per_step} direction(s) per step over {where} of the {'x'.join(map(str, cfg['grid']))} grid"
-              + (" (first tomogram of the batch)" if args.workload == "batch" else "") + ", FP64 numpy, 1 thread")
+    sample = (f"{len(timed)} directions (one per step) over {where} of the {'x'.join(map(str, cfg['grid']))} grid"
+              + (" (first tomogram of the batch)" if args.workload == "batch" else "")
+              + f", FP64 numpy oracle in {min(cores, len(timed))} spawned processes on {cores} host cores ({model});"
+              f" each direction's FFT / per-layer filter work is done in full, the backprojection on the voxel set")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3 / len(timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload], "sample": sample},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": min(cores, len(timed)), "host_cores": cores,
+                             "cpu_model": model, "kind": "oracle", "sample": sample, "seconds": t},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     del torch
     print(json.dumps(line))
@@ -444,14 +472,15 @@ def run_ours(args):
             "gpu_launches": sum(kern_n) + (2 * kern_n[0] if args.filter == "mlp" else 0), "roofline": roofline, "kernels": kernels, "clocks": clocks}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # the oracle on a bounded sample (a few directions, full volume), beside the same
-        # sample reconstructed on the GPU: the stated accuracy and the CPU rate
-        sel = [int(x) for x in np.linspace(0, D - 1, args.cpu_dirs).round()]
+        # the oracle on a bounded sample (a few directions spread over the host cores), beside
+        # the same sample reconstructed on the GPU: the stated accuracy and the CPU rate
+        cores, model = host_cpu()
+        n_sel = args.cpu_dirs if args.cpu_dirs else cores
+        sel = [int(x) for x in np.linspace(0, D - 1, n_sel).round()]
         img_np = images.cpu().numpy()
         vox = sample_voxels(cfg)
-        t0 = time.perf_counter()
-        ref = oracle_sample(cfg, img_np, sel, mlp, vox)
-        dt = time.perf_counter() - t0
+        workers = min(cores, len(sel))
+        ref, dt = oracle_timed(cfg, img_np, sel, workers, mlp, vox)
         rs = Reconstructor(cfg["rot"][sel], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
                            defocus=cfg["defocus"][sel], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"],
                            eps=cfg["eps"], cs=cfg["cs"], stack_dtype=args.stack, ramp=cfg["ramp"], device=dev,
@@ -465,9 +494,11 @@ def run_ours(args):
             got = got[tuple(torch.as_tensor(x, device=dev) for x in vox[::-1])].cpu().numpy()
             n_vox, where = vox[0].size, f"{vox[0].size} random voxels"
         rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
-        sample = f"{len(sel)} of {D} directions over {where} ({len(sel) * n_vox:.3e} updates), FP64 numpy"
-        line["cpu_baseline"] = {"value": len(sel) * n_vox / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": sample, "seconds": dt}
+        sample = (f"{len(sel)} of {D} directions (a scan of their own) over {where} ({len(sel) * n_vox:.3e} updates),"
+                  f" FP64 numpy oracle in {workers} spawned processes on {cores} host cores ({model}); each "
+                  f"direction's FFT / per-layer filter work is done in full")
+        line["cpu_baseline"] = {"value": len(sel) * n_vox / dt, "unit": UNIT, "cores": workers, "host_cores": cores,
+                                "cpu_model": model, "kind": "oracle", "sample": sample, "seconds": dt}
         line["accuracy"] = {"rel_l2_vs_fp64_oracle": rel, "sample": sample,
                             "target": 1e-5 if args.stack == "f32" else 3e-3}
     if rank == 0:
@@ -590,7 +621,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=list(WORKLOAD_TEXT), default="mid")
+    ap.add_argument("--workload", choices=list(WORKLOAD_TEXT), default="slab",
+                    help="slab (the default) is the largest single-GPU workload")
     ap.add_argument("--stack", choices=["f32", "bf16"], default=None,
                     help="layer-stack precision (default: the workload's, f32 for mid/small, bf16 otherwise)")
     ap.add_argument("--filter", choices=["tikhonov", "mlp"], default="tikhonov",
@@ -601,15 +633,12 @@ def main():
                     help="single-axis backprojection variant")
     ap.add_argument("--dirs", type=int, default=None, help="first N directions only (small profiling cases)")
     ap.add_argument("--cpu-dirs", type=int, default=None, help="oracle directions of the CPU baseline "
-                    "(default 3, 1 for the 512^3 and slab workloads)")
-    ap.add_argument("--ref-dirs", type=int, default=1)
+                    "(default: one per host core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
     if args.stack is None:
         args.stack = DEFAULT_STACK[args.workload]
-    if args.cpu_dirs is None:
-        args.cpu_dirs = 1 if args.workload in ("learned", "slab") else 3
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":

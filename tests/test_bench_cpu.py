@@ -26,7 +26,18 @@ def test_reference_arm_prints_one_contract_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
-    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and 1 <= cb["cores"] <= cb["host_cores"] == (os.cpu_count() or 1)
+    assert cb["cores"] == min(os.cpu_count() or 1, 1) and cb["cpu_model"]  # one timed step, one process
+    assert cb["value"] == d["value"] and cb["seconds"] > 0
+
+
+def test_default_workload_is_the_largest_single_gpu_one():
+    """With no flags the bench measures the 1024 x 1024 x 256 slab under 1500 views."""
+    import bench
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    assert 'choices=list(WORKLOAD_TEXT), default="slab"' in src
+    assert "1024x1024x256" in bench.WORKLOAD_TEXT["slab"] and "1500" in bench.WORKLOAD_TEXT["slab"]
 
 
 def test_work_counts_follow_the_shapes():
