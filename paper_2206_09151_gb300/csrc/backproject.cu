@@ -21,6 +21,8 @@ namespace recon {
 namespace {
 
 constexpr int kTX = kGenTile[0], kTY = kGenTile[1], kTZ = kGenTile[2];
+static_assert(kTX % 8 == 0 && kTY % 4 == 0 && (kTX / 8) * (kTY / 4) * 32 == kTX * kTY,
+              "the 8 x 4 warp patches must tile the voxel columns");
 
 // Integer pixel (floor) and FP32 fraction of a coordinate in 2^-40 pixel units.
 __device__ __forceinline__ int pix_floor(long long x) { return (int)(x >> kPixFracBits); }
@@ -67,7 +69,8 @@ __device__ __forceinline__ void generic_run(const TileDir& td, const ST* __restr
     const int rb = __float_as_int(tb) - kMagicBits;
     const float fa = CLAMP ? __saturatef(ap - (ta - kMagic) + 0.5f) : ap - (ta - kMagic) + 0.5f;
     const float fb = CLAMP ? __saturatef(bp - (tb - kMagic) + 0.5f) : bp - (tb - kMagic) + 0.5f;
-    const ST* p = base + (size_t)layer * c.layer_elems + (ptrdiff_t)rb * c.su + ra;
+    // one direction's stack holds at most 96 x 1026 x 1025 entries: 32-bit offsets
+    const ST* p = base + (layer * (int)c.layer_elems + rb * c.su + ra);
     const float2 r0 = stack_pair(p), r1 = stack_pair(p + c.su);
     const float top = fmaf(fa, r0.y - r0.x, r0.x);
     const float bot = fmaf(fa, r1.y - r1.x, r1.x);
@@ -85,7 +88,12 @@ __device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const Di
                                                 int dir_begin, int dir_count, float* __restrict__ vol,
                                                 int accumulate, TileDir* s_dir) {
   const int i0 = bx * kTX, j0 = by * kTY, k0 = bz * kTZ;
-  const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+  // a warp covers an 8 (x) x 4 (y) patch of voxel columns rather than a line of 32: its
+  // samples in one z plane fall on a compact detector patch in any view orientation, so
+  // a row gather touches fewer cache lines
+  constexpr int kWX = 8, kWY = 32 / kWX;
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int tx = (w % (kTX / kWX)) * kWX + (l % kWX), ty = (w / (kTX / kWX)) * kWY + l / kWX;
   for (int d = threadIdx.x; d < dir_count; d += blockDim.x) {
     const DirParams& p = dirs[dir_begin + d];
     // tile origin on the detector: exact integer sums in 2^-40 pixel

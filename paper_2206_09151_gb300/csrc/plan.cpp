@@ -307,7 +307,23 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
     }
     // per-pass twiddles of the register FFT: pass at sub-length Ns (radix R) holds
     // exp(-2 pi i kb r / (Ns R)) at (Ns - 8) + kb (R - 1) + (r - 1)
-    p->twp.assign(P >= 16 ? P - 8 : 1, float2{0.f, 0.f});
+    // For P >= 256 the table of the 16-value FFT (fft16.cuh) follows it: the pass at
+    // sub-length Ns (radix R, first radix 16) at (P - 8) + (Ns - 16) + kb (R - 1) + (r - 1).
+    p->twp.assign(P >= 16 ? (P - 8) + (P >= 256 ? P - 16 : 0) : 1, float2{0.f, 0.f});
+    if (P >= 256) {
+      for (int Ns = 1; Ns < P;) {
+        const int rem = P / Ns;
+        const int R = (rem % 16 == 0) ? 16 : rem;
+        if (Ns > 1)
+          for (int kb = 0; kb < Ns; ++kb)
+            for (int r = 1; r < R; ++r) {
+              const double ang = -2.0 * M_PI * (double)kb * r / ((double)Ns * R);
+              p->twp[(P - 8) + (Ns - 16) + kb * (R - 1) + (r - 1)] =
+                  float2{(float)std::cos(ang), (float)std::sin(ang)};
+            }
+        Ns *= R;
+      }
+    }
     if (P >= 16) {
       for (int Ns = 1; Ns < P;) {
         const int rem = P / Ns;
@@ -432,17 +448,20 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   const size_t inter_dir = (size_t)p->nv * p->half * 8 * (1 + (size_t)nz_layers);
   const size_t per_dir = inter_dir + p->stack_dir_bytes;
   // Where one direction's intermediates are large (big images, many layers), stage A runs
-  // in sub-blocks whose intermediates fit 1 GiB by default, and the rest of the budget
-  // holds stacks: a larger direction block means fewer volume read-modify-writes and tile
-  // set-ups in the backprojection (1024^2 images, Nz = 64: 13 instead of 5 directions).
+  // in sub-blocks whose intermediates fit 2 GiB by default (two directions of 1024^2 images
+  // with Nz = 64: the column stage then fills the GPU with fewer layer groups, each of which
+  // repeats a column's forward FFT), and the rest of the budget holds stacks: a larger
+  // direction block means fewer volume read-modify-writes and tile set-ups in the
+  // backprojection.
   const bool big_dir = inter_dir > ((size_t)64 << 20);
   int auto_sub = 0;
-  if (big_dir && o.stage_block == 0) auto_sub = (int)std::max<size_t>(1, ((size_t)1 << 30) / inter_dir);
+  if (big_dir && o.stage_block == 0) auto_sub = (int)std::max<size_t>(1, ((size_t)2 << 30) / inter_dir);
   int db = o.dir_block;
   if (db == 0) {
-    // as many directions per block as a 4 GiB stage budget holds (fewer volume
-    // read-modify-writes), then balanced so that the blocks are of equal size
-    const size_t budget = (size_t)4 << 30;
+    // as many directions per block as the stage budget holds (fewer volume
+    // read-modify-writes), then balanced so that the blocks are of equal size: 4 GiB, or
+    // 8 GiB where one direction's intermediates are large
+    const size_t budget = (size_t)(big_dir ? 8 : 4) << 30;
     if (auto_sub > 0) {
       const size_t used = (size_t)auto_sub * inter_dir;
       db = used < budget ? (int)std::min<size_t>((budget - used) / p->stack_dir_bytes, 1024) : 1;

@@ -77,7 +77,8 @@ struct Workspace {
   uint64_t* uA;         // [D][Nz]: pi lambda (R_n - z_k)/(P delta)^2 per unit m, fraction of 2 pi
   float* ramp;          // [P/2+1]: ramp weight, includes pi/D and 1/P^2
   float2* tw;           // [P]: exp(-2 pi i j / P)
-  float2* twp;          // [P - 8]: per-pass twiddles of the register FFT (fft_reg.cuh), P >= 16
+  float2* twp;          // [P - 8]: per-pass twiddles of the register FFT (fft_reg.cuh), P >= 16,
+                        // then for P >= 256 [P - 16] of the 16-value FFT (fft16.cuh)
   float2* S;            // [DB][nv][P/2+1]: row transforms
   float2* T;            // [DB][Nz][P/2+1][nv]: per-layer column inverse transforms (column-major)
   void* stack;          // [DB][Nz][nv+2][nu+1] tap pairs (Y[v][u-1], Y[v][u]), zero outside

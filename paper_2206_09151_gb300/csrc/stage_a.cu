@@ -16,7 +16,10 @@
 // circular filters this equals any other placement with the same crop.
 #include <cuda_bf16.h>
 
+#include <cmath>
+
 #include "density.cuh"
+#include "fft16.cuh"
 #include "fft_reg.cuh"
 #include "recon_internal.h"
 
@@ -327,6 +330,268 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(const float2* __restrict_
     for (int i = threadIdx.x; i < sp; i += kThreads) Lk[(size_t)(c.nv + 1) * sp + i] = make_pair<PairT>(0.f, 0.f);
 }
 
+
+// ------------------------------------------------------------------ 16-value kernels (P >= 1024)
+// The same column and row stages with the 16-value FFT of fft16.cuh: three passes and two
+// exchanges per length-2048 transform instead of four and three, exchange addresses that
+// are a per-thread base plus constants, and (in the column kernel) double-buffered
+// exchanges, so two group barriers per transform instead of six.
+constexpr int kThreads16 = 256;
+
+template <int P>
+__host__ __device__ constexpr int cols16_per_cta() {
+  return kThreads16 / (P / 16);
+}
+
+// Column stage: a group of P/16 threads per spectrum column, cols16_per_cta columns per CTA.
+// The forward FFT along v stays in registers, multiplied once by the column's weight (ramp
+// or density weight, with the filter prefactor and 1/P^2); per layer: the CTF filter,
+// inverse FFT, store v < nv.
+template <int P, int FILT, bool DENS>
+__global__ void __launch_bounds__(kThreads16, 2) k_cols16(const float2* __restrict__ S, float2* __restrict__ T,
+                                                          const float2* __restrict__ twg,
+                                                          const uint64_t* __restrict__ uA,
+                                                          const float* __restrict__ ramp,
+                                                          const DirParams* __restrict__ dirs,
+                                                          const float* __restrict__ dens,
+                                                          const double* __restrict__ band_sum,
+                                                          const float* __restrict__ eps_tab, int n_bins,
+                                                          int bin_width, StageAConst c, int dir_begin) {
+  constexpr int TT = P / 16, CB = cols16_per_cta<P>(), L = fft16::buffer_len(P), NT = fft16::table_len(P);
+  extern __shared__ float2 smem16[];
+  float2* tw = smem16;
+  const int g = threadIdx.x / TT, j = threadIdx.x % TT;
+  float2* buf0 = smem16 + NT + (2 * g) * L;
+  float2* buf1 = buf0 + L;
+  for (int i = threadIdx.x; i < NT; i += kThreads16) tw[i] = twg[i];
+  const int n = blockIdx.y;
+  const int col = blockIdx.x * CB + g;
+  const bool ok = col < c.half;
+  const int colc = ok ? col : c.half - 1;
+  const float2* Sn = S + (size_t)n * c.nv * c.half;
+  float2 xg[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    const int v = j + s * TT;
+    xg[s] = v < c.nv ? Sn[(size_t)v * c.half + colc] : make_float2(0.f, 0.f);
+  }
+  __syncthreads();  // twiddle table
+  const fft::GroupSync gsync{1 + g, TT};
+  fft16::group_fft_db<P, false>(xg, buf0, buf1, tw, j, gsync);  // G(col, m_v) at m_v = j + s*TT
+  // ramp (single-axis scans) or sampling-density weight (any geometry), 1/P^2 included, and
+  // with a filter its prefactor lambda / (4 pi sqrt(1+sigma^2)): layer-independent, so
+  // folded into the spectrum once
+  {
+    const float pref = FILT != 0 ? c.pref : 1.f;
+    if constexpr (DENS) {
+      const DirParams& dp = dirs[dir_begin + n];
+#pragma unroll
+      for (int s = 0; s < 16; ++s) {
+        const int m = j + s * TT;
+        const int mv = m < P / 2 ? m : m - P;
+        float wv = density_weight(c.dens, dens, band_sum, dp.af, dp.bf, (float)colc, (float)mv);
+        const bool nyq_u = colc == P / 2, nyq_v = m == P / 2;  // the Nyquist bin is its own alias
+        if (nyq_u || nyq_v) {
+          const float w2 = density_weight(c.dens, dens, band_sum, dp.af, dp.bf, nyq_u ? -(float)colc : (float)colc,
+                                          (nyq_v && !nyq_u) ? -(float)mv : (float)mv);
+          wv = 0.5f * (wv + w2);
+        }
+        wv *= pref;
+        xg[s] = make_float2(xg[s].x * wv, xg[s].y * wv);
+      }
+    } else {
+      const float wv = ramp[colc] * pref;
+#pragma unroll
+      for (int s = 0; s < 16; ++s) xg[s] = make_float2(xg[s].x * wv, xg[s].y * wv);
+    }
+  }
+  // chi/(2 pi) in 2^-32 turns (top 32 bits of the 64-bit fixed-point phase): per layer
+  // hi(uA_k) m + umulhi(lo(uA_k), m), plus the layer-independent uC m^2 - uW
+  uint32_t msq[16], base_hi[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    const int m = j + s * TT;
+    const int mv = m < P / 2 ? m : m - P;
+    const uint32_t q2 = (uint32_t)(colc * colc + mv * mv);
+    const uint64_t m64 = q2;
+    base_hi[s] = (uint32_t)((c.uC * (m64 * m64) - c.uW) >> 32);
+    if constexpr (FILT == 2) {  // radial bin (exact isqrt) packed above the 22-bit m
+      int r = (int)sqrtf((float)q2);
+      while ((uint32_t)r * (uint32_t)r > q2) --r;
+      while ((uint32_t)(r + 1) * (uint32_t)(r + 1) <= q2) ++r;
+      const int b = min(r / bin_width, n_bins - 1);
+      msq[s] = q2 | ((uint32_t)b << 22);
+    } else {
+      msq[s] = q2;
+    }
+  }
+  const uint64_t* uAn = uA + (size_t)(dir_begin + n) * c.nz_layers;
+  float2* Tn = T + (size_t)n * c.nz_layers * c.half * c.nv;
+  const int lg = (c.nz_layers + gridDim.z - 1) / gridDim.z;
+  const int k_begin = blockIdx.z * lg;
+  const int k_end = min(c.nz_layers, k_begin + lg);
+  for (int k = k_begin; k < k_end; ++k) {
+    const uint64_t uAk = uAn[k];
+    const uint32_t a_hi = (uint32_t)(uAk >> 32), a_lo = (uint32_t)uAk;
+    const float* eps_k = eps_tab + ((size_t)n * c.nz_layers + k) * n_bins;
+    float2 x[16];
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+      if constexpr (FILT != 0) {
+        const uint32_t q2 = FILT == 2 ? (msq[s] & 0x3FFFFFu) : msq[s];
+        const uint32_t hi = a_hi * q2 + __umulhi(a_lo, q2) + base_hi[s];
+        const float sn = sin_half_turns((int32_t)hi);
+        float e;
+        if constexpr (FILT == 2) e = __ldg(eps_k + (msq[s] >> 22));  // learned eps
+        else e = c.eps;                                             // Tikhonov eps
+        const float f = __fdividef(sn, fmaf(sn, sn, e));           // real part of the Eq. 11 bracket
+        x[s] = make_float2(xg[s].x * f, xg[s].y * f);
+      } else {
+        x[s] = xg[s];
+      }
+    }
+    fft16::group_fft_db<P, true>(x, buf0, buf1, tw, j, gsync);
+    if (ok) {
+      float2* out = Tn + ((size_t)k * c.half + col) * c.nv;
+#pragma unroll
+      for (int s = 0; s < 16; ++s) {
+        const int v = j + s * TT;
+        if (v < c.nv) out[v] = x[s];
+      }
+    }
+  }
+}
+
+template <int P, int FILT, bool DENS>
+constexpr size_t cols16_smem() {
+  return sizeof(float2) * ((size_t)fft16::table_len(P) + 2 * (size_t)cols16_per_cta<P>() * fft16::buffer_len(P));
+}
+
+// Row stage: four row pairs (eight detector rows) of one layer per CTA, a group of P/16
+// threads per pair.  The CTA reads eight consecutive v of every column of T (64 bytes per
+// column), Hermitian-extends both half spectra of a pair, packs them as real + i real,
+// inverse FFT, crop u < nu, stores tap pairs.
+constexpr int kRowPairs16 = 4;
+
+template <int P>
+__host__ __device__ constexpr int rows16_threads() {
+  return kRowPairs16 * (P / 16);
+}
+
+template <int P>
+__host__ __device__ constexpr int rows16_tile_stride() {
+  // stride = 2 (mod 16) float2: a half-warp of the fill (8 rows x 2 columns) writes 16
+  // distinct bank pairs
+  return (P / 2 + 1) + ((2 - (P / 2 + 1) % 16) % 16 + 16) % 16;
+}
+
+template <int P>
+constexpr size_t rows16_smem() {
+  constexpr size_t tile = (size_t)2 * kRowPairs16 * rows16_tile_stride<P>();
+  constexpr size_t bufs = (size_t)kRowPairs16 * fft16::buffer_len(P);
+  return sizeof(float2) * ((size_t)fft16::table_len(P) + (tile > bufs ? tile : bufs));
+}
+
+template <int P, typename PairT>
+__global__ void __launch_bounds__(rows16_threads<P>(), 2) k_rows_inv16(const float2* __restrict__ T,
+                                                                        PairT* __restrict__ stack,
+                                                                        const float2* __restrict__ twg,
+                                                                        StageAConst c) {
+  constexpr int TT = P / 16, NTH = rows16_threads<P>(), H = P / 2 + 1, HS = rows16_tile_stride<P>();
+  constexpr int ROWS = 2 * kRowPairs16, L = fft16::buffer_len(P), NT = fft16::table_len(P);
+  constexpr int USED = ROWS * H;
+  constexpr int FILL = (USED + NTH - 1) / NTH;
+  extern __shared__ float2 smem16[];
+  float2* tw = smem16;
+  // the half-spectrum tile is read once, before the first exchange: the exchange buffers
+  // reuse its memory
+  float2* tile = smem16 + NT;
+  const int g = threadIdx.x / TT, j = threadIdx.x % TT;
+  float2* buf = smem16 + NT + g * L;
+  for (int i = threadIdx.x; i < NT; i += NTH) tw[i] = twg[i];
+  const int n = blockIdx.z, k = blockIdx.y;
+  const int vbase = blockIdx.x * ROWS;
+  const float2* Tk = T + ((size_t)n * c.nz_layers + k) * H * c.nv;
+  {  // all loads in flight before the shared stores
+    float2 tmp[FILL];
+#pragma unroll
+    for (int it = 0; it < FILL; ++it) {
+      const int idx = threadIdx.x + it * NTH;
+      const int vv = idx % ROWS, cc = idx / ROWS;
+      const int v = vbase + vv;
+      tmp[it] = (idx < USED && v < c.nv) ? Tk[(size_t)cc * c.nv + v] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int it = 0; it < FILL; ++it) {
+      const int idx = threadIdx.x + it * NTH;
+      if (idx < USED) tile[(idx % ROWS) * HS + idx / ROWS] = tmp[it];
+    }
+  }
+  __syncthreads();
+  const int v0 = vbase + 2 * g;
+  const float2* X1 = tile + (2 * g) * HS;
+  const float2* X2 = X1 + HS;
+  float2 x[16];
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    const int m = j + s * TT;
+    float2 a, b;
+    if (m <= P / 2) {
+      a = X1[m];
+      b = X2[m];
+      if (m == 0 || m == P / 2) {  // C2R: DC and Nyquist bins are real
+        a.y = 0.f;
+        b.y = 0.f;
+      }
+    } else {  // Hermitian extension X[m] = conj X[P - m]
+      a = X1[P - m];
+      b = X2[P - m];
+      a.y = -a.y;
+      b.y = -b.y;
+    }
+    x[s] = make_float2(a.x - b.y, a.y + b.x);  // a + i b
+  }
+  __syncthreads();  // every group has read its rows: the tile is free for the exchange buffers
+  const fft::GroupSync gsync{1 + g, TT};
+  fft16::group_fft_sb<P, true>(x, buf, tw, j, gsync);
+  // rows v0 (real part) and v0 + 1 (imaginary part) at u = j + s*TT.  The tap pair of column
+  // cc = j + s*TT is (Y[cc - 1], Y[cc]): the left value comes from lane l - 1 by a warp
+  // shuffle; lane 0 takes the last lane of the group's previous warp (same s), and thread 0
+  // the group's last thread at s - 1, both published through the exchange buffer.
+  gsync();  // the last pass's reads of the buffer are done
+  const int lane = threadIdx.x & 31, wg = j >> 5;
+  float2* edge = buf;  // [TT / 32][16]
+  if (lane == 31) {
+#pragma unroll
+    for (int s = 0; s < 16; ++s) edge[wg * 16 + s] = x[s];
+  }
+  gsync();
+  PairT* Lk = stack + ((size_t)n * c.nz_layers + k) * c.layer_elems;
+  const int sp = c.su;
+  const bool row1 = v0 < c.nv, two = v0 + 1 < c.nv;
+  PairT* r1 = Lk + (size_t)(v0 + 1) * sp;
+  PairT* r2 = r1 + sp;
+#pragma unroll
+  for (int s = 0; s < 16; ++s) {
+    if (s * TT > c.nu) break;  // the same for every thread of the group
+    const int cc = j + s * TT;  // pair column: (Y[cc - 1], Y[cc])
+    float2 left = make_float2(__shfl_up_sync(0xffffffffu, x[s].x, 1), __shfl_up_sync(0xffffffffu, x[s].y, 1));
+    if (lane == 0) {
+      if (wg > 0) left = edge[(wg - 1) * 16 + s];
+      else left = s > 0 ? edge[(TT / 32 - 1) * 16 + s - 1] : make_float2(0.f, 0.f);
+    }
+    const float2 right = cc < c.nu ? x[s] : make_float2(0.f, 0.f);
+    if (row1 && cc <= c.nu) {
+      r1[cc] = make_pair<PairT>(left.x, right.x);
+      if (two) r2[cc] = make_pair<PairT>(left.y, right.y);
+    }
+  }
+  if (blockIdx.x == 0)  // top border row
+    for (int i = threadIdx.x; i < sp; i += NTH) Lk[i] = make_pair<PairT>(0.f, 0.f);
+  if (vbase + ROWS >= c.nv)  // bottom border row
+    for (int i = threadIdx.x; i < sp; i += NTH) Lk[(size_t)(c.nv + 1) * sp + i] = make_pair<PairT>(0.f, 0.f);
+}
+
 // ------------------------------------------------------------------ radix-2 fallback (P <= 8)
 __device__ __forceinline__ int bitrev(int i, int logP) { return (int)(__brev((unsigned)i) >> (32 - logP)); }
 
@@ -475,6 +740,66 @@ __global__ void k_count_nonfinite(const float* __restrict__ x, size_t n, unsigne
 }
 
 // ------------------------------------------------------------------ launch
+// Layer groups of the column stage: the split of the Nz layers over CTAs that keeps the
+// last wave of `slots` resident CTAs fullest, counting the set-up each group repeats (the
+// column's forward FFT and weights, `setup` layers' worth of work) as extra work.
+int pick_layer_groups(int ctas_per_group, int nz_layers, int slots, double setup) {
+  int best = 1;
+  double best_eff = 0.0;
+  const int max_lg = nz_layers / 2 > 0 ? (nz_layers / 2 < 16 ? nz_layers / 2 : 16) : 1;
+  for (int lg = 1; lg <= max_lg; ++lg) {
+    const double waves = (double)ctas_per_group * lg / slots;
+    const double fill = waves / std::ceil(waves);
+    const double eff = fill * (double)nz_layers / (nz_layers + setup * lg);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = lg;
+    }
+  }
+  return best;
+}
+
+template <int P, int FILT, bool DENS>
+cudaError_t launch_cols16(const StageAConst& c, const Workspace& ws, const float2* twq, int d0, int cnt, int sms,
+                          cudaStream_t stream) {
+  constexpr size_t smem = cols16_smem<P, FILT, DENS>();
+  static unsigned long long attr_set = 0;  // devices on which the shared-memory limit is raised
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64 || !(attr_set >> dev & 1ull)) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_cols16<P, FILT, DENS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) attr_set |= 1ull << dev;
+  }
+  constexpr int CB = cols16_per_cta<P>();
+  const int col_groups = (c.half + CB - 1) / CB;
+  // set-up per group: the forward FFT (about one layer's work), and with the density
+  // weighting about one more for the weights' trilinear lookups
+  const int lg = pick_layer_groups(col_groups * cnt, c.nz_layers, 2 * sms, DENS ? 2.2 : 1.2);
+  k_cols16<P, FILT, DENS><<<dim3(col_groups, cnt, lg), kThreads16, smem, stream>>>(
+      ws.S, ws.T, twq, ws.uA, ws.ramp, ws.dirs, ws.dens, ws.band_sum, ws.eps, ws.n_bins, ws.bin_width, c, d0);
+  return cudaGetLastError();
+}
+
+template <int P, typename PairT>
+cudaError_t launch_rows_inv16(const StageAConst& c, const float2* T, PairT* stack, const float2* twq, int cnt,
+                              cudaStream_t stream) {
+  constexpr size_t smem = rows16_smem<P>();
+  static unsigned long long attr_set = 0;  // devices on which the shared-memory limit is raised
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64 || !(attr_set >> dev & 1ull)) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_rows_inv16<P, PairT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) attr_set |= 1ull << dev;
+  }
+  const dim3 gi((c.nv + 2 * kRowPairs16 - 1) / (2 * kRowPairs16), c.nz_layers, cnt);
+  k_rows_inv16<P, PairT><<<gi, rows16_threads<P>(), smem, stream>>>(T, stack, twq, c);
+  return cudaGetLastError();
+}
+
 template <int P>
 cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* images, int dir_begin, int dir_count,
                        cudaStream_t stream, EventRecorder* rec, const StageAHook* hook) {
@@ -493,6 +818,28 @@ cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* i
       if (e != cudaSuccess) return e;
     }
     if (rec) rec->mark(0, stream);
+    const bool dens = c.dens.enabled != 0;
+    const size_t stack_off = (size_t)s0 * c.nz_layers * c.layer_elems;
+    if constexpr (P >= 1024) {
+      // 16-value FFTs (fft16.cuh); their twiddle table follows the 8-value one
+      const float2* twq = ws.twp + (P - 8);
+      cudaError_t e;
+      if (c.filter == 0) e = dens ? launch_cols16<P, 0, true>(c, ws, twq, d0, cnt, sms, stream)
+                                  : launch_cols16<P, 0, false>(c, ws, twq, d0, cnt, sms, stream);
+      else if (c.filter == 2) e = dens ? launch_cols16<P, 2, true>(c, ws, twq, d0, cnt, sms, stream)
+                                       : launch_cols16<P, 2, false>(c, ws, twq, d0, cnt, sms, stream);
+      else e = dens ? launch_cols16<P, 1, true>(c, ws, twq, d0, cnt, sms, stream)
+                    : launch_cols16<P, 1, false>(c, ws, twq, d0, cnt, sms, stream);
+      if (e != cudaSuccess) return e;
+      if (rec) rec->mark(1, stream);
+      if (c.stack_bf16)
+        e = launch_rows_inv16<P, __nv_bfloat162>(c, ws.T, (__nv_bfloat162*)ws.stack + stack_off, twq, cnt, stream);
+      else
+        e = launch_rows_inv16<P, float2>(c, ws.T, (float2*)ws.stack + stack_off, twq, cnt, stream);
+      if (e != cudaSuccess) return e;
+      if (rec) rec->mark(2, stream);
+      continue;
+    }
     // layer groups so that about 2 waves of CTAs run even for a small sub-block
     const int target = 2 * sms * 4;
     int lgroups = (target + col_groups * cnt - 1) / (col_groups * cnt);
@@ -501,7 +848,6 @@ cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* i
 #define RECON_K_COLS(F, D)                                                                                      \
   k_cols<P, F, D><<<gc, kThreads, 0, stream>>>(ws.S, ws.T, ws.twp, ws.uA, ws.ramp, ws.dirs, ws.dens, ws.band_sum, \
                                                ws.eps, ws.n_bins, ws.bin_width, c, d0)
-    const bool dens = c.dens.enabled != 0;
     if (c.filter == 0) {
       if (dens) RECON_K_COLS(0, true); else RECON_K_COLS(0, false);
     } else if (c.filter == 2) {
@@ -512,7 +858,6 @@ cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* i
 #undef RECON_K_COLS
     if (rec) rec->mark(1, stream);
     const dim3 gi((c.nv + 2 * G - 1) / (2 * G), c.nz_layers, cnt);
-    const size_t stack_off = (size_t)s0 * c.nz_layers * c.layer_elems;
     if (c.stack_bf16)
       k_rows_inv<P, __nv_bfloat162><<<gi, kThreads, 0, stream>>>(ws.T, (__nv_bfloat162*)ws.stack + stack_off, ws.twp,
                                                                  c);

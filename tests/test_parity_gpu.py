@@ -46,6 +46,8 @@ STAGE_A_CASES = [
     (33, 200, 5, "off", "intensity", 0.0, 0.0, 0.1, 1e-10, 1e-9, 60e-9),
     (256, 256, 4, "tikhonov", "intensity", 2.7e-3, 0.07, 0.1, 1.97e-12, 1e-10, 1e-6),
     (1024, 1024, 2, "tikhonov", "intensity", 2.7e-3, 0.07, 0.1, 1.97e-12, 5e-11, 1e-6),
+    (512, 400, 3, "tikhonov", "intensity", 2.7e-3, 0.07, 0.1, 1.97e-12, 1e-10, 1e-6),   # P = 1024, ragged rows
+    (1000, 777, 3, "off", "contrast", 0.0, 0.0, 0.1, 1.97e-12, 5e-11, 1e-6),           # P = 2048, ragged both
     (1, 1, 1, "tikhonov", "intensity", 0.0, 0.1, 0.1, 1e-10, 1e-9, 1e-7),
 ]
 

@@ -16,6 +16,7 @@ from paper_2206_09151_gb300 import _abi, phantoms as ph
 pytestmark = pytest.mark.gpu
 
 TOL_F32 = 1e-5
+TOL_BF16 = 3e-3
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -59,7 +60,10 @@ def test_noalloc_run_matches_recon_run_twice(n, D, nzl):
 def test_noalloc_learned_filter_bf16_density_matches_recon_run_twice():
     """The learned regulariser keeps its power spectra and eps table in the static scratch
     (after the stacks), the bfloat16 stack and the sampling-density grid too: 64^2 images,
-    Nz = 4, 24 directions of a 60-degree cone, against recon_run with its own workspace."""
+    Nz = 4, 24 directions of a 60-degree cone, against recon_run with its own workspace.
+    The learned regulariser's radial power spectrum is summed with float atomics, so two
+    runs differ in the last bits of eps and a few stack values round to the other
+    bfloat16 neighbour: the bfloat16-stack tolerance of the other tests applies."""
     n, D, nzl = 64, 24, 4
     rot = ph.cone_rotations(D, 60.0, seed=11)
     rng = np.random.default_rng(5)
@@ -82,7 +86,7 @@ def test_noalloc_learned_filter_bf16_density_matches_recon_run_twice():
         _abi.recon_run_noalloc(plan, img.data_ptr(), vol.data_ptr(), stream)
         _abi.recon_sync(stream)
         assert torch.isfinite(vol).all()
-        assert rel_l2(vol, ref) <= TOL_F32
+        assert rel_l2(vol, ref) <= TOL_BF16
     _abi.recon_destroy(plan)
 
 
