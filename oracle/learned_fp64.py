@@ -149,7 +149,7 @@ def learned_filter(P, delta, lam, r_eff, sigma, eps_bins, cs=0.0):
 def _partial_learned(args):
     """Sum over directions ``dirs`` of their learned-filter contributions to voxels (i, j, k)."""
     (images, rot, dirs, theta, lam, delta, defocus, nz_layers, grid, sigma, nsr, cs, input_mode, i, j, k,
-     density) = args
+     density, interp) = args
     D, nv, nu = images.shape
     P = R.padded_size(max(nu, nv))
     A, B = R.pixel_coefficients(rot, grid, nu, nv)
@@ -170,12 +170,13 @@ def _partial_learned(args):
         for kk_ in range(nz_layers):
             H, _ = learned_filter(P, delta, lam, r_eff[kk_], sigma, eps[kk_], cs)
             st[kk_] = np.fft.ifft2(G * H * W).real[ov:ov + nv, ou:ou + nu]
-        acc += R.backproject_direction(st, A[n], B[n], T[n], i, j, k)
+        acc += R.backproject_direction(st, A[n], B[n], T[n], i, j, k, interp)
     return acc
 
 
 def recon_learned(images, rot, theta, *, lam, delta, defocus, nz_layers, grid, sigma, nsr, cs=0.0,
-                  input_mode=R.INPUT_INTENSITY, voxels=None, workers: int = 1, density: bool = False):
+                  input_mode=R.INPUT_INTENSITY, voxels=None, workers: int = 1, density: bool = False,
+                  layer_interp: int = R.LAYER_NEAREST):
     """The whole operator with the learned regulariser: the single-axis ramp, or the
     sampling-density weighting of an arbitrary scan (``density``).  ``voxels`` = (i, j, k)
     returns those voxels only; ``workers`` > 1 splits the directions over a spawned
@@ -191,7 +192,7 @@ def recon_learned(images, rot, theta, *, lam, delta, defocus, nz_layers, grid, s
     else:
         i, j, k = (np.asarray(x, np.int64) for x in voxels)
     common = (theta, lam, delta, np.asarray(defocus, np.float64), nz_layers, tuple(grid), sigma, nsr, cs, input_mode,
-              i, j, k, density)
+              i, j, k, density, layer_interp)
     dirs = list(range(D))
     if workers <= 1 or D < 2:
         acc = _partial_learned((images, rot, dirs) + common)

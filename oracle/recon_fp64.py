@@ -20,7 +20,10 @@ What it computes, in the paper's order and notation (Sec. 2):
    discretised as the band-limited Ram-Lak kernel and scaled by pi/D.
 5. Y_{n,k} = crop( Re IDFT[ G_n * H_k * W ] ): the layer stack.
 6. Backprojection: every voxel takes, from each direction, a bilinear sample of the
-   layer that contains its depth, and sums over directions.
+   layer that contains its depth, and sums over directions.  Optionally (``layer_interp
+   = LAYER_LINEAR``) it takes the linear blend of the samples of the two layers whose
+   centres bracket its depth, which keeps the layers' defocus error below half a layer
+   once the layers are thinner than the DOF Delta^2 / (2 lambda) of Sec. 1.
 
 Readings where the paper is silent (each is listed in the design notes):
 * layers are Nz equal slabs over the volume's bounding-box extent along the beam,
@@ -28,7 +31,9 @@ Readings where the paper is silent (each is listed in the design notes):
   (``layer_constants``), so that every implementation takes the same decision;
 * P = smallest power of two >= 2*max(nu, nv), zero padding;
 * pixel and voxel centres at (index - (n-1)/2) * delta; bilinear, zero outside the
-  detector; nearest (containing) layer;
+  detector; nearest (containing) layer, or the blend of the two whose centres bracket
+  the depth (layer k centred at k + 1/2 in layer units; beyond the outer centres the
+  outer layer alone);
 * intensities are floored at 1e-6 before the logarithm.
 
 Every function states the passage it follows.  Pins (tests marked ``not gpu``) tie
@@ -43,6 +48,9 @@ import numpy as np
 
 INTENSITY_FLOOR = 1e-6
 LAYER_FRAC_BITS = 24
+
+LAYER_NEAREST = 0  # a voxel takes the layer that contains its depth
+LAYER_LINEAR = 1   # a voxel takes the linear blend of the two layers whose centres bracket it
 
 FILTER_OFF = 0
 FILTER_TIKHONOV = 1
@@ -121,6 +129,24 @@ def layer_index(T: np.ndarray, nz_layers: int, i, j, k) -> np.ndarray:
     """Layer of voxel (i, j, k) for one direction's constants ``T`` (exact integers)."""
     t = T[0] + T[1] * np.asarray(i, np.int64) + T[2] * np.asarray(j, np.int64) + T[3] * np.asarray(k, np.int64)
     return np.clip(t >> LAYER_FRAC_BITS, 0, nz_layers - 1)
+
+
+def layer_blend(T: np.ndarray, nz_layers: int, i, j, k) -> tuple[np.ndarray, np.ndarray]:
+    """Linear blend between adjacent layers: the two layers whose centres bracket the
+    voxel's depth, k0 and k0 + 1, with weight w on k0 + 1.  In layer units the depth is
+    t (the exact 2^-24 fixed-point sum of ``layer_index``) and layer k is centred at
+    k + 1/2, so t' = t - 1/2, k0 = floor(t'), w = t' - k0; above the first centre (t' < 0)
+    and below the last (k0 >= Nz - 1) a voxel takes that layer alone (w = 0).  Returns
+    (k0, w) with w exact (a 24-bit fraction)."""
+    t = T[0] + T[1] * np.asarray(i, np.int64) + T[2] * np.asarray(j, np.int64) + T[3] * np.asarray(k, np.int64)
+    tp = t - (1 << (LAYER_FRAC_BITS - 1))
+    k0 = tp >> LAYER_FRAC_BITS
+    w = (tp - (k0 << LAYER_FRAC_BITS)).astype(np.float64) / float(1 << LAYER_FRAC_BITS)
+    below = k0 < 0
+    above = k0 >= nz_layers - 1
+    k0 = np.where(below, 0, np.where(above, nz_layers - 1, k0))
+    w = np.where(below | above, 0.0, w)
+    return k0, w
 
 
 # ----------------------------------------------------------------------------- filters
@@ -297,25 +323,35 @@ def bilinear(img: np.ndarray, a: np.ndarray, b: np.ndarray) -> np.ndarray:
 
 
 def backproject_direction(stack: np.ndarray, A: np.ndarray, B: np.ndarray, T: np.ndarray,
-                          i, j, k) -> np.ndarray:
+                          i, j, k, interp: int = LAYER_NEAREST) -> np.ndarray:
     """One direction's contribution to voxels (i, j, k): bilinear sample of the layer
     containing each voxel's depth (the real-space counterpart of gridding onto the
-    direction's Ewald patch, Sec. 2)."""
+    direction's Ewald patch, Sec. 2), or with ``interp = LAYER_LINEAR`` the linear blend
+    of the bilinear samples of the two layers whose centres bracket the depth
+    (``layer_blend``)."""
     nz_layers = stack.shape[0]
     a = A[0] * i + A[1] * j + A[2] * k + A[3]
     b = B[0] * i + B[1] * j + B[2] * k + B[3]
-    lay = layer_index(T, nz_layers, i, j, k)
     out = np.zeros(np.shape(a))
-    for L in np.unique(lay):
-        sel = lay == L
-        out[sel] = bilinear(stack[L], a[sel], b[sel])
+    if interp == LAYER_NEAREST:
+        lay = layer_index(T, nz_layers, i, j, k)
+        for L in np.unique(lay):
+            sel = lay == L
+            out[sel] = bilinear(stack[L], a[sel], b[sel])
+        return out
+    k0, w = layer_blend(T, nz_layers, i, j, k)
+    for L in np.unique(k0):
+        sel = k0 == L
+        lo = bilinear(stack[L], a[sel], b[sel])
+        hi = bilinear(stack[min(L + 1, nz_layers - 1)], a[sel], b[sel])
+        out[sel] = (1.0 - w[sel]) * lo + w[sel] * hi
     return out
 
 
 def _partial_recon(args):
     """Sum over directions ``dirs`` of their contributions to voxels (i, j, k)."""
     (images, rot, dirs, lam, delta, defocus, nz_layers, grid, sigma, eps, cs, filt, input_mode, i, j, k,
-     n_dir, density) = args
+     n_dir, density, interp) = args
     nu, nv = images.shape[2], images.shape[1]
     dens = density_weights(rot, padded_size(max(nu, nv)), delta, dirs) if density else None
     A, B = pixel_coefficients(rot, grid, nu, nv)
@@ -329,20 +365,22 @@ def _partial_recon(args):
                          weight=None if dens is None else dens[o])
         for s0 in range(0, i.size, chunk):
             sl = slice(s0, s0 + chunk)
-            acc[sl] += backproject_direction(st, A[n], B[n], T[n], i[sl], j[sl], k[sl])
+            acc[sl] += backproject_direction(st, A[n], B[n], T[n], i[sl], j[sl], k[sl], interp)
     return acc
 
 
 def recon(images, rot, *, lam: float, delta: float, defocus, nz_layers: int, grid, sigma: float = 0.0,
           eps: float = 0.1, cs: float = 0.0, filt: int = FILTER_TIKHONOV, input_mode: int = INPUT_INTENSITY,
-          voxels=None, dirs=None, workers: int = 1, density: bool = False) -> np.ndarray:
+          voxels=None, dirs=None, workers: int = 1, density: bool = False,
+          layer_interp: int = LAYER_NEAREST) -> np.ndarray:
     """The whole operator, FP64.  ``images`` (D, nv, nu); ``rot`` (D, 3, 3);
     ``defocus`` (D,).  Returns vol[z][y][x] float64, or, when ``voxels = (i, j, k)``
     index arrays are given, the values at those voxels only.  ``dirs`` restricts the
     sum to a subset of the directions (the ramp keeps its pi/D for all D);
     ``workers`` > 1 splits the directions over a spawned process pool (the same
     arithmetic, summed in a different order).  ``density`` selects the sampling-density
-    weighting of an arbitrary scan instead of the single-axis ramp."""
+    weighting of an arbitrary scan instead of the single-axis ramp; ``layer_interp`` picks
+    the nearest layer or the linear blend of the two bracketing layers."""
     images = np.asarray(images)
     rot = np.asarray(rot, dtype=np.float64)
     D = images.shape[0]
@@ -354,7 +392,7 @@ def recon(images, rot, *, lam: float, delta: float, defocus, nz_layers: int, gri
         i, j, k = (np.asarray(x, np.int64) for x in voxels)
     dirs = list(range(D)) if dirs is None else list(dirs)
     common = (lam, delta, np.asarray(defocus, np.float64), nz_layers, tuple(grid), sigma, eps, cs, filt,
-              input_mode, i, j, k, D, density)
+              input_mode, i, j, k, D, density, layer_interp)
     if workers <= 1 or len(dirs) < 2:
         acc = _partial_recon((images, rot, dirs) + common)
     else:
