@@ -77,6 +77,13 @@ extern "C" {
 #define RECON_RAMP_DENSITY 1     /* any geometry: W = g / (S(q) + eps_S), S the gridded
                                     sampling density of all views' slices (Sec. 2)        */
 
+#define RECON_LAYER_NEAREST 0    /* a voxel takes the layer that contains its depth      */
+#define RECON_LAYER_LINEAR 1     /* the linear blend of the two layers whose centres
+                                    bracket its depth (layer k centred at k + 1/2 in layer
+                                    units; the outer layer alone beyond the outer centres);
+                                    four row gathers per sample instead of two, in the
+                                    general backprojection kernel for every geometry      */
+
 #define RECON_BP_AUTO 0          /* the single-axis variant measured faster (DIRECT)     */
 #define RECON_BP_DIRECT 1        /* single-axis: bilinear gathers straight from the stack */
 #define RECON_BP_STAGED 2        /* single-axis: footprint staged in shared memory        */
@@ -122,17 +129,20 @@ typedef struct {
                        for the scan (the call then synchronises its stream) and returns
                        RECON_E_NONFINITE without touching the volume if it finds any; 0: no
                        scan (a NaN then propagates into the voxels it reaches)             */
+  int layer_interp; /* RECON_LAYER_*: nearest layer, or the blend of the two bracketing ones */
 } recon_options;
 
 /* Fills *opts with defaults: sigma 0, eps 0.1 (the value of Sec. 3), cs 0, Tikhonov
  * filter, intensity input, float32 stack, single-axis ramp, overwrite, automatic
- * block, no finiteness scan.  No error (opts NULL is ignored). */
+ * block, no finiteness scan, nearest layer.  No error (opts NULL is ignored). */
 void recon_default_options(recon_options* opts);
 
 /* Builds a plan (host memory only; no CUDA call, no device allocation).
  *   geom      geometry, rot copied                    lambda  wavelength (m), > 0
  *   delta     voxel and pixel pitch (m), > 0           defocus host [n_dir] R_n (m), copied
- *   nz_layers Nz depth layers                          grid    output volume size
+ *   nz_layers Nz depth layers, or 0 for the smallest Nz whose layers are no thicker
+ *             than the depth of field (recon_layers_for_dof; recon_plan_layers reports it)
+ *   grid      output volume size
  *   opts      NULL = recon_default_options
  * The per-direction FP64 tables are computed here: layer depths z_k and defocus
  * R_n - z_k (Eq. 5), the CTF phase constants (Eq. 7, Eq. 11), the ramp (Sec. 2).
@@ -208,6 +218,8 @@ int recon_run_batch(int n, const recon_plan_t* plans, const float* const* images
  *                       is <= DOF for every direction of `geom` over `grid` (1 when the
  *                       scan has no direction). */
 int recon_plan_dof(recon_plan_t plan, double* pitch_max, double* dof);
+/* The plan's number of depth layers (the automatic choice when recon_plan had 0). */
+int recon_plan_layers(recon_plan_t plan, int* nz_layers);
 const char* recon_plan_warning(recon_plan_t plan);
 int recon_layers_for_dof(const recon_geometry* geom, const recon_grid* grid, double lambda, double delta, int* nz);
 

@@ -33,6 +33,7 @@ RECON_STACK_BF16 = 1
 RECON_RAMP_SINGLE_AXIS = 0
 RECON_RAMP_DENSITY = 1
 RECON_BP_AUTO, RECON_BP_DIRECT, RECON_BP_STAGED = 0, 1, 2
+RECON_LAYER_NEAREST, RECON_LAYER_LINEAR = 0, 1
 RECON_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 RECON_MAX_LAYERS = 96
 
@@ -51,7 +52,8 @@ class ReconOptions(ctypes.Structure):
                 ("filter", ctypes.c_int), ("input_mode", ctypes.c_int), ("stack_dtype", ctypes.c_int),
                 ("ramp_mode", ctypes.c_int), ("accumulate", ctypes.c_int), ("dir_block", ctypes.c_int),
                 ("mlp_weights", ctypes.POINTER(ctypes.c_float)), ("nsr", ctypes.c_double),
-                ("stage_block", ctypes.c_int), ("bp_kernel", ctypes.c_int), ("check_finite", ctypes.c_int)]
+                ("stage_block", ctypes.c_int), ("bp_kernel", ctypes.c_int), ("check_finite", ctypes.c_int),
+                ("layer_interp", ctypes.c_int)]
 
 
 class ReconTrainCfg(ctypes.Structure):
@@ -94,6 +96,7 @@ def load_library(path: str = LIB_PATH):
     L.recon_plan_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]
     L.recon_run_noalloc.argtypes = [vp, vp, vp, vp]
     L.recon_plan_dof.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.recon_plan_layers.argtypes = [vp, ctypes.POINTER(ip)]
     L.recon_plan_warning.argtypes = [vp]
     L.recon_plan_warning.restype = ctypes.c_char_p
     L.recon_layers_for_dof.argtypes = [ctypes.POINTER(ReconGeometry), ctypes.POINTER(ReconGrid), ctypes.c_double,
@@ -121,7 +124,8 @@ def load_library(path: str = LIB_PATH):
                  "recon_plan_info", "recon_sync", "recon_destroy", "recon_profile_enable", "recon_profile_read",
                  "recon_run_noalloc", "recon_mlp_train_workspace_size", "recon_mlp_train", "recon_batch_create",
                  "recon_batch_workspace_size", "recon_batch_run", "recon_batch_run_graph", "recon_batch_destroy",
-                 "recon_run_batch_workspace_size", "recon_run_batch", "recon_plan_dof", "recon_layers_for_dof"):
+                 "recon_run_batch_workspace_size", "recon_run_batch", "recon_plan_dof", "recon_layers_for_dof",
+                 "recon_plan_layers"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -213,6 +217,12 @@ def recon_plan_dof(plan) -> tuple[float, float]:
     h, d = ctypes.c_double(), ctypes.c_double()
     _check(load_library().recon_plan_dof(plan, ctypes.byref(h), ctypes.byref(d)), "recon_plan_dof")
     return h.value, d.value
+
+
+def recon_plan_layers(plan) -> int:
+    n = ctypes.c_int()
+    _check(load_library().recon_plan_layers(plan, ctypes.byref(n)), "recon_plan_layers")
+    return n.value
 
 
 def recon_plan_warning(plan) -> str:

@@ -50,8 +50,11 @@ constexpr int kMagicBits = 0x4B400000;
 
 // One direction's samples for a thread's run of kTZ voxels along z.  CLAMP: the taps are
 // clamped to the zero border and the weights saturated (any tile); without it the tile
-// is known to lie inside the detector and the layer range.
-template <typename ST, bool CLAMP>
+// is known to lie inside the detector and the layer range.  LIN: blend the two layers
+// whose centres bracket the depth (layer k centred at k + 1/2 in layer units: t' = t - 1/2,
+// k0 = floor t', weight t' - k0 on k0 + 1, the outer layer alone beyond the outer
+// centres) instead of taking the layer that contains it.
+template <typename ST, bool CLAMP, bool LIN>
 __device__ __forceinline__ void generic_run(const TileDir& td, const ST* __restrict__ base, const BackprojConst& c,
                                             float ftx, float fty, int tx, int ty, float (&acc)[kTZ]) {
   float ap = fmaf(td.af0, ftx, fmaf(td.af1, fty, td.fa));
@@ -60,9 +63,9 @@ __device__ __forceinline__ void generic_run(const TileDir& td, const ST* __restr
   const float loa = (float)(-1 - td.ia), hia = (float)(c.nu - 1 - td.ia);
   const float lob = (float)(-1 - td.ib), hib = (float)(c.nv - 1 - td.ib);
   const int last_layer = c.nz_layers - 1;
+  const int LE = (int)c.layer_elems;
 #pragma unroll
   for (int z = 0; z < kTZ; ++z) {
-    const int layer = CLAMP ? min(max((int32_t)t >> 24, 0), last_layer) : (int32_t)t >> 24;
     const float ta = (CLAMP ? fminf(fmaxf(ap, loa), hia) : ap) + kMagic;
     const float tb = (CLAMP ? fminf(fmaxf(bp, lob), hib) : bp) + kMagic;
     const int ra = __float_as_int(ta) - kMagicBits;
@@ -70,11 +73,29 @@ __device__ __forceinline__ void generic_run(const TileDir& td, const ST* __restr
     const float fa = CLAMP ? __saturatef(ap - (ta - kMagic) + 0.5f) : ap - (ta - kMagic) + 0.5f;
     const float fb = CLAMP ? __saturatef(bp - (tb - kMagic) + 0.5f) : bp - (tb - kMagic) + 0.5f;
     // one direction's stack holds at most 96 x 1026 x 1025 entries: 32-bit offsets
-    const ST* p = base + (layer * (int)c.layer_elems + rb * c.su + ra);
-    const float2 r0 = stack_pair(p), r1 = stack_pair(p + c.su);
-    const float top = fmaf(fa, r0.y - r0.x, r0.x);
-    const float bot = fmaf(fa, r1.y - r1.x, r1.x);
-    acc[z] += fmaf(fb, bot - top, top);
+    if constexpr (LIN) {
+      const int32_t tp = (int32_t)t - (1 << 23);
+      const int k0r = tp >> 24;
+      const bool outer = tp < 0 || k0r >= last_layer;
+      const int k0 = tp < 0 ? 0 : min(k0r, last_layer);
+      const float w = outer ? 0.f : (float)(tp & 0xFFFFFF) * 0x1p-24f;  // exact 24-bit fraction
+      const int k1 = min(k0 + 1, last_layer);
+      const ST* p0 = base + (k0 * LE + rb * c.su + ra);
+      const ST* p1 = p0 + (k1 - k0) * LE;
+      const float2 r0 = stack_pair(p0), r1 = stack_pair(p0 + c.su);
+      const float2 s0 = stack_pair(p1), s1 = stack_pair(p1 + c.su);
+      const float top0 = fmaf(fa, r0.y - r0.x, r0.x), bot0 = fmaf(fa, r1.y - r1.x, r1.x);
+      const float top1 = fmaf(fa, s0.y - s0.x, s0.x), bot1 = fmaf(fa, s1.y - s1.x, s1.x);
+      const float v0 = fmaf(fb, bot0 - top0, top0), v1 = fmaf(fb, bot1 - top1, top1);
+      acc[z] += fmaf(w, v1 - v0, v0);
+    } else {
+      const int layer = CLAMP ? min(max((int32_t)t >> 24, 0), last_layer) : (int32_t)t >> 24;
+      const ST* p = base + (layer * LE + rb * c.su + ra);
+      const float2 r0 = stack_pair(p), r1 = stack_pair(p + c.su);
+      const float top = fmaf(fa, r0.y - r0.x, r0.x);
+      const float bot = fmaf(fa, r1.y - r1.x, r1.x);
+      acc[z] += fmaf(fb, bot - top, top);
+    }
     ap += td.af2;
     bp += td.bf2;
     t += td.tk;
@@ -82,7 +103,7 @@ __device__ __forceinline__ void generic_run(const TileDir& td, const ST* __restr
 }
 
 // One 32 x 8 x 8 tile (tile coordinates bx, by, bz); s_dir: dir_count TileDir records.
-template <typename ST>
+template <typename ST, bool LIN>
 __device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const DirParams* __restrict__ dirs,
                                                 const ST* __restrict__ stack, const BackprojConst& c,
                                                 int dir_begin, int dir_count, float* __restrict__ vol,
@@ -140,8 +161,8 @@ __device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const Di
   for (int d = 0; d < dir_count; ++d) {
     const TileDir& td = s_dir[d];
     const ST* base = stack + (size_t)d * c.nz_layers * c.layer_elems + (ptrdiff_t)(td.ib + 1) * c.su + (td.ia + 1);
-    if (td.pad[0]) generic_run<ST, false>(td, base, c, ftx, fty, tx, ty, acc);
-    else generic_run<ST, true>(td, base, c, ftx, fty, tx, ty, acc);
+    if (td.pad[0]) generic_run<ST, false, LIN>(td, base, c, ftx, fty, tx, ty, acc);
+    else generic_run<ST, true, LIN>(td, base, c, ftx, fty, tx, ty, acc);
   }
 
   const int i = i0 + tx, j = j0 + ty;
@@ -156,13 +177,13 @@ __device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const Di
   }
 }
 
-template <typename ST>
+template <typename ST, bool LIN>
 __global__ void __launch_bounds__(kTX* kTY, 4) k_backproject(const DirParams* __restrict__ dirs,
                                                            const ST* __restrict__ stack, BackprojConst c,
                                                            int dir_begin, int dir_count, float* __restrict__ vol,
                                                            int accumulate) {
   extern __shared__ TileDir s_dir[];
-  bp_generic_tile<ST>(blockIdx.x, blockIdx.y, blockIdx.z, dirs, stack, c, dir_begin, dir_count, vol, accumulate,
+  bp_generic_tile<ST, LIN>(blockIdx.x, blockIdx.y, blockIdx.z, dirs, stack, c, dir_begin, dir_count, vol, accumulate,
                       s_dir);
 }
 
@@ -559,12 +580,20 @@ __global__ void __launch_bounds__(256) k_backproject_persistent(const BatchBp* _
     const int bx = (int)(t % d.gx), by = (int)((t / d.gx) % d.gy), bz = (int)(t / ((unsigned long long)d.gx * d.gy));
     switch (d.kind) {
       case 0:
-        bp_generic_tile<float2>(bx, by, bz, d.dirs, (const float2*)d.stack, d.c, d.dir_begin, d.dir_count, d.vol,
-                                d.accumulate, (TileDir*)smem_raw);
+        bp_generic_tile<float2, false>(bx, by, bz, d.dirs, (const float2*)d.stack, d.c, d.dir_begin, d.dir_count,
+                                       d.vol, d.accumulate, (TileDir*)smem_raw);
         break;
       case 1:
-        bp_generic_tile<__nv_bfloat162>(bx, by, bz, d.dirs, (const __nv_bfloat162*)d.stack, d.c, d.dir_begin,
-                                        d.dir_count, d.vol, d.accumulate, (TileDir*)smem_raw);
+        bp_generic_tile<__nv_bfloat162, false>(bx, by, bz, d.dirs, (const __nv_bfloat162*)d.stack, d.c,
+                                               d.dir_begin, d.dir_count, d.vol, d.accumulate, (TileDir*)smem_raw);
+        break;
+      case 6:
+        bp_generic_tile<float2, true>(bx, by, bz, d.dirs, (const float2*)d.stack, d.c, d.dir_begin, d.dir_count,
+                                      d.vol, d.accumulate, (TileDir*)smem_raw);
+        break;
+      case 7:
+        bp_generic_tile<__nv_bfloat162, true>(bx, by, bz, d.dirs, (const __nv_bfloat162*)d.stack, d.c,
+                                              d.dir_begin, d.dir_count, d.vol, d.accumulate, (TileDir*)smem_raw);
         break;
       case 2:
         bp_axis_tile<float2, false>(bx, by, bz, d.dirs, (const float2*)d.stack, d.c, d.dir_begin, d.dir_count, d.vol,
@@ -578,7 +607,7 @@ __global__ void __launch_bounds__(256) k_backproject_persistent(const BatchBp* _
         bp_axis_tile<__nv_bfloat162, false>(bx, by, bz, d.dirs, (const __nv_bfloat162*)d.stack, d.c, d.dir_begin,
                                             d.dir_count, d.vol, d.accumulate, (AxisDir*)smem_raw);
         break;
-      default:
+      case 5:
         bp_axis_tile<__nv_bfloat162, true>(bx, by, bz, d.dirs, (const __nv_bfloat162*)d.stack, d.c, d.dir_begin,
                                            d.dir_count, d.vol, d.accumulate, (AxisDir*)smem_raw);
         break;
@@ -588,10 +617,26 @@ __global__ void __launch_bounds__(256) k_backproject_persistent(const BatchBp* _
 
 }  // namespace
 
+template <typename ST, bool LIN>
+cudaError_t launch_generic(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
+                           int dir_count, float* volume, int accumulate, cudaStream_t stream) {
+  dim3 grid((c.nx + kTX - 1) / kTX, (c.ny + kTY - 1) / kTY, (c.nz + kTZ - 1) / kTZ);
+  const size_t smem = (size_t)dir_count * sizeof(TileDir);
+  if (smem > 48 * 1024) {
+    cudaError_t e =
+        cudaFuncSetAttribute(k_backproject<ST, LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_backproject<ST, LIN><<<grid, kTX * kTY, smem, stream>>>(dirs, (const ST*)stack, c, dir_begin, dir_count, volume,
+                                                            accumulate);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
                                int dir_count, float* volume, int accumulate, cudaStream_t stream) {
   if (dir_count <= 0 || c.nx <= 0 || c.ny <= 0 || c.nz <= 0) return cudaSuccess;
-  if (c.axis_y && !c.staged) {
+  // the layer blend runs in the general kernel for every geometry
+  if (c.axis_y && !c.staged && !c.layer_linear) {
     const bool two = c.b_frac != 0.f;
     if (c.stack_bf16)
       return two ? launch_axis<__nv_bfloat162, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream)
@@ -599,7 +644,7 @@ cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, co
     return two ? launch_axis<float2, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream)
                : launch_axis<float2, false>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream);
   }
-  if (c.axis_y) {
+  if (c.axis_y && !c.layer_linear) {
     const bool two = c.b_frac != 0.f;
     if (c.stack_bf16)
       return two ? launch_axis_staged<__nv_bfloat162, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate,
@@ -609,26 +654,14 @@ cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, co
     return two ? launch_axis_staged<float2, true>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream)
                : launch_axis_staged<float2, false>(c, dirs, stack, dir_begin, dir_count, volume, accumulate, stream);
   }
-  dim3 grid((c.nx + kTX - 1) / kTX, (c.ny + kTY - 1) / kTY, (c.nz + kTZ - 1) / kTZ);
-  const size_t smem = (size_t)dir_count * sizeof(TileDir);
-  if (c.stack_bf16) {
-    if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k_backproject<__nv_bfloat162>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    k_backproject<__nv_bfloat162><<<grid, kTX * kTY, smem, stream>>>(
-        dirs, (const __nv_bfloat162*)stack, c, dir_begin, dir_count, volume, accumulate);
-  } else {
-    if (smem > 48 * 1024) {
-      cudaError_t e =
-          cudaFuncSetAttribute(k_backproject<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-    }
-    k_backproject<float2><<<grid, kTX * kTY, smem, stream>>>(dirs, (const float2*)stack, c, dir_begin, dir_count,
-                                                              volume, accumulate);
-  }
-  return cudaGetLastError();
+  return c.stack_bf16 ? (c.layer_linear ? launch_generic<__nv_bfloat162, true>(c, dirs, stack, dir_begin, dir_count,
+                                                                               volume, accumulate, stream)
+                                         : launch_generic<__nv_bfloat162, false>(c, dirs, stack, dir_begin, dir_count,
+                                                                                 volume, accumulate, stream))
+                      : (c.layer_linear ? launch_generic<float2, true>(c, dirs, stack, dir_begin, dir_count, volume,
+                                                                       accumulate, stream)
+                                        : launch_generic<float2, false>(c, dirs, stack, dir_begin, dir_count, volume,
+                                                                        accumulate, stream));
 }
 
 void describe_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
@@ -640,18 +673,19 @@ void describe_backproject(const BackprojConst& c, const DirParams* dirs, const v
   out->dir_begin = dir_begin;
   out->dir_count = dir_count;
   out->accumulate = accumulate;
-  if (c.axis_y) {
+  const bool axis = c.axis_y && !c.layer_linear;
+  if (axis) {
     out->kind = 2 + (c.stack_bf16 ? 2 : 0) + (c.b_frac != 0.f ? 1 : 0);
     out->gx = (c.nx + kAX - 1) / kAX;
     out->gy = (c.nz + kAZ - 1) / kAZ;
     out->gz = (c.ny + kJ - 1) / kJ;
   } else {
-    out->kind = c.stack_bf16 ? 1 : 0;
+    out->kind = (c.stack_bf16 ? 1 : 0) + (c.layer_linear ? 6 : 0);
     out->gx = (c.nx + kTX - 1) / kTX;
     out->gy = (c.ny + kTY - 1) / kTY;
     out->gz = (c.nz + kTZ - 1) / kTZ;
   }
-  out->smem = (size_t)dir_count * (c.axis_y ? sizeof(AxisDir) : sizeof(TileDir));
+  out->smem = (size_t)dir_count * (axis ? sizeof(AxisDir) : sizeof(TileDir));
 }
 
 cudaError_t launch_backproject_persistent(const BatchBp* desc_dev, int n_desc, unsigned long long total,

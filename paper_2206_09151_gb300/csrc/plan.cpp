@@ -94,6 +94,7 @@ void recon_default_options(recon_options* o) {
   o->stage_block = 0;
   o->bp_kernel = RECON_BP_AUTO;
   o->check_finite = 0;
+  o->layer_interp = RECON_LAYER_NEAREST;
 }
 
 const char* recon_error_string(int code) {
@@ -129,7 +130,13 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   if (grid->nx < 0 || grid->ny < 0 || grid->nz < 0) return fail(RECON_E_INVALID_ARG, "recon_plan: grid < 0");
   if (grid->nx > RECON_MAX_GRID || grid->ny > RECON_MAX_GRID || grid->nz > RECON_MAX_GRID)
     return fail(RECON_E_UNSUPPORTED_SIZE, "recon_plan: grid side > RECON_MAX_GRID");
-  if (nz_layers < 1) return fail(RECON_E_INVALID_ARG, "recon_plan: nz_layers < 1");
+  if (nz_layers < 0) return fail(RECON_E_INVALID_ARG, "recon_plan: nz_layers < 0");
+  if (nz_layers == 0) {  // automatic: layers no thicker than the depth of field
+    if (!(lambda > 0.0) || !(delta > 0.0) || !std::isfinite(lambda) || !std::isfinite(delta))
+      return fail(RECON_E_INVALID_ARG, "recon_plan: lambda and delta must be > 0");
+    const int rc = recon_layers_for_dof(geom, grid, lambda, delta, &nz_layers);
+    if (rc) return rc;
+  }
   if (nz_layers > RECON_MAX_LAYERS) return fail(RECON_E_UNSUPPORTED_SIZE, "recon_plan: nz_layers > RECON_MAX_LAYERS");
   if (!(lambda > 0.0) || !std::isfinite(lambda)) return fail(RECON_E_INVALID_ARG, "recon_plan: lambda must be > 0");
   if (!(delta > 0.0) || !std::isfinite(delta)) return fail(RECON_E_INVALID_ARG, "recon_plan: delta must be > 0");
@@ -143,6 +150,8 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   if (o.filter == RECON_FILTER_MLP && !training && (!(o.nsr > 0.0) || !std::isfinite(o.nsr)))
     return fail(RECON_E_INVALID_ARG, "recon_plan: the learned filter needs nsr > 0");
   if (o.check_finite != 0 && o.check_finite != 1) return fail(RECON_E_INVALID_ARG, "recon_plan: check_finite must be 0 or 1");
+  if (o.layer_interp != RECON_LAYER_NEAREST && o.layer_interp != RECON_LAYER_LINEAR)
+    return fail(RECON_E_INVALID_ARG, "recon_plan: unknown layer_interp");
   if (o.input_mode != RECON_INPUT_INTENSITY && o.input_mode != RECON_INPUT_CONTRAST)
     return fail(RECON_E_INVALID_ARG, "recon_plan: unknown input_mode");
   if (o.stack_dtype != RECON_STACK_F32 && o.stack_dtype != RECON_STACK_BF16)
@@ -441,6 +450,7 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
     cb.b_frac = (float)(boff - fl);
   }
   cb.staged = o.bp_kernel == RECON_BP_STAGED;
+  cb.layer_linear = o.layer_interp == RECON_LAYER_LINEAR;
 
   const size_t elem = ca.stack_bf16 ? 4 : 8;  // one tap pair
   p->stack_dir_bytes = (size_t)nz_layers * ca.layer_elems * elem;
@@ -569,6 +579,12 @@ int recon_plan_dof(recon_plan_t p, double* pitch_max, double* dof) {
 }
 
 const char* recon_plan_warning(recon_plan_t p) { return p ? p->warning.c_str() : ""; }
+
+int recon_plan_layers(recon_plan_t p, int* nz_layers) {
+  if (!p || !nz_layers) return fail(RECON_E_INVALID_ARG, "recon_plan_layers: null argument");
+  *nz_layers = p->nzl;
+  return RECON_OK;
+}
 
 int recon_layers_for_dof(const recon_geometry* geom, const recon_grid* grid, double lambda, double delta, int* nz) {
   if (!geom || !grid || !nz) return fail(RECON_E_INVALID_ARG, "recon_layers_for_dof: null argument");

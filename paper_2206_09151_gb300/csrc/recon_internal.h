@@ -134,13 +134,15 @@ struct BackprojConst {
   int b_int;      // floor(b_off)
   float b_frac;   // b_off - floor(b_off), 0 or 1/2
   int staged;     // single-axis kernel with shared-memory staging of each footprint
+  int layer_linear;  // blend the two layers whose centres bracket the depth (general kernel)
 };
 
 cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
                                int dir_count, float* volume, int accumulate, cudaStream_t stream);
 
 // One tomogram's share of a persistent batched backprojection: its constants, pointers,
-// kernel kind (general / single-axis, float32 / bfloat16 stack, one or two detector rows),
+// kernel kind (general 0/1, single-axis 2..5 (float32 / bfloat16 stack, one or two detector
+// rows), general with the layer blend 6/7),
 // tile grid and the index of its first work item.
 struct BatchBp {
   BackprojConst c;

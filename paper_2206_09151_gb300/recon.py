@@ -14,6 +14,7 @@ _INPUTS = {"intensity": _abi.RECON_INPUT_INTENSITY, "contrast": _abi.RECON_INPUT
 _STACKS = {"f32": _abi.RECON_STACK_F32, "bf16": _abi.RECON_STACK_BF16}
 _RAMPS = {"single_axis": _abi.RECON_RAMP_SINGLE_AXIS, "density": _abi.RECON_RAMP_DENSITY}
 _BP_KERNELS = {"auto": _abi.RECON_BP_AUTO, "direct": _abi.RECON_BP_DIRECT, "staged": _abi.RECON_BP_STAGED}
+_LAYER_INTERP = {"nearest": _abi.RECON_LAYER_NEAREST, "linear": _abi.RECON_LAYER_LINEAR}
 
 
 class Reconstructor:
@@ -21,14 +22,15 @@ class Reconstructor:
 
     ``rot`` (D, 3, 3) volume->beam rotations, ``nu``/``nv`` image size, ``grid`` =
     (nx, ny, nz), ``lam`` wavelength, ``delta`` pitch, ``defocus`` (D,) R_n,
-    ``nz_layers`` depth layers; options as in ``recon_options``."""
+    ``nz_layers`` depth layers (0: as many as the depth of field asks for); options as in
+    ``recon_options``."""
 
     def __init__(self, rot, nu: int, nv: int, grid, *, lam: float, delta: float, defocus, nz_layers: int,
                  sigma: float = 0.0, eps: float = 0.1, cs: float = 0.0, filter: str = "tikhonov",
                  input_mode: str = "intensity", stack_dtype: str = "f32", accumulate: bool = False,
                  dir_block: int = 0, ramp: str = "single_axis", mlp_weights=None, nsr: float = 0.0,
-                 stage_block: int = 0, bp_kernel: str = "auto", check_finite: bool = False, device=None,
-                 allocate: bool = True):
+                 stage_block: int = 0, bp_kernel: str = "auto", check_finite: bool = False,
+                 layer_interp: str = "nearest", device=None, allocate: bool = True):
         o = _abi.recon_default_options()
         o.sigma, o.eps, o.cs = float(sigma), float(eps), float(cs)
         o.filter, o.input_mode, o.stack_dtype = _FILTERS[filter], _INPUTS[input_mode], _STACKS[stack_dtype]
@@ -38,15 +40,17 @@ class Reconstructor:
         o.stage_block = int(stage_block)
         o.bp_kernel = _BP_KERNELS[bp_kernel]
         o.check_finite = int(bool(check_finite))
+        o.layer_interp = _LAYER_INTERP[layer_interp]
         self._weights = None
         if mlp_weights is not None:
             self._weights = np.ascontiguousarray(mlp_weights, dtype=np.float32)
             o.mlp_weights = self._weights.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
         self.rot = np.ascontiguousarray(rot, np.float64).reshape(-1, 3, 3)
         self.D = self.rot.shape[0]
-        self.nu, self.nv, self.grid, self.nz_layers = nu, nv, tuple(grid), nz_layers
+        self.nu, self.nv, self.grid = nu, nv, tuple(grid)
         self.stack_dtype = torch.bfloat16 if stack_dtype == "bf16" else torch.float32
         self.plan = _abi.recon_plan(self.rot, nu, nv, lam, delta, defocus, nz_layers, self.grid, o)
+        self.nz_layers = _abi.recon_plan_layers(self.plan)
         self.ws_bytes = _abi.recon_workspace_size(self.plan)
         self.padded, self.dir_block, self.n_blocks, self.stage_block = _abi.recon_plan_info(self.plan)
         self.device = torch.device(device) if device is not None else (

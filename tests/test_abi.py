@@ -86,13 +86,13 @@ def test_block_sizing_follows_the_per_direction_intermediates(lib):
 def test_default_options(lib):
     o = _abi.recon_default_options()
     assert (o.sigma, o.eps, o.cs, o.filter, o.input_mode, o.stack_dtype, o.accumulate, o.dir_block,
-            o.check_finite) == (0.0, 0.1, 0.0, 1, 0, 0, 0, 0, 0)
+            o.check_finite, o.layer_interp) == (0.0, 0.1, 0.0, 1, 0, 0, 0, 0, 0, 0)
 
 
 @pytest.mark.parametrize("kw,code", [
     (dict(nu=0), _abi.RECON_E_INVALID_ARG),
     (dict(nu=1025), _abi.RECON_E_UNSUPPORTED_SIZE),
-    (dict(nz_layers=0), _abi.RECON_E_INVALID_ARG),
+    (dict(nz_layers=-1), _abi.RECON_E_INVALID_ARG),
     (dict(nz_layers=97), _abi.RECON_E_UNSUPPORTED_SIZE),
     (dict(lam=0.0), _abi.RECON_E_INVALID_ARG),
     (dict(delta=-1.0), _abi.RECON_E_INVALID_ARG),
@@ -209,3 +209,19 @@ def test_learned_filter_needs_weights_and_nsr(lib):
     o.filter = _abi.RECON_FILTER_MLP
     with pytest.raises(_abi.ReconError):
         _plan(opts=o)
+
+
+def test_layer_interp_is_validated_and_nz_zero_follows_the_depth_of_field(lib):
+    o = _abi.recon_default_options()
+    o.layer_interp = 2
+    with pytest.raises(_abi.ReconError) as e:
+        _plan(opts=o)
+    assert e.value.code == _abi.RECON_E_INVALID_ARG
+    o.layer_interp = _abi.RECON_LAYER_LINEAR
+    _abi.recon_destroy(_plan(opts=o))
+    # Nz = 0: the smallest layer count whose layers are no thicker than the DOF
+    rot = ph.single_axis_rotations(4)
+    p = _plan(rot=rot, nu=64, nv=64, defocus=np.full(4, 1e-7), nz_layers=0, grid=(64, 64, 64))
+    assert _abi.recon_plan_layers(p) == _abi.recon_layers_for_dof(rot, (64, 64, 64), 1e-10, 1e-9) == 19
+    assert _abi.recon_plan_warning(p) == ""
+    _abi.recon_destroy(p)

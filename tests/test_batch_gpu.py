@@ -27,7 +27,7 @@ def rel_l2(a, b):
 def _tomograms():
     """Seeded uneven tomograms: grids 24..64, images 24..72, 7..70 directions, 1..8
     layers; single-axis and cone geometries (density weighting), float32 and bfloat16
-    stacks, a learned-filter one and an accumulating one."""
+    stacks, a learned-filter one, an accumulating one and two with the layer blend."""
     rng = np.random.default_rng(41)
     specs = [
         dict(n=64, nu=64, D=70, nz=8, ramp="single_axis", stack="f32"),
@@ -37,6 +37,8 @@ def _tomograms():
         dict(n=32, nu=72, D=35, nz=5, ramp="single_axis", stack="f32", filter="mlp"),
         dict(n=36, nu=40, D=12, nz=2, ramp="single_axis", stack="f32", accumulate=True),
         dict(n=30, nu=30, D=0, nz=2, ramp="single_axis", stack="f32"),
+        dict(n=40, nu=40, D=25, nz=6, ramp="single_axis", stack="f32", interp="linear"),
+        dict(n=32, nu=36, D=20, nz=4, ramp="density", stack="bf16", interp="linear"),
     ]
     out = []
     for q, sp in enumerate(specs):
@@ -50,7 +52,7 @@ def _tomograms():
         img = torch.from_numpy((1.0 + 1e-2 * rng.standard_normal((D, nu, nu))).astype(np.float32)).cuda()
         kw = dict(lam=1e-10, delta=1e-9, defocus=R, nz_layers=sp["nz"], sigma=0.05, eps=0.02, ramp=sp["ramp"],
                   stack_dtype=sp["stack"], filter=sp.get("filter", "tikhonov"),
-                  accumulate=sp.get("accumulate", False))
+                  accumulate=sp.get("accumulate", False), layer_interp=sp.get("interp", "nearest"))
         if kw["filter"] == "mlp":
             kw.update(mlp_weights=ph.mlp_init(q).astype(np.float32), nsr=1e-2)
         out.append((rot, nu, grid, kw, img))
@@ -92,9 +94,13 @@ def test_batch_matches_single_runs(dir_block):
 
 def _same(q, toms, a, c):
     """Bitwise for the deterministic tomograms; the density splat and the learned path's
-    power spectrum sum with float atomics, whose order varies from run to run."""
+    power spectrum sum with float atomics, whose order varies from run to run (with a
+    bfloat16 stack a few values then round to the other neighbour: the bfloat16
+    tolerance applies)."""
     kw = toms[q][3]
     if kw["ramp"] == "density" or kw["filter"] == "mlp":
+        if kw["stack_dtype"] == "bf16":
+            return rel_l2(a.cpu().numpy(), c.cpu().numpy()) <= 3e-3
         return torch.allclose(a, c, rtol=1e-6, atol=1e-6 * float(c.abs().max()))
     return torch.equal(a, c)
 
@@ -138,6 +144,11 @@ def test_batch_member_matches_oracle():
     ref = O.recon(img.cpu().numpy(), rot, lam=kw["lam"], delta=kw["delta"], defocus=kw["defocus"],
                   nz_layers=kw["nz_layers"], grid=grid, sigma=kw["sigma"], eps=kw["eps"])
     assert rel_l2(vols[0].cpu().numpy(), ref) <= 1e-5
+    q = next(q for q, t in enumerate(toms) if t[3]["layer_interp"] == "linear" and t[3]["stack_dtype"] == "f32")
+    rot, nu, grid, kw, img = toms[q]
+    ref = O.recon(img.cpu().numpy(), rot, lam=kw["lam"], delta=kw["delta"], defocus=kw["defocus"],
+                  nz_layers=kw["nz_layers"], grid=grid, sigma=kw["sigma"], eps=kw["eps"], layer_interp=O.LAYER_LINEAR)
+    assert rel_l2(vols[q].cpu().numpy(), ref) <= 1e-5
     b.close()
     for r in recons:
         r.close()

@@ -84,11 +84,13 @@ def test_stage_a_layer_stack_matches_oracle(case):
 
 
 # ---------------------------------------------------------------- stage B
-def _stage_b_case(grid, nu, nv, nzl, D, seed, start=0.1, span=math.pi, axis=None, bp_kernel="auto"):
+def _stage_b_case(grid, nu, nv, nzl, D, seed, start=0.1, span=math.pi, axis=None, bp_kernel="auto",
+                  interp="nearest", rot=None):
     rng = np.random.default_rng(seed)
-    rot = ph.single_axis_rotations(D, span=span, start=start, axis=axis)
+    if rot is None:
+        rot = ph.single_axis_rotations(D, span=span, start=start, axis=axis)
     r = make(rot, nu, nv, grid, lam=1e-10, delta=1e-9, defocus=np.zeros(D), nz_layers=nzl, dir_block=D,
-             bp_kernel=bp_kernel)
+             bp_kernel=bp_kernel, layer_interp=interp)
     stacks = rng.standard_normal((D, nzl, nv, nu)).astype(np.float32)
     padded = np.zeros((D, nzl, nv + 2, nu + 2), np.float32)
     padded[:, :, 1:-1, 1:-1] = stacks
@@ -101,8 +103,9 @@ def _stage_b_case(grid, nu, nv, nzl, D, seed, start=0.1, span=math.pi, axis=None
     kk, jj, ii = np.meshgrid(*(np.arange(g) for g in grid[::-1]), indexing="ij")
     i, j, k = ii.ravel(), jj.ravel(), kk.ravel()
     ref = np.zeros(i.size)
+    mode = O.LAYER_LINEAR if interp == "linear" else O.LAYER_NEAREST
     for n in range(D):
-        ref += O.backproject_direction(stacks[n].astype(np.float64), A[n], B[n], T[n], i, j, k)
+        ref += O.backproject_direction(stacks[n].astype(np.float64), A[n], B[n], T[n], i, j, k, mode)
     r.close()
     return got.ravel(), ref
 
@@ -124,6 +127,22 @@ def test_stage_b_backprojection_matches_oracle(grid, nu, nv, nzl, D, axis, bp_ke
     got, ref = _stage_b_case(grid, nu, nv, nzl, D, seed=sum(grid) + D, axis=axis, bp_kernel=bp_kernel)
     assert rel_l2(got, ref) <= TOL_F32
     # any layer or tap decided differently would show as an O(1) error at that voxel
+    assert np.max(np.abs(got - ref)) <= 1e-4 * max(np.max(np.abs(ref)), 1.0)
+
+
+@pytest.mark.parametrize("grid,nu,nv,nzl,D,axis", [
+    ((37, 20, 9), 41, 23, 5, 7, None),          # single axis (runs in the general kernel)
+    ((33, 70, 130), 160, 72, 16, 11, None),
+    ((37, 20, 9), 41, 23, 5, 7, (0.3, 1.0, -0.2)),
+    ((48, 40, 56), 64, 64, 6, 30, (0.0, 1.0, 0.5)),
+    ((20, 20, 20), 24, 24, 1, 4, (0.2, 1.0, 0.1)),   # one layer: the blend is that layer
+    ((64, 64, 64), 64, 64, 96, 12, (0.1, 1.0, 0.3)),
+], ids=["y", "y-tall", "tilted", "tilted-2", "one-layer", "thin-layers"])
+def test_stage_b_layer_blend_matches_oracle(grid, nu, nv, nzl, D, axis):
+    """The blend of the two layers whose centres bracket each voxel's depth (exact 2^-24
+    weights on both sides), voxel by voxel."""
+    got, ref = _stage_b_case(grid, nu, nv, nzl, D, seed=sum(grid) + 3 * D, axis=axis, interp="linear")
+    assert rel_l2(got, ref) <= TOL_F32
     assert np.max(np.abs(got - ref)) <= 1e-4 * max(np.max(np.abs(ref)), 1.0)
 
 
@@ -164,6 +183,18 @@ def test_small_workload_ragged_direction_blocks(small):
     cfg, img, ref = small
     got = _gpu_recon(cfg, img, dir_block=7)  # 90 = 12 * 7 + 6
     assert rel_l2(got, ref) <= TOL_F32
+
+
+def test_small_workload_layer_blend_matches_oracle(small):
+    """The whole operator with the layer blend (float32 stack) against the oracle's."""
+    cfg, img, _ = small
+    ref = O.recon(img, cfg["rot"], lam=cfg["lam"], delta=cfg["delta"], defocus=cfg["defocus"],
+                  nz_layers=cfg["nz_layers"], grid=cfg["grid"], sigma=cfg["sigma"], eps=cfg["eps"], cs=cfg["cs"],
+                  layer_interp=O.LAYER_LINEAR)
+    got = _gpu_recon(cfg, img, layer_interp="linear")
+    assert rel_l2(got, ref) <= TOL_F32, rel_l2(got, ref)
+    got16 = _gpu_recon(cfg, img, layer_interp="linear", stack_dtype="bf16")
+    assert rel_l2(got16, ref) <= TOL_BF16, rel_l2(got16, ref)
 
 
 def test_small_workload_bf16_stack(small):
