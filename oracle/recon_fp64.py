@@ -54,6 +54,7 @@ LAYER_LINEAR = 1   # a voxel takes the linear blend of the two layers whose cent
 
 FILTER_OFF = 0
 FILTER_TIKHONOV = 1
+FILTER_PAIR = 2  # the complex bracket of Eq. 11, exact for opposite-view pairs (Eq. 10)
 INPUT_INTENSITY = 0
 INPUT_CONTRAST = 1
 
@@ -177,6 +178,28 @@ def ctf_filter(P: int, delta: float, lam: float, r_eff: float, sigma: float, eps
     return lam / (4.0 * math.pi * math.sqrt(1.0 + sigma * sigma)) * s / (s * s + eps)
 
 
+def ctf_pair_filter(P: int, delta: float, lam: float, r_n: float, z_k: float, sigma: float, eps: float,
+                    cs: float = 0.0) -> np.ndarray:
+    """Per-layer filter of the opposite-pair form: the real part of one view's Eq. 11 term
+    carried to depth z_k,
+        lambda / (4 pi sqrt(1+sigma^2)) * Re{ [sin chi / (sin^2 chi + eps)
+                                               - i cos chi / (cos^2 chi + eps)] * exp(-i pi lambda z_k q^2) },
+    chi = pi lambda R_n q^2 + (pi/2) Cs lambda^3 q^4 - omega at the view's own image plane
+    (Eq. 11).  The complex term sits on the Ewald paraboloid (q, -lambda q^2 / 2) (Eq. 8);
+    its inverse 3D transform at depth z carries the factor exp(-i pi lambda z q^2) (z
+    positive downstream, so that the defocus of depth z is R - z as in Eq. 5).  A single
+    view's term is complex; summed with the opposite view's (Eq. 9: its depth -z, mirrored
+    u) the imaginary parts cancel and Eq. 10 follows, so the real part of each term is the
+    term's share of the real reconstruction."""
+    m = signed_freq(P).astype(np.float64)
+    q2 = (m[None, :] ** 2 + m[:, None] ** 2) / (P * delta) ** 2
+    chi = math.pi * lam * r_n * q2 + 0.5 * math.pi * cs * lam ** 3 * q2 * q2 - math.atan(sigma)
+    s, c = np.sin(chi), np.cos(chi)
+    bracket = s / (s * s + eps) - 1j * c / (c * c + eps)
+    depth = np.exp(-1j * math.pi * lam * z_k * q2)
+    return lam / (4.0 * math.pi * math.sqrt(1.0 + sigma * sigma)) * (bracket * depth).real
+
+
 # ----------------------------------------------------------------------------- density
 DENSITY_EPS_REL = 1e-3
 
@@ -290,7 +313,8 @@ def layer_stack(image: np.ndarray, *, delta: float, lam: float, r_n: float, z_la
     """Layer stack Y_k (k over ``z_layers``) of one image, float64 ``(Nz, nv, nu)``:
     crop(Re IDFT[G * H_k * W]) with G the DFT of the zero-padded contrast, image
     centred in the P x P frame; W is the single-axis ramp, or ``weight`` (P x P, the
-    density weighting of an arbitrary scan)."""
+    density weighting of an arbitrary scan); H_k the real-bracket layer filter
+    (``FILTER_TIKHONOV``), the opposite-pair one (``FILTER_PAIR``) or 1 (``FILTER_OFF``)."""
     nv, nu = image.shape
     P = padded_size(max(nu, nv))
     ou, ov = (P - nu) // 2, (P - nv) // 2
@@ -300,7 +324,12 @@ def layer_stack(image: np.ndarray, *, delta: float, lam: float, r_n: float, z_la
     W = ramp_weights(P, delta, n_dir)[None, :] if weight is None else weight
     out = np.empty((len(z_layers), nv, nu))
     for k, z in enumerate(z_layers):
-        F = W * ctf_filter(P, delta, lam, r_n - z, sigma, eps, cs) if filt == FILTER_TIKHONOV else W
+        if filt == FILTER_TIKHONOV:
+            F = W * ctf_filter(P, delta, lam, r_n - z, sigma, eps, cs)
+        elif filt == FILTER_PAIR:
+            F = W * ctf_pair_filter(P, delta, lam, r_n, z, sigma, eps, cs)
+        else:
+            F = W
         out[k] = np.fft.ifft2(G * F).real[ov:ov + nv, ou:ou + nu]
     return out
 

@@ -186,6 +186,55 @@ def test_layer_centres_refocus_each_layer_end_to_end(layer):
         assert err < 2e-2, err
 
 
+# ---------------------------------------------------------------- opposite-pair form (Eq. 10, 11)
+def _pair_case(layer, filt, views):
+    """Two weak blobs at the centre depth of layer `layer` of Nz = 4 over a 40-voxel-thick
+    volume, imaged along the given single-axis angles by the 4-slab multislice simulator;
+    returns the worst relative L2 error over that layer's volume slices against the same
+    scan's filter-off reconstruction of the true projections."""
+    n, nzv, nzl = 64, 40, 4
+    delta, lam, sigma, R = 1e-9, 1e-10, 0.5, 2e-7
+    z0 = -15.0 + 10.0 * layer
+    phan = ph.Phantom("blob", np.array([[3.0, -2.0, z0], [-8.0, 5.0, z0]]), np.array([2.0, 3.0]),
+                      np.array([2e-6, 1e-6]))
+    rot = np.stack([ph.single_axis_rotations(1, start=a, span=0.0)[0] for a in views])
+    Rs = np.full(len(views), R)
+    img = ph.multislice_images(phan, rot, n, n, delta, lam, Rs, sigma, n_slabs=4, thickness=40.0,
+                               dtype=__import__("torch").float64).numpy()
+    truth = ph.layer_projections(phan, rot, n, n, (n, n, nzv), 1, delta)[:, 0]
+    vol = O.recon(img, rot, lam=lam, delta=delta, defocus=Rs, nz_layers=nzl, grid=(n, n, nzv), sigma=sigma,
+                  eps=1e-14, filt=filt)
+    ref = O.recon(truth, rot, lam=lam, delta=delta, defocus=Rs, nz_layers=1, grid=(n, n, nzv), filt=O.FILTER_OFF,
+                  input_mode=O.INPUT_CONTRAST)
+    return max(np.linalg.norm(vol[q] - ref[q]) / np.linalg.norm(ref[q]) for q in range(10 * layer, 10 * layer + 10))
+
+
+@pytest.mark.parametrize("layer", [0, 1, 3])
+def test_pair_form_recovers_a_slab_from_a_view_and_its_opposite(layer):
+    """Eq. 10: the images at opposite directions (0 and 180 degrees about y) together
+    determine F3 delta on the Ewald paraboloid; with eps -> 0 the pair filter (the real part
+    of each view's Eq. 11 term at the layer depth) returns the slab's true projection at
+    its depth, for slabs upstream, near and downstream of the centre (0.25 % here).  One
+    view alone is not enough: its imaginary part has no partner (error far above 100 %)."""
+    assert _pair_case(layer, O.FILTER_PAIR, (0.0, math.pi)) < 1e-2
+    assert _pair_case(layer, O.FILTER_PAIR, (0.0,)) > 1.0
+
+
+def test_pair_filter_at_the_image_plane_is_the_real_bracket_inverse():
+    """With eps -> 0 at depth 0 the pair filter reduces to Re{2 e^{-i chi} / sin 2 chi} =
+    1 / sin chi, Eq. 13's inverse at the image-plane defocus (the identity linking Eq. 10
+    and Eq. 11), away from the zeros of sin chi and cos chi."""
+    P, delta, lam, sigma, R = 64, 1e-9, 1e-10, 0.3, 1.3e-7
+    m = O.signed_freq(P).astype(float)
+    q2 = (m[None, :] ** 2 + m[:, None] ** 2) / (P * delta) ** 2
+    chi = math.pi * lam * R * q2 - math.atan(sigma)
+    a = O.ctf_pair_filter(P, delta, lam, R, 0.0, sigma, 1e-15)
+    b = O.ctf_filter(P, delta, lam, R, sigma, 1e-15)
+    good = (np.abs(np.sin(chi)) > 1e-3) & (np.abs(np.cos(chi)) > 1e-3)
+    assert good.sum() > P * P // 2
+    assert np.allclose(a[good], b[good], rtol=1e-6, atol=0)
+
+
 # ---------------------------------------------------------------- linear blend between layers
 def test_layer_blend_is_affine_in_the_exact_depth():
     """Layers that are affine in their index, Y_k = k U + V, blend to (t - 1/2) U + V with t
