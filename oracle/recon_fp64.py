@@ -55,6 +55,8 @@ LAYER_LINEAR = 1   # a voxel takes the linear blend of the two layers whose cent
 FILTER_OFF = 0
 FILTER_TIKHONOV = 1
 FILTER_PAIR = 2  # the complex bracket of Eq. 11, exact for opposite-view pairs (Eq. 10)
+FILTER_DEPTH_COS = 3  # per layer cos(pi lambda z_k q^2): the real part of the Ewald placement
+FILTER_DEPTH_SIN = 4  # per layer sin(pi lambda z_k q^2): minus its imaginary part
 INPUT_INTENSITY = 0
 INPUT_CONTRAST = 1
 
@@ -200,6 +202,18 @@ def ctf_pair_filter(P: int, delta: float, lam: float, r_n: float, z_k: float, si
     return lam / (4.0 * math.pi * math.sqrt(1.0 + sigma * sigma)) * (bracket * depth).real
 
 
+def depth_phase_filter(P: int, delta: float, lam: float, z_k: float, sine: bool) -> np.ndarray:
+    """cos or sin of pi lambda z_k q^2 on the P x P DFT grid: the real part and minus the
+    imaginary part of exp(-i pi lambda z_k q^2), which carries a sample of the Ewald
+    paraboloid (q, -lambda q^2 / 2) to depth z_k (Eq. 8).  With these per-layer filters and
+    no CTF bracket the layered reconstruction is the CT step of Eq. 12 (the Ewald-placed
+    reconstruction of the contrasts, as two real volumes)."""
+    m = signed_freq(P).astype(np.float64)
+    q2 = (m[None, :] ** 2 + m[:, None] ** 2) / (P * delta) ** 2
+    ph = math.pi * lam * z_k * q2
+    return np.sin(ph) if sine else np.cos(ph)
+
+
 # ----------------------------------------------------------------------------- density
 DENSITY_EPS_REL = 1e-3
 
@@ -328,6 +342,8 @@ def layer_stack(image: np.ndarray, *, delta: float, lam: float, r_n: float, z_la
             F = W * ctf_filter(P, delta, lam, r_n - z, sigma, eps, cs)
         elif filt == FILTER_PAIR:
             F = W * ctf_pair_filter(P, delta, lam, r_n, z, sigma, eps, cs)
+        elif filt in (FILTER_DEPTH_COS, FILTER_DEPTH_SIN):
+            F = W * depth_phase_filter(P, delta, lam, z, filt == FILTER_DEPTH_SIN)
         else:
             F = W
         out[k] = np.fft.ifft2(G * F).real[ov:ov + nv, ou:ou + nu]
