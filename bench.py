@@ -43,7 +43,7 @@ WORKLOAD_TEXT = {
               "20 uniform balls (r U[2,8] vox, delta U[1e-6,1e-5]); multislice images, 1e4 photons/px"),
     "learned": ("learned-filter scan: 512^3 grid (0.1 nm voxels), 720 single-axis directions over 180 deg, "
                 "512x512 float32 images, lambda 1.97 pm, Nz=64 layers, R_n ~ U[0.5,1.5] um, Cs 2.7 mm, sigma "
-                "0.07, eps 0.1; 1.6e5 Gaussian pseudo-atoms; 100 e/px (--filter mlp: seeded network)"),
+                "0.07, eps 0.1; 1.6e5 Gaussian pseudo-atoms; 100 e/px (--filter mlp: the trained network)"),
     "slab": ("arbitrary geometry, large slab: 1024x1024x256 grid (0.05 nm voxels), 1500 Haar-random directions "
              "within 60 deg of the slab normal, 1024x1024 float32 images, lambda 1.97 pm, Nz=64 layers, R 1 um, "
              "Cs 2.7 mm, sampling-density weighting; 2e5 Gaussian pseudo-atoms filling the slab; 50 e/px"),
@@ -179,13 +179,14 @@ def sample_voxels(cfg):
 def oracle_sample(cfg, images_np, dirs, mlp=None, voxels=None, workers: int = 1):
     """FP64 oracle on the directions ``dirs`` alone (a D = len(dirs) scan), at ``voxels`` or
     over the full volume, in ``workers`` processes; ``mlp`` = (weights, nsr) selects the
-    learned regulariser."""
+    learned regulariser (with ``views``, the divisor of its eps)."""
     import oracle as O
     kw = dict(lam=cfg["lam"], delta=cfg["delta"], defocus=cfg["defocus"][dirs], nz_layers=cfg["nz_layers"],
               grid=cfg["grid"], sigma=cfg["sigma"], cs=cfg["cs"], voxels=voxels, workers=workers,
               density=cfg.get("ramp", "single_axis") == "density")
     if mlp is not None:
         return O.learned.recon_learned(images_np[dirs], cfg["rot"][dirs], mlp[0].astype(np.float64), nsr=mlp[1],
+                                       views=mlp[2],
                                        **kw)
     return O.recon(images_np[dirs], cfg["rot"][dirs], eps=cfg["eps"], **kw)
 
@@ -345,9 +346,10 @@ def run_ours(args):
     filt_kw = {}
     mlp = None
     if args.filter == "mlp":
-        from paper_2206_09151_gb300 import phantoms as ph
-        mlp = (ph.mlp_init(17).astype(np.float32), float(cfg["photons"]) ** -0.5)
-        filt_kw = dict(filter="mlp", mlp_weights=mlp[0], nsr=mlp[1])
+        # the trained regulariser; its per-view eps divided by the D views the volume averages
+        from paper_2206_09151_gb300.train_regulariser import load_weights
+        mlp = (load_weights(), float(cfg["photons"]) ** -0.5, float(D))
+        filt_kw = dict(filter="mlp", mlp_weights=mlp[0], nsr=mlp[1], mlp_views=mlp[2])
     r = Reconstructor(cfg["rot"], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
                       defocus=cfg["defocus"], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"], eps=cfg["eps"],
                       cs=cfg["cs"], stack_dtype=args.stack, dir_block=args.dir_block, stage_block=args.stage_block,
@@ -471,6 +473,43 @@ def run_ours(args):
                     "d2h_bytes_per_step": vol.numel() * 4},
             "gpu_launches": sum(kern_n) + (2 * kern_n[0] if args.filter == "mlp" else 0), "roofline": roofline, "kernels": kernels, "clocks": clocks}
 
+    if rank == 0 and world == 1 and args.filter == "mlp":
+        # learned against analytic regulariser on the same GPU: speed, and the error of each
+        # against the phantom (pseudo-atoms sampled at the voxel centres) over the field of view
+        from paper_2206_09151_gb300 import phantoms as ph
+        from paper_2206_09151_gb300.layer_study import phantom_volume
+        truth = phantom_volume(ph.make_phantom(cfg), cfg["grid"], dev)
+        nx, ny, nz = cfg["grid"]
+        if cfg["ramp"] == "single_axis":
+            xx = torch.arange(nx, device=dev, dtype=torch.float64) - (nx - 1) / 2
+            zz = torch.arange(nz, device=dev, dtype=torch.float64) - (nz - 1) / 2
+            fov = ((xx[None, :] ** 2 + zz[:, None] ** 2) <= (0.5 * min(nx, nz) - 2) ** 2)[:, None, :].expand(nz, ny, nx)
+        else:
+            fov = torch.ones((nz, ny, nx), dtype=torch.bool, device=dev)
+        compare = {}
+        for name, kw in (("learned", filt_kw), ("tikhonov eps=%g" % cfg["eps"], {})):
+            rr = Reconstructor(cfg["rot"], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
+                               defocus=cfg["defocus"], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"], eps=cfg["eps"],
+                               cs=cfg["cs"], stack_dtype=args.stack, dir_block=args.dir_block, ramp=cfg["ramp"],
+                               device=dev, **kw)
+            vv = rr.new_volume()
+            rr.run(images, vv)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rr.run(images, vv, stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            err = float(torch.linalg.norm((vv.double() - truth)[fov]) / torch.linalg.norm(truth[fov]))
+            compare[name] = {"ms_per_step": min(ts), "rel_l2_vs_phantom": err}
+            rr.close()
+            del vv
+        line["learned_vs_analytic"] = dict(compare, nsr=mlp[1], mlp_views=D,
+                                           weights="paper_2206_09151_gb300/data/regulariser.npz")
+        del truth
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # the oracle on a bounded sample (a few directions spread over the host cores), beside
         # the same sample reconstructed on the GPU: the stated accuracy and the CPU rate
@@ -626,7 +665,8 @@ def main():
     ap.add_argument("--stack", choices=["f32", "bf16"], default=None,
                     help="layer-stack precision (default: the workload's, f32 for mid/small, bf16 otherwise)")
     ap.add_argument("--filter", choices=["tikhonov", "mlp"], default="tikhonov",
-                    help="mlp: the learned regulariser (seeded untrained weights; speed and parity)")
+                    help="mlp: the trained learned regulariser (data/regulariser.npz), reported beside the "
+                         "analytic one")
     ap.add_argument("--dir-block", type=int, default=0)
     ap.add_argument("--stage-block", type=int, default=0, help="directions per FFT/filter sub-block, 0 = auto")
     ap.add_argument("--bp-kernel", choices=["auto", "direct", "staged"], default="auto",

@@ -62,6 +62,12 @@ extern "C" {
 #define RECON_FILTER_OFF 0       /* H = 1: ramp-filtered backprojection of g (Eq. 15)   */
 #define RECON_FILTER_TIKHONOV 1  /* H_k above (real part of Eq. 11, per layer)         */
 #define RECON_FILTER_MLP 2       /* H_k with eps from the learned network (see below)   */
+#define RECON_FILTER_PAIR 3      /* the opposite-pair form of Eq. 10 / Eq. 11: per layer
+                                    lambda / (4 pi sqrt(1+sigma^2)) Re{[sin chi / (sin^2 chi
+                                    + eps) - i cos chi / (cos^2 chi + eps)] exp(-i pi lambda
+                                    z_k q^2)} with chi at the view's image plane (R_n, Cs,
+                                    omega); exact (eps -> 0) only when the scan holds each
+                                    view's opposite (360-degree or full-sphere scans)       */
 
 /* Parameters of the learned regulariser: a 3 -> 64 -> 64 -> 1 ReLU network, float32,
  * laid out W1[64][3], b1[64], W2[64][64], b2[64], w3[64], b3. */
@@ -108,7 +114,7 @@ typedef struct {
 
 typedef struct {
   double sigma;    /* beta/delta of the monomorphous object (Eq. 7); omega = atan(sigma) */
-  double eps;      /* Tikhonov parameter of Eq. 11, > 0 when filter = TIKHONOV         */
+  double eps;      /* Tikhonov parameter of Eq. 11, > 0 when filter = TIKHONOV or PAIR  */
   double cs;       /* spherical aberration Cs (metres), 0 = none                        */
   int filter;      /* RECON_FILTER_*                                                    */
   int input_mode;  /* RECON_INPUT_*                                                     */
@@ -130,6 +136,10 @@ typedef struct {
                        RECON_E_NONFINITE without touching the volume if it finds any; 0: no
                        scan (a NaN then propagates into the voxels it reaches)             */
   int layer_interp; /* RECON_LAYER_*: nearest layer, or the blend of the two bracketing ones */
+  double mlp_views; /* RECON_FILTER_MLP: views averaged per voxel (a full scan's D); the
+                       network's eps, a per-view noise-to-signal power (Wiener), is divided by
+                       it, since the reconstruction averages that many independent views;
+                       0 or 1 = a single view's eps                                          */
 } recon_options;
 
 /* Fills *opts with defaults: sigma 0, eps 0.1 (the value of Sec. 3), cs 0, Tikhonov
@@ -223,6 +233,42 @@ int recon_plan_layers(recon_plan_t plan, int* nz_layers);
 const char* recon_plan_warning(recon_plan_t plan);
 int recon_layers_for_dof(const recon_geometry* geom, const recon_grid* grid, double lambda, double delta, int* nz);
 
+/* ---------------------------------------------------------------- 3D-Fourier forms
+ * Eq. 12 (Sec. 2): with one defocus R for every view, the CT reconstruction comes first and
+ * the CTF inversion is one 3D filter after it, so another (sigma, eps) reruns only that.
+ *   recon_swap_ct     the CT step: the layered reconstruction of the contrasts with the
+ *                     Ewald placement and no CTF (per layer cos and sin of pi lambda z_k q^2:
+ *                     two real volumes V_c, V_s), packed as V_c + i V_s into a grid zero-
+ *                     padded to P3 = the next power of two >= 2 n per axis and transformed;
+ *                     the spectrum stays in the workspace.  The plan must use
+ *                     RECON_FILTER_PAIR (its depth tables) and one defocus for every view.
+ *   recon_swap_phase  the CTF inversion of the kept spectrum: F3 delta = lambda / (4 pi
+ *                     sqrt(1+sigma^2)) [s' F3 V_c - c' F3 V_s], s' = sin chi / (sin^2 chi +
+ *                     eps), c' = cos chi / (cos^2 chi + eps), chi at the in-plane frequency
+ *                     of each 3D frequency's Ewald-paraboloid point (the plan's Cs); inverse
+ *                     transform, crop into volume [nz][ny][nx].  Needs a workspace on which
+ *                     recon_swap_ct has run; can run any number of times.
+ * The Fourier-gridding UTR (Sec. 2 after Eq. 11; Sec. 3 for the noise filter):
+ *   recon_grid_run    every 2D DFT coefficient of every view times Eq. 11's bracket at the
+ *                     view's own R_n, spread with trilinear weights onto the 8 cells around
+ *                     its point Rot_n^T (q_u, q_v, -lambda q^2 / 2) of the padded volume's DFT
+ *                     grid; divided by S + eps_S (S the summed weights, eps_S = 1e-3 x its
+ *                     mean over the non-empty cells); nsr > 0 zeroes the coefficients whose
+ *                     gridded contrast (the same splat without the bracket, over S + eps_S)
+ *                     is below nsr M / sqrt(S), M^2 = nu nv; inverse transform, crop.  Any
+ *                     geometry; the plan's sigma, eps, cs and input mode; its filter must be
+ *                     TIKHONOV or PAIR (eps > 0).
+ * The caller owns images, volume and workspace (256-byte aligned, of the *_workspace_size
+ * bytes).  Limits: every grid side <= 1024 (UNSUPPORTED_SIZE beyond), images of more than
+ * 8 pixels. */
+int recon_swap_workspace_size(recon_plan_t plan, size_t* bytes);
+int recon_swap_ct(recon_plan_t plan, const float* images, void* workspace, size_t ws_bytes, void* stream);
+int recon_swap_phase(recon_plan_t plan, double sigma, double eps, float* volume, void* workspace, size_t ws_bytes,
+                     void* stream);
+int recon_grid_workspace_size(recon_plan_t plan, size_t* bytes);
+int recon_grid_run(recon_plan_t plan, const float* images, float* volume, double nsr, void* workspace,
+                   size_t ws_bytes, void* stream);
+
 /* Plan facts: padded FFT size P, directions per block, number of blocks, directions per
  * FFT/filter sub-block (any pointer may be NULL). */
 int recon_plan_info(recon_plan_t plan, int* padded, int* dir_block, int* n_blocks, int* stage_block);
@@ -239,7 +285,9 @@ int recon_plan_info(recon_plan_t plan, int* padded, int* dir_block, int* n_block
  * T_nk(q)|^2 / sum |T_nk(q)|^2 (G: DFT of the contrast, T: DFT of the true projection of
  * layer k's slab, in metres) with Adam (beta 0.9 / 0.999), on the GPU.  steps = 0
  * returns the loss and (if grad != NULL) its gradient at the given weights.  The call
- * waits for `stream` before returning. */
+ * waits for `stream` before returning.  The loss is over the call's images (full batch);
+ * a training set larger than one workspace is fed as mini-batches in successive calls
+ * that pass the same adam_state and advance adam_step by steps each time. */
 typedef struct {
   int n_img, nu, nv, nz_layers;  /* training images, image size, layers per image        */
   const double* rot;             /* host [n_img][9] rotations (as in recon_geometry)      */
@@ -251,6 +299,11 @@ typedef struct {
   const float* targets;          /* device [n_img][nz_layers][nv][nu] layer projections   */
   int steps;                     /* Adam steps                                            */
   float lr;                      /* Adam step size                                        */
+  float* adam_state;             /* host [2 RECON_MLP_PARAMS]: Adam's first and second
+                                    moments, read at the start and written back at the end
+                                    (mini-batches in successive calls continue one
+                                    optimisation), or NULL: fresh moments, not returned     */
+  int adam_step;                 /* Adam steps taken before this call (bias correction)   */
 } recon_train_cfg;
 
 int recon_mlp_train_workspace_size(const recon_train_cfg* cfg, size_t* bytes);

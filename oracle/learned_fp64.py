@@ -149,7 +149,7 @@ def learned_filter(P, delta, lam, r_eff, sigma, eps_bins, cs=0.0):
 def _partial_learned(args):
     """Sum over directions ``dirs`` of their learned-filter contributions to voxels (i, j, k)."""
     (images, rot, dirs, theta, lam, delta, defocus, nz_layers, grid, sigma, nsr, cs, input_mode, i, j, k,
-     density, interp) = args
+     density, interp, views) = args
     D, nv, nu = images.shape
     P = R.padded_size(max(nu, nv))
     A, B = R.pixel_coefficients(rot, grid, nu, nv)
@@ -162,6 +162,7 @@ def _partial_learned(args):
     for o, n in enumerate(dirs):
         r_eff = float(defocus[n]) - zc[n]
         eps = eps_table(theta, images[n], r_eff=r_eff, lam=lam, delta=delta, nsr=nsr, input_mode=input_mode)
+        eps = eps / views
         g = np.zeros((P, P))
         g[ov:ov + nv, ou:ou + nu] = R.contrast(images[n], input_mode)
         G = np.fft.fft2(g)
@@ -176,11 +177,13 @@ def _partial_learned(args):
 
 def recon_learned(images, rot, theta, *, lam, delta, defocus, nz_layers, grid, sigma, nsr, cs=0.0,
                   input_mode=R.INPUT_INTENSITY, voxels=None, workers: int = 1, density: bool = False,
-                  layer_interp: int = R.LAYER_NEAREST):
+                  layer_interp: int = R.LAYER_NEAREST, views: float = 1.0):
     """The whole operator with the learned regulariser: the single-axis ramp, or the
     sampling-density weighting of an arbitrary scan (``density``).  ``voxels`` = (i, j, k)
     returns those voxels only; ``workers`` > 1 splits the directions over a spawned
-    process pool (the same arithmetic, summed in another order)."""
+    process pool (the same arithmetic, summed in another order).  ``views`` > 1 divides the
+    network's eps (a per-view noise-to-signal power, the Wiener reading) by the number of
+    independent views the reconstruction averages."""
     images = np.asarray(images)
     rot = np.asarray(rot, np.float64)
     theta = np.asarray(theta, np.float64)
@@ -192,7 +195,7 @@ def recon_learned(images, rot, theta, *, lam, delta, defocus, nz_layers, grid, s
     else:
         i, j, k = (np.asarray(x, np.int64) for x in voxels)
     common = (theta, lam, delta, np.asarray(defocus, np.float64), nz_layers, tuple(grid), sigma, nsr, cs, input_mode,
-              i, j, k, density, layer_interp)
+              i, j, k, density, layer_interp, max(1.0, float(views)))
     dirs = list(range(D))
     if workers <= 1 or D < 2:
         acc = _partial_learned((images, rot, dirs) + common)

@@ -25,6 +25,7 @@ RECON_E_NO_WEIGHTS = -7
 RECON_FILTER_OFF = 0
 RECON_FILTER_TIKHONOV = 1
 RECON_FILTER_MLP = 2
+RECON_FILTER_PAIR = 3
 RECON_MLP_PARAMS = 4481
 RECON_INPUT_INTENSITY = 0
 RECON_INPUT_CONTRAST = 1
@@ -53,7 +54,7 @@ class ReconOptions(ctypes.Structure):
                 ("ramp_mode", ctypes.c_int), ("accumulate", ctypes.c_int), ("dir_block", ctypes.c_int),
                 ("mlp_weights", ctypes.POINTER(ctypes.c_float)), ("nsr", ctypes.c_double),
                 ("stage_block", ctypes.c_int), ("bp_kernel", ctypes.c_int), ("check_finite", ctypes.c_int),
-                ("layer_interp", ctypes.c_int)]
+                ("layer_interp", ctypes.c_int), ("mlp_views", ctypes.c_double)]
 
 
 class ReconTrainCfg(ctypes.Structure):
@@ -63,7 +64,7 @@ class ReconTrainCfg(ctypes.Structure):
                 ("lambda_", ctypes.c_double), ("delta", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("cs", ctypes.c_double), ("nsr", ctypes.c_double), ("input_mode", ctypes.c_int),
                 ("images", ctypes.c_void_p), ("targets", ctypes.c_void_p), ("steps", ctypes.c_int),
-                ("lr", ctypes.c_float)]
+                ("lr", ctypes.c_float), ("adam_state", ctypes.POINTER(ctypes.c_float)), ("adam_step", ctypes.c_int)]
 
 
 class ReconError(RuntimeError):
@@ -97,6 +98,11 @@ def load_library(path: str = LIB_PATH):
     L.recon_run_noalloc.argtypes = [vp, vp, vp, vp]
     L.recon_plan_dof.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.recon_plan_layers.argtypes = [vp, ctypes.POINTER(ip)]
+    L.recon_swap_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
+    L.recon_swap_ct.argtypes = [vp, vp, vp, sz, vp]
+    L.recon_swap_phase.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp, vp, sz, vp]
+    L.recon_grid_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
+    L.recon_grid_run.argtypes = [vp, vp, vp, ctypes.c_double, vp, sz, vp]
     L.recon_plan_warning.argtypes = [vp]
     L.recon_plan_warning.restype = ctypes.c_char_p
     L.recon_layers_for_dof.argtypes = [ctypes.POINTER(ReconGeometry), ctypes.POINTER(ReconGrid), ctypes.c_double,
@@ -125,7 +131,8 @@ def load_library(path: str = LIB_PATH):
                  "recon_run_noalloc", "recon_mlp_train_workspace_size", "recon_mlp_train", "recon_batch_create",
                  "recon_batch_workspace_size", "recon_batch_run", "recon_batch_run_graph", "recon_batch_destroy",
                  "recon_run_batch_workspace_size", "recon_run_batch", "recon_plan_dof", "recon_layers_for_dof",
-                 "recon_plan_layers"):
+                 "recon_plan_layers", "recon_swap_workspace_size", "recon_swap_ct", "recon_swap_phase",
+                 "recon_grid_workspace_size", "recon_grid_run"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -166,14 +173,21 @@ def recon_plan(rot: np.ndarray, nu: int, nv: int, lam: float, delta: float, defo
 
 
 def make_train_cfg(rot, defocus, nu, nv, nz_layers, grid, lam, delta, sigma, cs, nsr, input_mode, images_ptr,
-                   targets_ptr, steps, lr):
-    """A recon_train_cfg; returns it with the host arrays it points to (keep both alive)."""
+                   targets_ptr, steps, lr, adam_state=None, adam_step=0):
+    """A recon_train_cfg; returns it with the host arrays it points to (keep both alive).
+    ``adam_state`` (float32 [2 RECON_MLP_PARAMS], updated in place) carries Adam's moments
+    from one call to the next."""
     rot = np.ascontiguousarray(rot, dtype=np.float64).reshape(-1, 3, 3)
     defocus = np.ascontiguousarray(defocus, dtype=np.float64).reshape(-1)
+    fp = ctypes.POINTER(ctypes.c_float)
+    if adam_state is not None and (adam_state.dtype != np.float32 or adam_state.size != 2 * RECON_MLP_PARAMS
+                                   or not adam_state.flags["C_CONTIGUOUS"]):
+        raise ValueError("adam_state must be a contiguous float32 array of 2 * RECON_MLP_PARAMS values")
     cfg = ReconTrainCfg(rot.shape[0], nu, nv, nz_layers, rot.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                         defocus.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), grid[0], grid[1], grid[2], lam,
-                        delta, sigma, cs, nsr, input_mode, images_ptr, targets_ptr, steps, lr)
-    return cfg, (rot, defocus)
+                        delta, sigma, cs, nsr, input_mode, images_ptr, targets_ptr, steps, lr,
+                        adam_state.ctypes.data_as(fp) if adam_state is not None else None, int(adam_step))
+    return cfg, (rot, defocus, adam_state)
 
 
 def recon_mlp_train_workspace_size(cfg: ReconTrainCfg) -> int:
@@ -242,6 +256,30 @@ def recon_layers_for_dof(rot: np.ndarray, grid, lam: float, delta: float) -> int
 
 def recon_run(plan, images_ptr: int, volume_ptr: int, ws_ptr: int, ws_bytes: int, stream: int):
     _check(load_library().recon_run(plan, images_ptr, volume_ptr, ws_ptr, ws_bytes, stream), "recon_run")
+
+
+def recon_swap_workspace_size(plan) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().recon_swap_workspace_size(plan, ctypes.byref(n)), "recon_swap_workspace_size")
+    return n.value
+
+
+def recon_swap_ct(plan, images_ptr: int, ws_ptr: int, ws_bytes: int, stream: int):
+    _check(load_library().recon_swap_ct(plan, images_ptr, ws_ptr, ws_bytes, stream), "recon_swap_ct")
+
+
+def recon_swap_phase(plan, sigma: float, eps: float, volume_ptr: int, ws_ptr: int, ws_bytes: int, stream: int):
+    _check(load_library().recon_swap_phase(plan, sigma, eps, volume_ptr, ws_ptr, ws_bytes, stream), "recon_swap_phase")
+
+
+def recon_grid_workspace_size(plan) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().recon_grid_workspace_size(plan, ctypes.byref(n)), "recon_grid_workspace_size")
+    return n.value
+
+
+def recon_grid_run(plan, images_ptr: int, volume_ptr: int, nsr: float, ws_ptr: int, ws_bytes: int, stream: int):
+    _check(load_library().recon_grid_run(plan, images_ptr, volume_ptr, nsr, ws_ptr, ws_bytes, stream), "recon_grid_run")
 
 
 def recon_run_noalloc(plan, images_ptr: int, volume_ptr: int, stream: int):

@@ -177,8 +177,14 @@ __device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const Di
   }
 }
 
+// Resident CTAs per SM the general kernel asks for (registers per thread = 65536 / (256 x
+// this)); a compile-time tuning constant.
+#ifndef RECON_GEN_MIN_CTAS
+#define RECON_GEN_MIN_CTAS 4
+#endif
+
 template <typename ST, bool LIN>
-__global__ void __launch_bounds__(kTX* kTY, 4) k_backproject(const DirParams* __restrict__ dirs,
+__global__ void __launch_bounds__(kTX* kTY, RECON_GEN_MIN_CTAS) k_backproject(const DirParams* __restrict__ dirs,
                                                            const ST* __restrict__ stack, BackprojConst c,
                                                            int dir_begin, int dir_count, float* __restrict__ vol,
                                                            int accumulate) {

@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(kThreads) k_eps_table(const float* __restrict_
     acts[row * kActStride + 2] = x[2];
     acts[row * kActStride + 3 + 2 * H] = o;
   }
-  eps[row] = softplus(o);
+  eps[row] = softplus(o) * lc.eps_scale;
 }
 
 // ----------------------------------------------------------------- training loss

@@ -18,6 +18,7 @@ struct LearnConst {
   int n_bins, bin_width;
   float inv_half_p;   // 2 / P
   float noise_floor;  // nsr^2 * nu * nv: Poisson power per DFT coefficient (Parseval)
+  float eps_scale;    // 1 / (views averaged per voxel): the network's per-view eps divided (1 in training)
 };
 
 cudaError_t launch_cols_forward(const StageAConst& c, const LearnConst& lc, const float2* S, float2* G_out,

@@ -43,6 +43,40 @@ uint64_t half_turns_fixed(double x) {
   return (uint64_t)scaled;
 }
 
+// Per-pass twiddles of the register FFTs for length P: the 8-value table of fft_reg.cuh
+// (the pass at sub-length Ns, radix R, holds exp(-2 pi i kb r / (Ns R)) at (Ns - 8) +
+// kb (R - 1) + (r - 1)), then for P >= 256 that of fft16.cuh at (P - 8) + (Ns - 16) + ...
+std::vector<float2> fft_twiddles(int P) {
+  std::vector<float2> t(P >= 16 ? (P - 8) + (P >= 256 ? P - 16 : 0) : 1, float2{0.f, 0.f});
+  if (P >= 256) {
+    for (int Ns = 1; Ns < P;) {
+      const int rem = P / Ns;
+      const int R = (rem % 16 == 0) ? 16 : rem;
+      if (Ns > 1)
+        for (int kb = 0; kb < Ns; ++kb)
+          for (int r = 1; r < R; ++r) {
+            const double ang = -2.0 * M_PI * (double)kb * r / ((double)Ns * R);
+            t[(P - 8) + (Ns - 16) + kb * (R - 1) + (r - 1)] = float2{(float)std::cos(ang), (float)std::sin(ang)};
+          }
+      Ns *= R;
+    }
+  }
+  if (P >= 16) {
+    for (int Ns = 1; Ns < P;) {
+      const int rem = P / Ns;
+      const int R = (rem % 8 == 0) ? 8 : rem;
+      if (Ns > 1)
+        for (int kb = 0; kb < Ns; ++kb)
+          for (int r = 1; r < R; ++r) {
+            const double ang = -2.0 * M_PI * (double)kb * r / ((double)Ns * R);
+            t[(Ns - 8) + kb * (R - 1) + (r - 1)] = float2{(float)std::cos(ang), (float)std::sin(ang)};
+          }
+      Ns *= R;
+    }
+  }
+  return t;
+}
+
 }  // namespace
 
 struct recon_plan_s {
@@ -66,6 +100,13 @@ struct recon_plan_s {
   size_t off_flag;                 // device counter of the finiteness scan
   double pitch_max = 0.0, dof = 0.0;  // largest layer pitch and Delta^2 / (2 lambda), metres
   std::string warning;             // plan-time warning ("" if none)
+  // the 3D-Fourier forms (Eq. 12, the Fourier-gridding UTR)
+  bool uniform_R = false;          // every view has the same defocus (Eq. 12's condition)
+  double R0 = 0.0;
+  bool f3_ok = false;              // every grid side <= 1024 (padded 3D grid <= 2048 per axis)
+  recon::Fourier3Const f3;
+  std::vector<float2> tw3[3];      // FFT twiddles of each padded grid axis
+  std::vector<recon::GridDir> gdirs;
   // optional profiling: one event after every launch (see recon::EventRecorder)
   bool profile = false;
   std::vector<cudaEvent_t> events;
@@ -95,6 +136,7 @@ void recon_default_options(recon_options* o) {
   o->bp_kernel = RECON_BP_AUTO;
   o->check_finite = 0;
   o->layer_interp = RECON_LAYER_NEAREST;
+  o->mlp_views = 0.0;
 }
 
 const char* recon_error_string(int code) {
@@ -143,13 +185,16 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   recon_options o;
   recon_default_options(&o);
   if (opts) o = *opts;
-  if (o.filter != RECON_FILTER_OFF && o.filter != RECON_FILTER_TIKHONOV && o.filter != RECON_FILTER_MLP)
+  if (o.filter != RECON_FILTER_OFF && o.filter != RECON_FILTER_TIKHONOV && o.filter != RECON_FILTER_MLP &&
+      o.filter != RECON_FILTER_PAIR)
     return fail(RECON_E_INVALID_ARG, "recon_plan: unknown filter");
   if (o.filter == RECON_FILTER_MLP && !training && !o.mlp_weights)
     return fail(RECON_E_NO_WEIGHTS, "recon_plan: the learned filter needs mlp_weights (RECON_MLP_PARAMS floats)");
   if (o.filter == RECON_FILTER_MLP && !training && (!(o.nsr > 0.0) || !std::isfinite(o.nsr)))
     return fail(RECON_E_INVALID_ARG, "recon_plan: the learned filter needs nsr > 0");
   if (o.check_finite != 0 && o.check_finite != 1) return fail(RECON_E_INVALID_ARG, "recon_plan: check_finite must be 0 or 1");
+  if (!(o.mlp_views >= 0.0) || !std::isfinite(o.mlp_views))
+    return fail(RECON_E_INVALID_ARG, "recon_plan: mlp_views must be >= 0");
   if (o.layer_interp != RECON_LAYER_NEAREST && o.layer_interp != RECON_LAYER_LINEAR)
     return fail(RECON_E_INVALID_ARG, "recon_plan: unknown layer_interp");
   if (o.input_mode != RECON_INPUT_INTENSITY && o.input_mode != RECON_INPUT_CONTRAST)
@@ -162,8 +207,8 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
     o.ramp_mode = RECON_RAMP_SINGLE_AXIS;
     o.filter = RECON_FILTER_MLP;
   }
-  if (o.filter == RECON_FILTER_TIKHONOV && !(o.eps > 0.0))
-    return fail(RECON_E_INVALID_ARG, "recon_plan: eps must be > 0 with the Tikhonov filter");
+  if ((o.filter == RECON_FILTER_TIKHONOV || o.filter == RECON_FILTER_PAIR) && !(o.eps > 0.0))
+    return fail(RECON_E_INVALID_ARG, "recon_plan: eps must be > 0 with the Tikhonov and pair filters");
   if (!std::isfinite(o.sigma) || !std::isfinite(o.eps) || !std::isfinite(o.cs))
     return fail(RECON_E_INVALID_ARG, "recon_plan: non-finite sigma, eps or cs");
   if (o.dir_block < 0) return fail(RECON_E_INVALID_ARG, "recon_plan: dir_block < 0");
@@ -195,7 +240,9 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
 
   try {
     p->dirs.resize(D);
-    p->uA.resize((size_t)D * nz_layers);
+    // per-layer phase constants; the pair filter keeps the image-plane constant after them
+    const int uA_row = nz_layers + (o.filter == RECON_FILTER_PAIR ? 1 : 0);
+    p->uA.resize((size_t)D * uA_row);
     const double cx = 0.5 * (p->nx - 1), cy = 0.5 * (p->ny - 1), cz = 0.5 * (p->nz - 1);
     const double PD = (double)P * delta;
     for (int n = 0; n < D; ++n) {
@@ -278,9 +325,16 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
       if (extm / nz_layers > p->pitch_max) p->pitch_max = extm / nz_layers;
       for (int k = 0; k < nz_layers; ++k) {
         const double zk = -0.5 * extm + (k + 0.5) * (extm / nz_layers);
-        const double Ak = lambda * (defocus[n] - zk) / (PD * PD);
-        p->uA[(size_t)n * nz_layers + k] = half_turns_fixed(Ak);
+        if (o.filter == RECON_FILTER_PAIR) {
+          // depth phase pi lambda z_k q^2 of the layer; chi's defocus term at the image plane
+          p->uA[(size_t)n * uA_row + k] = half_turns_fixed(lambda * zk / (PD * PD));
+        } else {
+          const double Ak = lambda * (defocus[n] - zk) / (PD * PD);
+          p->uA[(size_t)n * uA_row + k] = half_turns_fixed(Ak);
+        }
       }
+      if (o.filter == RECON_FILTER_PAIR)
+        p->uA[(size_t)n * uA_row + nz_layers] = half_turns_fixed(lambda * defocus[n] / (PD * PD));
     }
     // Depth of field (Sec. 1): a layer thicker than Delta^2 / (2 lambda) holds voxels out of
     // its own focus; reported as a warning, not an error.
@@ -314,38 +368,7 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
       p->tw[j].x = (float)std::cos(2.0 * M_PI * j / P);
       p->tw[j].y = (float)-std::sin(2.0 * M_PI * j / P);
     }
-    // per-pass twiddles of the register FFT: pass at sub-length Ns (radix R) holds
-    // exp(-2 pi i kb r / (Ns R)) at (Ns - 8) + kb (R - 1) + (r - 1)
-    // For P >= 256 the table of the 16-value FFT (fft16.cuh) follows it: the pass at
-    // sub-length Ns (radix R, first radix 16) at (P - 8) + (Ns - 16) + kb (R - 1) + (r - 1).
-    p->twp.assign(P >= 16 ? (P - 8) + (P >= 256 ? P - 16 : 0) : 1, float2{0.f, 0.f});
-    if (P >= 256) {
-      for (int Ns = 1; Ns < P;) {
-        const int rem = P / Ns;
-        const int R = (rem % 16 == 0) ? 16 : rem;
-        if (Ns > 1)
-          for (int kb = 0; kb < Ns; ++kb)
-            for (int r = 1; r < R; ++r) {
-              const double ang = -2.0 * M_PI * (double)kb * r / ((double)Ns * R);
-              p->twp[(P - 8) + (Ns - 16) + kb * (R - 1) + (r - 1)] =
-                  float2{(float)std::cos(ang), (float)std::sin(ang)};
-            }
-        Ns *= R;
-      }
-    }
-    if (P >= 16) {
-      for (int Ns = 1; Ns < P;) {
-        const int rem = P / Ns;
-        const int R = (rem % 8 == 0) ? 8 : rem;
-        if (Ns > 1)
-          for (int kb = 0; kb < Ns; ++kb)
-            for (int r = 1; r < R; ++r) {
-              const double ang = -2.0 * M_PI * (double)kb * r / ((double)Ns * R);
-              p->twp[(Ns - 8) + kb * (R - 1) + (r - 1)] = float2{(float)std::cos(ang), (float)std::sin(ang)};
-            }
-        Ns *= R;
-      }
-    }
+    p->twp = fft_twiddles(P);
   } catch (const std::bad_alloc&) {
     delete p;
     return fail(RECON_E_NO_MEMORY, "recon_plan: out of host memory");
@@ -398,6 +421,7 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
     lc.n_bins = (int)(r / lc.bin_width) + 1;
     lc.inv_half_p = 2.0f / (float)P;
     lc.noise_floor = (float)(o.nsr * o.nsr * (double)p->nu * (double)p->nv);
+    lc.eps_scale = (training || !(o.mlp_views > 1.0)) ? 1.0f : (float)(1.0 / o.mlp_views);
     if (o.filter == RECON_FILTER_MLP) {
       try {
         p->theta.assign(recon::kMlpParams, 0.f);
@@ -452,6 +476,41 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   cb.staged = o.bp_kernel == RECON_BP_STAGED;
   cb.layer_linear = o.layer_interp == RECON_LAYER_LINEAR;
 
+  {  // the 3D-Fourier forms: padded grid, per-axis twiddles, per-view gridding constants
+    p->uniform_R = true;
+    for (int n = 1; n < D; ++n)
+      if (defocus[n] != defocus[0]) p->uniform_R = false;
+    p->R0 = D > 0 ? defocus[0] : 0.0;
+    const int nn[3] = {p->nx, p->ny, p->nz};
+    p->f3_ok = true;
+    for (int a = 0; a < 3; ++a) {
+      int q = 1;
+      while (q < 2 * nn[a]) q *= 2;
+      if (nn[a] < 1 || q > 2048) p->f3_ok = false;
+      p->f3.P3[a] = q;
+      p->f3.n[a] = nn[a];
+      p->f3.off[a] = (q - nn[a]) / 2;
+      p->f3.scale[a] = (float)((double)q / P);
+    }
+    p->f3.lam = lambda;
+    p->f3.delta = delta;
+    if (p->f3_ok) {
+      try {
+        for (int a = 0; a < 3; ++a) p->tw3[a] = fft_twiddles(p->f3.P3[a]);
+        p->gdirs.resize(D > 0 ? D : 1);
+        for (int n = 0; n < D; ++n) {
+          const double* Rr = geom->rot + 9 * (size_t)n;
+          recon::GridDir& g = p->gdirs[n];
+          for (int q = 0; q < 9; ++q) g.r[q] = (float)Rr[q];
+          g.qz_coef = (float)(lambda / (2.0 * P * delta));
+          g.uR = half_turns_fixed(lambda * defocus[n] / ((double)P * delta * (double)P * delta));
+        }
+      } catch (const std::bad_alloc&) {
+        delete p;
+        return fail(RECON_E_NO_MEMORY, "recon_plan: out of host memory");
+      }
+    }
+  }
   const size_t elem = ca.stack_bf16 ? 4 : 8;  // one tap pair
   p->stack_dir_bytes = (size_t)nz_layers * ca.layer_elems * elem;
   // S and T of one direction (the stage-A intermediates)
@@ -502,7 +561,7 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   p->off_dirs = off;
   off = align256(off + sizeof(recon::DirParams) * (size_t)(D > 0 ? D : 1));
   p->off_uA = off;
-  off = align256(off + sizeof(uint64_t) * (size_t)(D > 0 ? D : 1) * nz_layers);
+  off = align256(off + sizeof(uint64_t) * (p->uA.size() > 0 ? p->uA.size() : (size_t)nz_layers + 1));
   p->off_ramp = off;
   off = align256(off + sizeof(float) * p->half);
   p->off_tw = off;
@@ -839,6 +898,234 @@ int recon_profile_read(recon_plan_t p, double* ms, int* launches) {
   return RECON_OK;
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------------ 3D-Fourier forms
+namespace {
+
+size_t grid3_cells(recon_plan_t p) { return (size_t)p->f3.P3[0] * p->f3.P3[1] * p->f3.P3[2]; }
+
+struct SwapLayout {
+  size_t vc, vs, Z, work, tw[3], total;
+};
+
+SwapLayout swap_layout(recon_plan_t p) {
+  SwapLayout L;
+  const size_t nvox = (size_t)p->nx * p->ny * p->nz;
+  size_t off = align256(p->ws_bytes);
+  L.vc = off;
+  off = align256(off + nvox * sizeof(float));
+  L.vs = off;
+  off = align256(off + nvox * sizeof(float));
+  L.Z = off;
+  off = align256(off + grid3_cells(p) * sizeof(float2));
+  L.work = off;
+  off = align256(off + grid3_cells(p) * sizeof(float2));
+  for (int a = 0; a < 3; ++a) {
+    L.tw[a] = off;
+    off = align256(off + p->tw3[a].size() * sizeof(float2));
+  }
+  L.total = off;
+  return L;
+}
+
+struct GridLayout {
+  size_t Srows, G, dirs, acc, raw, S, stats, tw[3], total;
+  int sub;
+};
+
+GridLayout grid_layout(recon_plan_t p) {
+  GridLayout L;
+  const size_t per_dir = (size_t)p->half * p->P * sizeof(float2) + (size_t)p->nv * p->half * sizeof(float2);
+  L.sub = (int)std::max<size_t>(1, std::min<size_t>((size_t)(p->D > 0 ? p->D : 1), ((size_t)1 << 30) / per_dir));
+  size_t off = p->table_bytes;
+  L.Srows = off;
+  off = align256(off + (size_t)L.sub * p->nv * p->half * sizeof(float2));
+  L.G = off;
+  off = align256(off + (size_t)L.sub * p->half * p->P * sizeof(float2));
+  L.dirs = off;
+  off = align256(off + p->gdirs.size() * sizeof(recon::GridDir));
+  L.acc = off;
+  off = align256(off + grid3_cells(p) * sizeof(float2));
+  L.raw = off;
+  off = align256(off + grid3_cells(p) * sizeof(float2));
+  L.S = off;
+  off = align256(off + grid3_cells(p) * sizeof(float));
+  L.stats = off;
+  off = align256(off + 2 * sizeof(double));
+  for (int a = 0; a < 3; ++a) {
+    L.tw[a] = off;
+    off = align256(off + p->tw3[a].size() * sizeof(float2));
+  }
+  L.total = off;
+  return L;
+}
+
+int f3_check(recon_plan_t p, const char* who) {
+  if (!p) return fail(RECON_E_INVALID_ARG, std::string(who) + ": null plan");
+  if (!p->f3_ok)
+    return fail(RECON_E_UNSUPPORTED_SIZE,
+                std::string(who) + ": the 3D-Fourier forms need every grid side <= 1024 (padded grid <= 2048)");
+  if (p->P < 16) return fail(RECON_E_UNSUPPORTED_SIZE, std::string(who) + ": images of more than 8 pixels needed");
+  return RECON_OK;
+}
+
+int upload_tw3(recon_plan_t p, char* b, const size_t off[3], float2* dev[3], cudaStream_t s) {
+  for (int a = 0; a < 3; ++a) {
+    dev[a] = (float2*)(b + off[a]);
+    const cudaError_t e =
+        cudaMemcpyAsync(dev[a], p->tw3[a].data(), sizeof(float2) * p->tw3[a].size(), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "upload of the 3D FFT twiddles");
+  }
+  return RECON_OK;
+}
+
+// the twiddle table of one axis as the line FFT of that length reads it (fft3.cu)
+const float2* axis_tw(recon_plan_t p, float2* dev, int a) {
+  return p->f3.P3[a] >= 1024 ? dev + (p->f3.P3[a] - 8) : dev;
+}
+
+}  // namespace
+
+extern "C" {
+
+int recon_swap_workspace_size(recon_plan_t p, size_t* bytes) {
+  int rc = f3_check(p, "recon_swap_workspace_size");
+  if (rc) return rc;
+  if (!bytes) return fail(RECON_E_INVALID_ARG, "recon_swap_workspace_size: null bytes");
+  *bytes = swap_layout(p).total;
+  return RECON_OK;
+}
+
+int recon_swap_ct(recon_plan_t p, const float* images, void* workspace, size_t ws_bytes, void* stream) {
+  int rc = f3_check(p, "recon_swap_ct");
+  if (rc) return rc;
+  if (p->opt.filter != RECON_FILTER_PAIR)
+    return fail(RECON_E_INVALID_ARG, "recon_swap_ct: the plan must use RECON_FILTER_PAIR (its depth tables)");
+  if (!p->uniform_R) return fail(RECON_E_INVALID_ARG, "recon_swap_ct: Eq. 12 needs one defocus for every view");
+  if (p->D > 0 && !images) return fail(RECON_E_INVALID_ARG, "recon_swap_ct: null images");
+  const SwapLayout L = swap_layout(p);
+  if (!workspace || ((uintptr_t)workspace & 255) != 0 || ws_bytes < L.total)
+    return fail(RECON_E_WORKSPACE, "recon_swap_ct: workspace too small or misaligned (needs " +
+                                       std::to_string(L.total) + " bytes)");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* b = (char*)workspace;
+  const recon::Workspace w = carve(p, workspace);
+  rc = upload_tables(p, w, s);
+  if (rc) return rc;
+  float2* tw[3];
+  rc = upload_tw3(p, b, L.tw, tw, s);
+  if (rc) return rc;
+  float* vc = (float*)(b + L.vc);
+  float* vs = (float*)(b + L.vs);
+  const size_t nvox = (size_t)p->nx * p->ny * p->nz;
+  for (int mode = 1; mode <= 2; ++mode) {  // cos, then sin of the layer's depth phase, no CTF
+    float* vol = mode == 1 ? vc : vs;
+    recon::StageAConst ca = p->ca;
+    ca.pair_mode = mode;
+    ca.pref = 1.0f;
+    if (p->D == 0) {
+      const cudaError_t e = cudaMemsetAsync(vol, 0, nvox * sizeof(float), s);
+      if (e != cudaSuccess) return cuda_fail(e, "recon_swap_ct: clearing");
+    }
+    for (int bk = 0; bk < p->n_blocks; ++bk) {
+      const int d0 = bk * p->db;
+      const int cnt = (p->D - d0) < p->db ? (p->D - d0) : p->db;
+      cudaError_t e = recon::launch_stage_a(ca, w, images, d0, cnt, s);
+      if (e != cudaSuccess) return cuda_fail(e, "recon_swap_ct: stage A launch");
+      e = recon::launch_backproject(p->cb, w.dirs, w.stack, d0, cnt, vol, bk > 0, s);
+      if (e != cudaSuccess) return cuda_fail(e, "recon_swap_ct: backprojection launch");
+    }
+  }
+  float2* Z = (float2*)(b + L.Z);
+  cudaError_t e = recon::launch_swap_pack(vc, vs, Z, p->f3, s);
+  const float2* twa[3] = {axis_tw(p, tw[0], 0), axis_tw(p, tw[1], 1), axis_tw(p, tw[2], 2)};
+  if (e == cudaSuccess) e = recon::launch_fft3(Z, p->f3.P3, twa, false, s);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_swap_ct: 3D transform");
+  return RECON_OK;
+}
+
+int recon_swap_phase(recon_plan_t p, double sigma, double eps, float* volume, void* workspace, size_t ws_bytes,
+                     void* stream) {
+  int rc = f3_check(p, "recon_swap_phase");
+  if (rc) return rc;
+  if (!(eps > 0.0) || !std::isfinite(eps) || !std::isfinite(sigma))
+    return fail(RECON_E_INVALID_ARG, "recon_swap_phase: eps > 0 and a finite sigma needed");
+  if (!volume) return fail(RECON_E_INVALID_ARG, "recon_swap_phase: null volume");
+  const SwapLayout L = swap_layout(p);
+  if (!workspace || ((uintptr_t)workspace & 255) != 0 || ws_bytes < L.total)
+    return fail(RECON_E_WORKSPACE, "recon_swap_phase: workspace too small or misaligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* b = (char*)workspace;
+  float2* tw[3] = {(float2*)(b + L.tw[0]), (float2*)(b + L.tw[1]), (float2*)(b + L.tw[2])};
+  const float2* twa[3] = {axis_tw(p, tw[0], 0), axis_tw(p, tw[1], 1), axis_tw(p, tw[2], 2)};
+  float2* work = (float2*)(b + L.work);
+  cudaError_t e = recon::launch_swap_phase((const float2*)(b + L.Z), work, p->f3, p->R0, sigma, eps, p->opt.cs, s);
+  if (e == cudaSuccess) e = recon::launch_fft3(work, p->f3.P3, twa, true, s);
+  if (e == cudaSuccess) e = recon::launch_crop_real(work, volume, p->f3, s);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_swap_phase");
+  return RECON_OK;
+}
+
+int recon_grid_workspace_size(recon_plan_t p, size_t* bytes) {
+  int rc = f3_check(p, "recon_grid_workspace_size");
+  if (rc) return rc;
+  if (!bytes) return fail(RECON_E_INVALID_ARG, "recon_grid_workspace_size: null bytes");
+  *bytes = grid_layout(p).total;
+  return RECON_OK;
+}
+
+int recon_grid_run(recon_plan_t p, const float* images, float* volume, double nsr, void* workspace, size_t ws_bytes,
+                   void* stream) {
+  int rc = f3_check(p, "recon_grid_run");
+  if (rc) return rc;
+  if (p->opt.filter != RECON_FILTER_TIKHONOV && p->opt.filter != RECON_FILTER_PAIR)
+    return fail(RECON_E_INVALID_ARG, "recon_grid_run: the plan's filter must carry eps (Tikhonov or pair)");
+  if (!(nsr >= 0.0) || !std::isfinite(nsr)) return fail(RECON_E_INVALID_ARG, "recon_grid_run: nsr must be >= 0");
+  if (!volume || (p->D > 0 && !images)) return fail(RECON_E_INVALID_ARG, "recon_grid_run: null images or volume");
+  const GridLayout L = grid_layout(p);
+  if (!workspace || ((uintptr_t)workspace & 255) != 0 || ws_bytes < L.total)
+    return fail(RECON_E_WORKSPACE, "recon_grid_run: workspace too small or misaligned (needs " +
+                                       std::to_string(L.total) + " bytes)");
+  cudaStream_t s = (cudaStream_t)stream;
+  char* b = (char*)workspace;
+  const recon::Workspace w = carve(p, workspace);
+  rc = upload_tables(p, w, s);
+  if (rc) return rc;
+  float2* tw[3];
+  rc = upload_tw3(p, b, L.tw, tw, s);
+  if (rc) return rc;
+  recon::GridDir* gd = (recon::GridDir*)(b + L.dirs);
+  float2* acc = (float2*)(b + L.acc);
+  float2* raw = (float2*)(b + L.raw);
+  float* S = (float*)(b + L.S);
+  const size_t cells = grid3_cells(p);
+  cudaError_t e = cudaMemcpyAsync(gd, p->gdirs.data(), sizeof(recon::GridDir) * p->gdirs.size(),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, cells * sizeof(float2), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(raw, 0, cells * sizeof(float2), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(S, 0, cells * sizeof(float), s);
+  float2* Srows = (float2*)(b + L.Srows);
+  float2* G = (float2*)(b + L.G);
+  for (int d0 = 0; d0 < p->D && e == cudaSuccess; d0 += L.sub) {
+    const int cnt = std::min(L.sub, p->D - d0);
+    e = recon::launch_rows_fwd(p->ca, Srows, w.twp, images, d0, cnt, s);
+    if (e == cudaSuccess) e = recon::launch_cols_forward(p->ca, p->lc, Srows, G, nullptr, w.twp, cnt, s);
+    if (e == cudaSuccess) e = recon::launch_grid_splat(G, gd, d0, cnt, p->ca, p->f3, acc, raw, S, nsr > 0.0, s);
+  }
+  const float nsr_m = (float)(nsr * std::sqrt((double)p->nu * p->nv));
+  if (e == cudaSuccess) e = recon::launch_grid_finish(acc, raw, S, (double*)(b + L.stats), p->f3, nsr_m, s);
+  const float2* twa[3] = {axis_tw(p, tw[0], 0), axis_tw(p, tw[1], 1), axis_tw(p, tw[2], 2)};
+  if (e == cudaSuccess) e = recon::launch_fft3(acc, p->f3.P3, twa, true, s);
+  if (e == cudaSuccess) e = recon::launch_crop_real(acc, volume, p->f3, s);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_grid_run");
+  return RECON_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
 int recon_sync(void* stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "recon_sync");
@@ -955,6 +1242,7 @@ int train_check(const recon_train_cfg* c) {
     return fail(RECON_E_INVALID_ARG, "recon_mlp_train: n_img, nz_layers >= 1 and steps >= 0 needed");
   if (!(c->nsr > 0.0) || !std::isfinite(c->nsr)) return fail(RECON_E_INVALID_ARG, "recon_mlp_train: nsr must be > 0");
   if (c->steps > 0 && !(c->lr > 0.f)) return fail(RECON_E_INVALID_ARG, "recon_mlp_train: lr must be > 0");
+  if (c->adam_step < 0) return fail(RECON_E_INVALID_ARG, "recon_mlp_train: adam_step must be >= 0");
   return RECON_OK;
 }
 
@@ -1047,9 +1335,19 @@ extern "C" int recon_mlp_train(const recon_train_cfg* cfg, float* weights, float
   const float* x2 = (const float*)(b + p->off_x2);
   cudaError_t e = cudaMemcpyAsync(theta, weights, sizeof(float) * recon::kMlpParams, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(pow, 0, sizeof(float) * (size_t)N * p->lc.n_bins, s);
-  // grad, m1 and m2 (separate 256-byte aligned arrays: the padding between them is not cleared)
-  for (float* a : {g, m1, m2})
-    if (e == cudaSuccess) e = cudaMemsetAsync(a, 0, sizeof(float) * recon::kMlpParams, s);
+  // grad, m1 and m2 (separate 256-byte aligned arrays: the padding between them is not cleared);
+  // the moments continue an earlier call's when the caller passes them
+  if (e == cudaSuccess) e = cudaMemsetAsync(g, 0, sizeof(float) * recon::kMlpParams, s);
+  if (cfg->adam_state) {
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(m1, cfg->adam_state, sizeof(float) * recon::kMlpParams, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(m2, cfg->adam_state + recon::kMlpParams, sizeof(float) * recon::kMlpParams,
+                          cudaMemcpyHostToDevice, s);
+  } else {
+    for (float* a : {m1, m2})
+      if (e == cudaSuccess) e = cudaMemsetAsync(a, 0, sizeof(float) * recon::kMlpParams, s);
+  }
   // spectra of the images (and their radial power) and of the layer targets
   if (e == cudaSuccess) e = recon::launch_rows_fwd(p->ca, S, w.twp, cfg->images, 0, N, s);
   if (e == cudaSuccess) e = recon::launch_cols_forward(p->ca, p->lc, S, G, pow, w.twp, N, s);
@@ -1064,12 +1362,18 @@ extern "C" int recon_mlp_train(const recon_train_cfg* cfg, float* weights, float
     if (e == cudaSuccess) e = recon::launch_eps_table(p->lc, pow, cnt, x2, theta, eps, acts, N, K, 0, s);
     if (e == cudaSuccess)
       e = recon::launch_train_step(p->ca, p->lc, G, T, eps, w.uA, acts, theta, theta, g, m1, m2, N, sums, deps,
-                                   cfg->steps > 0 ? it + 1 : 0, cfg->lr, loss + it, s);
+                                   cfg->steps > 0 ? cfg->adam_step + it + 1 : 0, cfg->lr, loss + it, s);
   }
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(loss_history, loss, sizeof(float) * iters, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess && cfg->steps > 0)
     e = cudaMemcpyAsync(weights, theta, sizeof(float) * recon::kMlpParams, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && cfg->steps > 0 && cfg->adam_state) {
+    e = cudaMemcpyAsync(cfg->adam_state, m1, sizeof(float) * recon::kMlpParams, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(cfg->adam_state + recon::kMlpParams, m2, sizeof(float) * recon::kMlpParams,
+                          cudaMemcpyDeviceToHost, s);
+  }
   if (e == cudaSuccess && cfg->steps == 0 && grad)
     e = cudaMemcpyAsync(grad, g, sizeof(float) * recon::kMlpParams, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

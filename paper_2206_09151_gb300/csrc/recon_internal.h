@@ -69,6 +69,8 @@ struct StageAConst {
   size_t layer_elems;   // pairs per layer, (nv + 2) * (nu + 1)
   DensityConst dens;
   int sub_block;        // directions per stage-A sub-block (S and T sized for it), 0 = whole block
+  int pair_mode;        // filter 3 only: 0 the opposite-pair bracket; 1 / 2 the depth factor
+                        // cos / sin of pi lambda z_k q^2 alone (the CT step of Eq. 12)
 };
 
 // Device pointers into the workspace.
@@ -158,6 +160,34 @@ void describe_backproject(const BackprojConst& c, const DirParams* dirs, const v
                           int dir_count, float* volume, int accumulate, BatchBp* out);
 cudaError_t launch_backproject_persistent(const BatchBp* desc_dev, int n_desc, unsigned long long total,
                                           unsigned long long* counter, size_t smem, cudaStream_t stream);
+
+// The 3D-Fourier forms (fft3.cu, fourier.cu): a zero-padded complex grid [P3z][P3y][P3x]
+// holding an n[0] x n[1] x n[2] volume at offset off (centred); scale[a] = P3[a] / P
+// converts a 2D frequency in units of 1 / (P delta) to bins of grid axis a.
+struct Fourier3Const {
+  int P3[3];
+  int n[3];
+  int off[3];
+  float scale[3];
+  double lam, delta;
+};
+// Per view of the gridding: rows of Rot_n (detector u, v, beam), lambda / (2 P delta) (the
+// paraboloid's depth per squared frequency bin), and the image-plane CTF phase constant.
+struct GridDir {
+  float r[9];
+  float qz_coef;
+  uint64_t uR;
+};
+cudaError_t launch_fft3(float2* data, const int P3[3], const float2* const tw[3], bool inverse, cudaStream_t s);
+cudaError_t launch_swap_pack(const float* vc, const float* vs, float2* grid, const Fourier3Const& f, cudaStream_t s);
+cudaError_t launch_swap_phase(const float2* Z, float2* out, const Fourier3Const& f, double R, double sigma, double eps,
+                              double cs, cudaStream_t s);
+cudaError_t launch_crop_real(const float2* grid, float* vol, const Fourier3Const& f, cudaStream_t s);
+cudaError_t launch_grid_splat(const float2* G, const GridDir* dirs, int dir_begin, int n_dirs, const StageAConst& c,
+                              const Fourier3Const& f, float2* acc, float2* raw, float* S, bool with_raw,
+                              cudaStream_t s);
+cudaError_t launch_grid_finish(float2* acc, const float2* raw, const float* S, double* stats, const Fourier3Const& f,
+                               float nsr_m, cudaStream_t s);
 
 // Whole-operator run with its workspace carved from `scratch` (tables first, then
 // the largest direction block that fits); used by recon_run_noalloc.

@@ -59,6 +59,11 @@ __device__ __forceinline__ float sin_half_turns(int32_t hi) {
   return __sinf((float)hi * 1.4629180792671596e-09f);  // hi * 2 pi / 2^32
 }
 
+// sin and cos of chi = pi t for t = hi * 2^-31 in [-1, 1) (hardware sine and cosine).
+__device__ __forceinline__ void sincos_half_turns(int32_t hi, float* sn, float* cs) {
+  __sincosf((float)hi * 1.4629180792671596e-09f, sn, cs);  // hi * 2 pi / 2^32
+}
+
 // The stack stores horizontal tap pairs: entry (row v + 1, column c) of a layer holds
 // (Y[v][c - 1], Y[v][c]) for c in [0, nu], zero outside the image, so a bilinear row is
 // one 8-byte (float32) or 4-byte (bfloat16) load.
@@ -112,7 +117,9 @@ __global__ void __launch_bounds__(kThreads) k_rows_fwd(const float* __restrict__
   }
 }
 
-// FILT: 0 ramp only (filter off), 1 Tikhonov eps, 2 learned eps table; DENS: density
+// FILT: 0 ramp only (filter off), 1 Tikhonov eps, 2 learned eps table, 3 the opposite-pair
+// form of Eq. 10 / 11 (real part of the complex bracket at the image plane carried to the
+// layer depth); DENS: density
 // weighting (any geometry) instead of the ramp.  Compile-time, so that each variant keeps
 // only the registers it uses.
 // 3 resident CTAs per SM (80 registers) measured faster than 4 (64 registers) at P = 512.
@@ -203,7 +210,21 @@ __global__ void __launch_bounds__(kThreads, 3) k_cols(const float2* __restrict__
       bin[s] = b < n_bins - 1 ? b : n_bins - 1;
     }
   }
-  const uint64_t* uAn = uA + (size_t)(dir_begin + n) * c.nz_layers;
+  // the opposite-pair filter (FILT 3) keeps one row more per direction: the image-plane
+  // phase constant after the Nz per-layer depth constants
+  const uint64_t* uAn = uA + (size_t)(dir_begin + n) * (c.nz_layers + (FILT == 3 ? 1 : 0));
+  float sp[FILT == 3 ? 8 : 1], cp[FILT == 3 ? 8 : 1];
+  if constexpr (FILT == 3) {  // image-plane sin chi / (sin^2 chi + eps), cos chi / (cos^2 chi + eps)
+    const uint64_t uR = uAn[c.nz_layers];
+    const uint32_t r_hi = (uint32_t)(uR >> 32), r_lo = (uint32_t)uR;
+#pragma unroll
+    for (int s = 0; s < 8; ++s) {
+      float sn, cs;
+      sincos_half_turns((int32_t)(r_hi * msq[s] + __umulhi(r_lo, msq[s]) + base_hi[s]), &sn, &cs);
+      sp[s] = c.pair_mode == 0 ? __fdividef(sn, fmaf(sn, sn, c.eps)) : (c.pair_mode == 1 ? 1.f : 0.f);
+      cp[s] = c.pair_mode == 0 ? __fdividef(cs, fmaf(cs, cs, c.eps)) : (c.pair_mode == 1 ? 0.f : -1.f);
+    }
+  }
   float2* Tn = T + (size_t)n * c.nz_layers * c.half * c.nv;
   // this CTA's layers: group blockIdx.z of gridDim.z equal groups
   const int lg = (c.nz_layers + gridDim.z - 1) / gridDim.z;
@@ -217,7 +238,11 @@ __global__ void __launch_bounds__(kThreads, 3) k_cols(const float2* __restrict__
 #pragma unroll
     for (int s = 0; s < 8; ++s) {
       float f = wgt[DENS ? s : 0];
-      if constexpr (FILT != 0) {
+      if constexpr (FILT == 3) {  // Re{bracket * exp(-i phi_k)}, phi_k = pi lambda z_k q^2
+        float sn, cs;
+        sincos_half_turns((int32_t)(a_hi * msq[s] + __umulhi(a_lo, msq[s])), &sn, &cs);
+        f *= fmaf(sp[s], cs, -cp[s] * sn);
+      } else if constexpr (FILT != 0) {
         const uint32_t hi = a_hi * msq[s] + __umulhi(a_lo, msq[s]) + base_hi[s];
         const float sn = sin_half_turns((int32_t)hi);
         float e;
@@ -348,7 +373,7 @@ __host__ __device__ constexpr int cols16_per_cta() {
 // or density weight, with the filter prefactor and 1/P^2); per layer: the CTF filter,
 // inverse FFT, store v < nv.
 template <int P, int FILT, bool DENS>
-__global__ void __launch_bounds__(kThreads16, 2) k_cols16(const float2* __restrict__ S, float2* __restrict__ T,
+__global__ void __launch_bounds__(kThreads16, FILT == 3 ? 1 : 2) k_cols16(const float2* __restrict__ S, float2* __restrict__ T,
                                                           const float2* __restrict__ twg,
                                                           const uint64_t* __restrict__ uA,
                                                           const float* __restrict__ ramp,
@@ -425,7 +450,19 @@ __global__ void __launch_bounds__(kThreads16, 2) k_cols16(const float2* __restri
       msq[s] = q2;
     }
   }
-  const uint64_t* uAn = uA + (size_t)(dir_begin + n) * c.nz_layers;
+  const uint64_t* uAn = uA + (size_t)(dir_begin + n) * (c.nz_layers + (FILT == 3 ? 1 : 0));
+  float sp[FILT == 3 ? 16 : 1], cp[FILT == 3 ? 16 : 1];
+  if constexpr (FILT == 3) {  // image-plane sin chi / (sin^2 chi + eps), cos chi / (cos^2 chi + eps)
+    const uint64_t uR = uAn[c.nz_layers];
+    const uint32_t r_hi = (uint32_t)(uR >> 32), r_lo = (uint32_t)uR;
+#pragma unroll
+    for (int s = 0; s < 16; ++s) {
+      float sn, cs;
+      sincos_half_turns((int32_t)(r_hi * msq[s] + __umulhi(r_lo, msq[s]) + base_hi[s]), &sn, &cs);
+      sp[s] = c.pair_mode == 0 ? __fdividef(sn, fmaf(sn, sn, c.eps)) : (c.pair_mode == 1 ? 1.f : 0.f);
+      cp[s] = c.pair_mode == 0 ? __fdividef(cs, fmaf(cs, cs, c.eps)) : (c.pair_mode == 1 ? 0.f : -1.f);
+    }
+  }
   float2* Tn = T + (size_t)n * c.nz_layers * c.half * c.nv;
   const int lg = (c.nz_layers + gridDim.z - 1) / gridDim.z;
   const int k_begin = blockIdx.z * lg;
@@ -437,7 +474,12 @@ __global__ void __launch_bounds__(kThreads16, 2) k_cols16(const float2* __restri
     float2 x[16];
 #pragma unroll
     for (int s = 0; s < 16; ++s) {
-      if constexpr (FILT != 0) {
+      if constexpr (FILT == 3) {  // Re{bracket * exp(-i phi_k)}, phi_k = pi lambda z_k q^2
+        float sn, cs;
+        sincos_half_turns((int32_t)(a_hi * msq[s] + __umulhi(a_lo, msq[s])), &sn, &cs);
+        const float f = fmaf(sp[s], cs, -cp[s] * sn);
+        x[s] = make_float2(xg[s].x * f, xg[s].y * f);
+      } else if constexpr (FILT != 0) {
         const uint32_t q2 = FILT == 2 ? (msq[s] & 0x3FFFFFu) : msq[s];
         const uint32_t hi = a_hi * q2 + __umulhi(a_lo, q2) + base_hi[s];
         const float sn = sin_half_turns((int32_t)hi);
@@ -658,7 +700,7 @@ __global__ void k_small_cols(const float2* __restrict__ S, float2* __restrict__ 
   for (int v = threadIdx.x; v < c.P; v += blockDim.x)
     G[bitrev(v, c.logP)] = v < c.nv ? Sn[(size_t)v * c.half + col] : make_float2(0.f, 0.f);
   fft_radix2<false>(G, c.P, c.logP, tw);
-  const uint64_t* uAn = uA + (size_t)(dir_begin + n) * c.nz_layers;
+  const uint64_t* uAn = uA + (size_t)(dir_begin + n) * (c.nz_layers + (c.filter == 3 ? 1 : 0));
   const int hP = c.P >> 1;
   for (int k = 0; k < c.nz_layers; ++k) {
     for (int m = threadIdx.x; m < c.P; m += blockDim.x) {
@@ -673,7 +715,14 @@ __global__ void k_small_cols(const float2* __restrict__ S, float2* __restrict__ 
           f = 0.5f * (f + density_weight(c.dens, dens, band_sum, dp.af, dp.bf, nyq_u ? -(float)col : (float)col,
                                          (nyq_v && !nyq_u) ? -(float)mv : (float)mv));
       }
-      if (c.filter) {
+      if (c.filter == 3) {  // opposite-pair filter: image-plane chi, depth phase of layer k
+        float sn, cs, sz, cz;
+        sincos_half_turns((int32_t)((uAn[c.nz_layers] * msq + c.uC * (msq * msq) - c.uW) >> 32), &sn, &cs);
+        sincos_half_turns((int32_t)((uAn[k] * msq) >> 32), &sz, &cz);
+        const float sp = c.pair_mode == 0 ? __fdividef(sn, fmaf(sn, sn, c.eps)) : (c.pair_mode == 1 ? 1.f : 0.f);
+        const float cp = c.pair_mode == 0 ? __fdividef(cs, fmaf(cs, cs, c.eps)) : (c.pair_mode == 1 ? 0.f : -1.f);
+        f *= c.pref * (sp * cz - cp * sz);
+      } else if (c.filter) {
         const float sn = sin_from_turns(uAn[k] * msq + c.uC * (msq * msq) - c.uW);
         float e = c.eps;
         if (c.filter == 2) {
@@ -776,7 +825,7 @@ cudaError_t launch_cols16(const StageAConst& c, const Workspace& ws, const float
   const int col_groups = (c.half + CB - 1) / CB;
   // set-up per group: the forward FFT (about one layer's work), and with the density
   // weighting about one more for the weights' trilinear lookups
-  const int lg = pick_layer_groups(col_groups * cnt, c.nz_layers, 2 * sms, DENS ? 2.2 : 1.2);
+  const int lg = pick_layer_groups(col_groups * cnt, c.nz_layers, (FILT == 3 ? 1 : 2) * sms, DENS ? 2.2 : 1.2);
   k_cols16<P, FILT, DENS><<<dim3(col_groups, cnt, lg), kThreads16, smem, stream>>>(
       ws.S, ws.T, twq, ws.uA, ws.ramp, ws.dirs, ws.dens, ws.band_sum, ws.eps, ws.n_bins, ws.bin_width, c, d0);
   return cudaGetLastError();
@@ -826,6 +875,8 @@ cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* i
       cudaError_t e;
       if (c.filter == 0) e = dens ? launch_cols16<P, 0, true>(c, ws, twq, d0, cnt, sms, stream)
                                   : launch_cols16<P, 0, false>(c, ws, twq, d0, cnt, sms, stream);
+      else if (c.filter == 3) e = dens ? launch_cols16<P, 3, true>(c, ws, twq, d0, cnt, sms, stream)
+                                       : launch_cols16<P, 3, false>(c, ws, twq, d0, cnt, sms, stream);
       else if (c.filter == 2) e = dens ? launch_cols16<P, 2, true>(c, ws, twq, d0, cnt, sms, stream)
                                        : launch_cols16<P, 2, false>(c, ws, twq, d0, cnt, sms, stream);
       else e = dens ? launch_cols16<P, 1, true>(c, ws, twq, d0, cnt, sms, stream)
@@ -852,6 +903,8 @@ cudaError_t launch_reg(const StageAConst& c, const Workspace& ws, const float* i
       if (dens) RECON_K_COLS(0, true); else RECON_K_COLS(0, false);
     } else if (c.filter == 2) {
       if (dens) RECON_K_COLS(2, true); else RECON_K_COLS(2, false);
+    } else if (c.filter == 3) {
+      if (dens) RECON_K_COLS(3, true); else RECON_K_COLS(3, false);
     } else {
       if (dens) RECON_K_COLS(1, true); else RECON_K_COLS(1, false);
     }

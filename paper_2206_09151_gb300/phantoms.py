@@ -315,6 +315,96 @@ def layer_projections(ph: Phantom, rot: np.ndarray, nu: int, nv: int, grid, nz_l
     return out
 
 
+def layer_projections_device(ph: Phantom, rot: np.ndarray, nu: int, nv: int, grid, nz_layers: int,
+                             delta: float, device="cuda") -> torch.Tensor:
+    """:func:`layer_projections` evaluated with torch on ``device`` (all primitives of a
+    direction splatted at once): float32 ``(D, Nz, nv, nu)`` true projections (metres) of
+    the parts of the phantom in each depth layer, a primitive assigned to the layer
+    holding its centre."""
+    nx, ny, nz = grid
+    D = rot.shape[0]
+    out = torch.zeros((D, nz_layers, nv, nu), dtype=torch.float32, device=device)
+    if ph.centre.shape[0] == 0:
+        return out
+    rad = int(math.ceil(float(ph.size.max()) * (1.0 if ph.kind == "ball" else 4.0))) + 1
+    offs = torch.arange(-rad, rad + 1, device=device, dtype=torch.float64)
+    size = torch.as_tensor(ph.size, device=device)[:, None, None]
+    amp = torch.as_tensor(ph.amp, device=device)[:, None, None]
+    for n in range(D):
+        d = rot[n, 2]
+        ext = abs(d[0]) * nx + abs(d[1]) * ny + abs(d[2]) * nz
+        c = ph.centre @ rot[n].T
+        layer = np.clip(np.floor((c[:, 2] + ext / 2) / (ext / nz_layers)), 0, nz_layers - 1).astype(np.int64)
+        cu = torch.as_tensor(c[:, 0] + (nu - 1) / 2.0, device=device)
+        cv = torch.as_tensor(c[:, 1] + (nv - 1) / 2.0, device=device)
+        iu = torch.floor(cu)[:, None, None] + offs[None, None, :]
+        iv = torch.floor(cv)[:, None, None] + offs[None, :, None]
+        rho2 = (iu - cu[:, None, None]) ** 2 + (iv - cv[:, None, None]) ** 2
+        if ph.kind == "ball":
+            val = 2.0 * amp * torch.sqrt(torch.clamp(size * size - rho2, min=0.0))
+        else:
+            val = amp * math.sqrt(2.0 * math.pi) * size * torch.exp(-rho2 / (2.0 * size * size))
+        iu_b, iv_b = iu.expand_as(val), iv.expand_as(val)
+        ok = (iu_b >= 0) & (iu_b < nu) & (iv_b >= 0) & (iv_b < nv)
+        lay = torch.as_tensor(layer, device=device)[:, None, None].expand_as(val)
+        idx = (lay * nv + iv_b.to(torch.int64)) * nu + iu_b.to(torch.int64)
+        acc = torch.zeros(nz_layers * nv * nu, dtype=torch.float64, device=device)
+        acc.index_add_(0, idx[ok], val[ok])
+        out[n] = (acc * delta).view(nz_layers, nv, nu).to(torch.float32)
+    return out
+
+
+def training_set(first: int, count: int, physics: str = "c3", n: int = 128, views: int = 4, nz_layers: int = 16,
+                 device="cuda", photons: float | None = None) -> dict:
+    """Seeded training data of the learned regulariser: ``count`` phantoms of n^3 voxels
+    (seeds first .. first + count - 1), alternately Gaussian pseudo-atoms and uniform balls,
+    each seen from ``views`` random directions, with their multislice images (Poisson
+    noise) and the true projections of each of Nz depth layers.
+
+    ``physics = "c3"``: 0.1 nm voxels, lambda 1.97 pm, R ~ U[0.5, 1.5] um, Cs 2.7 mm,
+    sigma 0.07, 100 e/px, pseudo-atoms of s = 0.1 nm at the density of the 512^3 scan,
+    random single-axis angles.  ``"c5"``: 0.05 nm voxels, R ~ U[0.75, 1.25] um, 50 e/px,
+    pseudo-atoms of s = 0.1 nm at the density of the 1024 x 1024 x 256 slab filling the box,
+    Haar-random directions within 60 deg of z.  Balls: 20 of radius U[2, 8] voxels with a
+    decrement giving 0.02-0.1 rad of peak phase.  ``photons`` overrides the dose per pixel."""
+    grid = (n, n, n)
+    dose = photons
+    if physics == "c3":
+        delta, photons, s_vox, blobs, region = 1e-10, 100.0, 1.0, int(round(160000 / 64 * (n / 128) ** 3)), "cylinder"
+        r_range = (0.5e-6, 1.5e-6)
+    elif physics == "c5":
+        delta, photons, s_vox, region = 5e-11, 50.0, 2.0, "box"
+        blobs = int(round(200000 * n ** 3 / (1024 * 1024 * 256)))
+        r_range = (0.75e-6, 1.25e-6)
+    else:
+        raise ValueError(physics)
+    if dose is not None:
+        photons = float(dose)
+    lam, sigma, cs = 1.97e-12, 0.07, 2.7e-3
+    amp = 0.01 * lam / (2 * math.pi * math.sqrt(2 * math.pi) * s_vox * delta)
+    ball_delta = (0.02 * lam / (2 * math.pi * 2 * 5 * delta), 0.1 * lam / (2 * math.pi * 2 * 5 * delta))
+    imgs, tgts, rots, Rs = [], [], [], []
+    for p in range(first, first + count):
+        rng = np.random.default_rng(50000 + p)
+        if p % 2 == 0:
+            phan = blob_phantom(grid, blobs, seed=60000 + p, s_vox=s_vox, amp_unit=amp, region=region)
+        else:
+            phan = ball_phantom(grid, 20, seed=60000 + p, delta_range=ball_delta)
+        if physics == "c3":
+            rot = np.stack([single_axis_rotations(1, start=float(a), span=0.0)[0]
+                            for a in rng.uniform(0, math.pi, views)])
+        else:
+            rot = cone_rotations(views, 60.0, seed=70000 + p)
+        R = rng.uniform(r_range[0], r_range[1], views)
+        imgs.append(multislice_images(phan, rot, n, n, delta, lam, R, sigma, cs=cs, photons=photons,
+                                      seed=80000 + p, device=device, dtype=torch.float32))
+        tgts.append(layer_projections_device(phan, rot, n, n, grid, nz_layers, delta, device))
+        rots.append(rot)
+        Rs.append(R)
+    return dict(images=torch.cat(imgs), targets=torch.cat(tgts), rot=np.concatenate(rots), defocus=np.concatenate(Rs),
+                grid=grid, nz_layers=nz_layers, lam=lam, delta=delta, sigma=sigma, cs=cs, nsr=photons ** -0.5)
+
+
 # ----------------------------------------------------------------------------- workloads
 def config_workload(name: str, *, scale_dirs: int | None = None):
     """Parameters of the named synthetic workloads (all seeded).

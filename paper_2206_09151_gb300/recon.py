@@ -9,7 +9,8 @@ import torch
 
 from . import _abi
 
-_FILTERS = {"off": _abi.RECON_FILTER_OFF, "tikhonov": _abi.RECON_FILTER_TIKHONOV, "mlp": _abi.RECON_FILTER_MLP}
+_FILTERS = {"off": _abi.RECON_FILTER_OFF, "tikhonov": _abi.RECON_FILTER_TIKHONOV, "mlp": _abi.RECON_FILTER_MLP,
+            "pair": _abi.RECON_FILTER_PAIR}
 _INPUTS = {"intensity": _abi.RECON_INPUT_INTENSITY, "contrast": _abi.RECON_INPUT_CONTRAST}
 _STACKS = {"f32": _abi.RECON_STACK_F32, "bf16": _abi.RECON_STACK_BF16}
 _RAMPS = {"single_axis": _abi.RECON_RAMP_SINGLE_AXIS, "density": _abi.RECON_RAMP_DENSITY}
@@ -30,7 +31,7 @@ class Reconstructor:
                  input_mode: str = "intensity", stack_dtype: str = "f32", accumulate: bool = False,
                  dir_block: int = 0, ramp: str = "single_axis", mlp_weights=None, nsr: float = 0.0,
                  stage_block: int = 0, bp_kernel: str = "auto", check_finite: bool = False,
-                 layer_interp: str = "nearest", device=None, allocate: bool = True):
+                 layer_interp: str = "nearest", mlp_views: float = 0.0, device=None, allocate: bool = True):
         o = _abi.recon_default_options()
         o.sigma, o.eps, o.cs = float(sigma), float(eps), float(cs)
         o.filter, o.input_mode, o.stack_dtype = _FILTERS[filter], _INPUTS[input_mode], _STACKS[stack_dtype]
@@ -41,6 +42,7 @@ class Reconstructor:
         o.bp_kernel = _BP_KERNELS[bp_kernel]
         o.check_finite = int(bool(check_finite))
         o.layer_interp = _LAYER_INTERP[layer_interp]
+        o.mlp_views = float(mlp_views)
         self._weights = None
         if mlp_weights is not None:
             self._weights = np.ascontiguousarray(mlp_weights, dtype=np.float32)
@@ -111,6 +113,37 @@ class Reconstructor:
                                int(bool(accumulate)), self.workspace.data_ptr(), self.ws_bytes, self._stream(stream))
         return volume
 
+    def swap_ct(self, images: torch.Tensor, stream=None) -> torch.Tensor:
+        """``recon_swap_ct`` (Eq. 12's CT step) into a workspace of its own, which is returned
+        and which :meth:`swap_phase` takes."""
+        self._check_images(images)
+        n = _abi.recon_swap_workspace_size(self.plan)
+        ws = torch.empty(n, dtype=torch.uint8, device=self.device)
+        _abi.recon_swap_ct(self.plan, images.data_ptr(), ws.data_ptr(), n, self._stream(stream))
+        return ws
+
+    def swap_phase(self, ws: torch.Tensor, sigma: float, eps: float, volume: torch.Tensor | None = None,
+                   stream=None) -> torch.Tensor:
+        """``recon_swap_phase``: Eq. 12's 3D CTF inversion with (sigma, eps) of the spectrum
+        that :meth:`swap_ct` left in ``ws``."""
+        if volume is None:
+            volume = self.new_volume()
+        _abi.recon_swap_phase(self.plan, float(sigma), float(eps), volume.data_ptr(), ws.data_ptr(), ws.numel(),
+                              self._stream(stream))
+        return volume
+
+    def grid_run(self, images: torch.Tensor, nsr: float = 0.0, volume: torch.Tensor | None = None,
+                 stream=None) -> torch.Tensor:
+        """``recon_grid_run``: the Fourier-gridding UTR (with the NSR noise filter when nsr > 0)."""
+        self._check_images(images)
+        if volume is None:
+            volume = self.new_volume()
+        n = _abi.recon_grid_workspace_size(self.plan)
+        ws = torch.empty(n, dtype=torch.uint8, device=self.device)
+        _abi.recon_grid_run(self.plan, images.data_ptr(), volume.data_ptr(), float(nsr), ws.data_ptr(), n,
+                            self._stream(stream))
+        return volume
+
     def close(self):
         if getattr(self, "plan", None) is not None:
             _abi.recon_destroy(self.plan)
@@ -125,15 +158,19 @@ class Reconstructor:
 
 def train_mlp(weights, images: torch.Tensor, targets: torch.Tensor, rot, defocus, grid, *, nz_layers: int,
               lam: float, delta: float, sigma: float, nsr: float, cs: float = 0.0, input_mode: str = "intensity",
-              steps: int = 200, lr: float = 1e-3, want_grad: bool = False, stream=None):
+              steps: int = 200, lr: float = 1e-3, want_grad: bool = False, stream=None, adam_state=None,
+              adam_step: int = 0):
     """``recon_mlp_train``: fits the regulariser network on the GPU.  ``images`` (N, nv, nu)
     and ``targets`` (N, Nz, nv, nu) are contiguous float32 CUDA tensors.  Returns
-    (weights, loss history, gradient at the input weights when steps == 0 and want_grad)."""
+    (weights, loss history, gradient at the input weights when steps == 0 and want_grad).
+    ``adam_state`` (float32 numpy [2 RECON_MLP_PARAMS], updated in place) and ``adam_step``
+    continue one Adam optimisation over mini-batches passed in successive calls."""
     N, nv, nu = images.shape
     if tuple(targets.shape) != (N, nz_layers, nv, nu):
         raise ValueError("targets must be (N, nz_layers, nv, nu)")
     cfg, keep = _abi.make_train_cfg(rot, defocus, nu, nv, nz_layers, grid, lam, delta, sigma, cs, nsr,
-                                    _INPUTS[input_mode], images.data_ptr(), targets.data_ptr(), steps, lr)
+                                    _INPUTS[input_mode], images.data_ptr(), targets.data_ptr(), steps, lr,
+                                    adam_state, adam_step)
     ws_bytes = _abi.recon_mlp_train_workspace_size(cfg)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=images.device)
     s = stream if stream is not None else torch.cuda.current_stream()

@@ -225,3 +225,31 @@ def test_layer_interp_is_validated_and_nz_zero_follows_the_depth_of_field(lib):
     assert _abi.recon_plan_layers(p) == _abi.recon_layers_for_dof(rot, (64, 64, 64), 1e-10, 1e-9) == 19
     assert _abi.recon_plan_warning(p) == ""
     _abi.recon_destroy(p)
+
+
+def test_fourier_forms_validate_on_the_host(lib):
+    """Eq. 12 needs the pair filter's depth tables and one defocus; both 3D-Fourier forms
+    refuse grids whose padded side would exceed 2048; the workspace sizes are queries."""
+    rot = ph.single_axis_rotations(12, span=2 * np.pi)
+    o = _abi.recon_default_options()
+    o.filter = _abi.RECON_FILTER_PAIR
+    p = _plan(rot=rot, defocus=np.full(12, 1e-7), opts=o)
+    P3 = (64, 64, 32)  # grid (30, 20, 10) padded to the next power of two >= 2 n
+    ws = _abi.recon_swap_workspace_size(p)
+    assert ws >= 2 * 8 * P3[0] * P3[1] * P3[2]
+    assert _abi.recon_grid_workspace_size(p) >= 3 * 8 * P3[0] * P3[1] * P3[2]
+    assert lib.recon_swap_ct(p, 16, None, 0, None) == _abi.RECON_E_WORKSPACE
+    assert lib.recon_swap_phase(p, 0.1, 0.0, 16, 256, ws, None) == _abi.RECON_E_INVALID_ARG  # eps = 0
+    assert lib.recon_grid_run(p, 16, 16, -1.0, 256, 1 << 40, None) == _abi.RECON_E_INVALID_ARG  # nsr < 0
+    _abi.recon_destroy(p)
+    p = _plan(rot=rot, defocus=np.linspace(1e-7, 2e-7, 12), opts=o)  # several defocus values
+    assert lib.recon_swap_ct(p, 16, 256, 1 << 40, None) == _abi.RECON_E_INVALID_ARG
+    _abi.recon_destroy(p)
+    p = _plan(rot=rot, defocus=np.full(12, 1e-7))  # Tikhonov plan: no depth tables for Eq. 12
+    assert lib.recon_swap_ct(p, 16, 256, 1 << 40, None) == _abi.RECON_E_INVALID_ARG
+    _abi.recon_destroy(p)
+    p = _plan(rot=rot, defocus=np.full(12, 1e-7), grid=(1100, 8, 8))
+    with pytest.raises(_abi.ReconError) as e:
+        _abi.recon_grid_workspace_size(p)
+    assert e.value.code == _abi.RECON_E_UNSUPPORTED_SIZE
+    _abi.recon_destroy(p)

@@ -49,6 +49,11 @@ STAGE_A_CASES = [
     (512, 400, 3, "tikhonov", "intensity", 2.7e-3, 0.07, 0.1, 1.97e-12, 1e-10, 1e-6),   # P = 1024, ragged rows
     (1000, 777, 3, "off", "contrast", 0.0, 0.0, 0.1, 1.97e-12, 5e-11, 1e-6),           # P = 2048, ragged both
     (1, 1, 1, "tikhonov", "intensity", 0.0, 0.1, 0.1, 1e-10, 1e-9, 1e-7),
+    # the opposite-pair filter (Eq. 10 / 11): radix-2 path, 8-value and 16-value FFTs
+    (3, 4, 2, "pair", "intensity", 0.0, 0.1, 0.05, 1e-10, 1e-9, 1e-7),
+    (64, 50, 6, "pair", "intensity", 2e-6, 0.2, 1e-2, 1e-10, 1e-9, 60e-9),
+    (256, 256, 4, "pair", "contrast", 2.7e-3, 0.07, 0.1, 1.97e-12, 1e-10, 1e-6),
+    (700, 1000, 3, "pair", "intensity", 2.7e-3, 0.07, 0.1, 1.97e-12, 5e-11, 1e-6),
 ]
 
 
@@ -71,7 +76,8 @@ def test_stage_a_layer_stack_matches_oracle(case):
     zc = O.layer_centres(rot, grid, nzl, delta)
     for n in range(D):
         ref = O.layer_stack(img[n], delta=delta, lam=lam, r_n=defocus[n], z_layers=zc[n], n_dir=D, sigma=sigma,
-                            eps=eps, cs=cs, filt=O.FILTER_TIKHONOV if filt == "tikhonov" else O.FILTER_OFF,
+                            eps=eps, cs=cs, filt={"tikhonov": O.FILTER_TIKHONOV, "pair": O.FILTER_PAIR,
+                                                  "off": O.FILTER_OFF}[filt],
                             input_mode=O.INPUT_INTENSITY if inp == "intensity" else O.INPUT_CONTRAST)
         got = st[n, :, 1:-1, 1:, 0]  # pair (Y[u], Y[u+1]) at column u + 1
         for k in range(nzl):
@@ -194,6 +200,23 @@ def test_small_workload_layer_blend_matches_oracle(small):
     got = _gpu_recon(cfg, img, layer_interp="linear")
     assert rel_l2(got, ref) <= TOL_F32, rel_l2(got, ref)
     got16 = _gpu_recon(cfg, img, layer_interp="linear", stack_dtype="bf16")
+    assert rel_l2(got16, ref) <= TOL_BF16, rel_l2(got16, ref)
+
+
+def test_pair_filter_whole_run_over_360_degrees_matches_oracle():
+    """The opposite-pair filter on a 360-degree single-axis scan (every view has its
+    opposite): 64^3, 60 views, Nz 8, the small workload's physics, against the oracle."""
+    cfg = ph.config_workload("small", scale_dirs=60)
+    cfg["rot"] = ph.single_axis_rotations(60, span=2 * math.pi)
+    phan = ph.make_phantom(cfg)
+    img = ph.multislice_images(phan, cfg["rot"], cfg["nu"], cfg["nv"], cfg["delta"], cfg["lam"], cfg["defocus"],
+                               cfg["sigma"], photons=cfg["photons"], seed=cfg["seed"]).numpy()
+    ref = O.recon(img, cfg["rot"], lam=cfg["lam"], delta=cfg["delta"], defocus=cfg["defocus"],
+                  nz_layers=cfg["nz_layers"], grid=cfg["grid"], sigma=cfg["sigma"], eps=cfg["eps"], cs=cfg["cs"],
+                  filt=O.FILTER_PAIR)
+    got = _gpu_recon(cfg, img, filter="pair")
+    assert rel_l2(got, ref) <= TOL_F32, rel_l2(got, ref)
+    got16 = _gpu_recon(cfg, img, filter="pair", stack_dtype="bf16", layer_interp="nearest")
     assert rel_l2(got16, ref) <= TOL_BF16, rel_l2(got16, ref)
 
 
