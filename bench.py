@@ -576,10 +576,14 @@ def run_batch(args):
     recons = [Reconstructor(c["rot"], c["nu"], c["nv"], c["grid"], lam=c["lam"], delta=c["delta"],
                             defocus=c["defocus"], nz_layers=c["nz_layers"], sigma=c["sigma"], eps=c["eps"],
                             cs=c["cs"], stack_dtype=args.stack, device=dev, allocate=False) for c in cfgs]
-    b = Batch(recons, dir_block=args.dir_block)
+    tuned = None
+    if args.dir_block <= 0:  # the round size from the autotuner (timed before the measured region)
+        from paper_2206_09151_gb300.autotune import tune_batch_round
+        tuned = tune_batch_round(recons, images, candidates=(16, 32, 64), repeats=1)
+    dbb = args.dir_block if args.dir_block > 0 else tuned["dir_block"]
+    b = Batch(recons, dir_block=dbb)
     vols = [r.new_volume() for r in recons]
     U = sum(int(np.prod(c["grid"])) * c["n_dir"] for c in cfgs)
-    dbb = args.dir_block if args.dir_block > 0 else 32
     rounds = max((c["n_dir"] + dbb - 1) // dbb for c in cfgs)
     # kernels per replay: per round, stage A (3 launches) for every tomogram still active,
     # and one persistent backprojection
@@ -634,6 +638,7 @@ def run_batch(args):
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.stack, "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT["batch"], "tomograms": len(cfgs), "round_directions": dbb,
+                       "round_tuning_ms": tuned["ms"] if tuned else None,
                        "rounds": rounds, "updates_per_step": U, "stack": args.stack,
                        "l2": "flushed between timed steps (256 MiB write outside the timed span)",
                        "parallelism": f"replicas x{world}"},

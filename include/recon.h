@@ -136,6 +136,9 @@ typedef struct {
                        RECON_E_NONFINITE without touching the volume if it finds any; 0: no
                        scan (a NaN then propagates into the voxels it reaches)             */
   int layer_interp; /* RECON_LAYER_*: nearest layer, or the blend of the two bracketing ones */
+  int bp_warp;      /* general backprojection: a warp's patch of voxel columns is bp_warp (x)
+                       by 32 / bp_warp (y) of its 32 x 8 tile; 8, 16 or 32, 0 = 8 (measured
+                       fastest on the slab; the autotuner can time the others)              */
   double mlp_views; /* RECON_FILTER_MLP: views averaged per voxel (a full scan's D); the
                        network's eps, a per-view noise-to-signal power (Wiener), is divided by
                        it, since the reconstruction averages that many independent views;

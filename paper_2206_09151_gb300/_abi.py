@@ -54,7 +54,7 @@ class ReconOptions(ctypes.Structure):
                 ("ramp_mode", ctypes.c_int), ("accumulate", ctypes.c_int), ("dir_block", ctypes.c_int),
                 ("mlp_weights", ctypes.POINTER(ctypes.c_float)), ("nsr", ctypes.c_double),
                 ("stage_block", ctypes.c_int), ("bp_kernel", ctypes.c_int), ("check_finite", ctypes.c_int),
-                ("layer_interp", ctypes.c_int), ("mlp_views", ctypes.c_double)]
+                ("layer_interp", ctypes.c_int), ("bp_warp", ctypes.c_int), ("mlp_views", ctypes.c_double)]
 
 
 class ReconTrainCfg(ctypes.Structure):

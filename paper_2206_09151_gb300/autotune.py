@@ -2,10 +2,13 @@
 
 The kernels' voxel tiles and FFT groups are fixed at compile time for sm_103a; what
 varies per problem is how many directions share one block of layer stacks (``dir_block``
-of a run: a larger block means fewer volume read-modify-writes but a larger workspace)
-and how many directions a batch round holds.  ``tune_dir_block`` times ``recon_run`` for
-each candidate with CUDA events (after a warm-up run) and returns the fastest; results are
-cached per problem shape in a JSON file when ``cache`` is given."""
+of a run: a larger block means fewer volume read-modify-writes but a larger workspace),
+how a warp of the general backprojection covers its tile's voxel columns (``bp_warp``:
+8 x 4, 16 x 2 or 32 x 1, which sets how many detector rows and cache lines one gather
+touches for the scan's view orientations), and how many directions a batch round holds.
+Each ``tune_*`` times ``recon_run`` (or a batch run) for every candidate with CUDA events
+after a warm-up run and returns the fastest; ``tune_dir_block`` and ``tune_bp_warp`` cache
+their result per problem shape in a JSON file when ``cache`` is given."""
 from __future__ import annotations
 
 import json
@@ -66,6 +69,35 @@ def tune_dir_block(rot, nu: int, nv: int, grid, images: torch.Tensor, *, nz_laye
         torch.cuda.empty_cache()
     best = min(timings, key=timings.get)
     out = {"dir_block": best, "ms": {str(k): v for k, v in timings.items()}}
+    if cache:
+        table = json.load(open(cache)) if os.path.exists(cache) else {}
+        table[key] = out
+        with open(cache, "w") as f:
+            json.dump(table, f, indent=1)
+    return out
+
+
+def tune_bp_warp(rot, nu: int, nv: int, grid, images: torch.Tensor, *, nz_layers: int, candidates=(8, 16, 32),
+                 repeats: int = 3, cache: str | None = None, **plan_kw) -> dict:
+    """Fastest warp patch of the general backprojection: {"bp_warp": best, "ms": {...}}.
+    The shapes give the same volume bit for bit (they only move voxels between threads)."""
+    key = _key(rot, nu, nv, grid, nz_layers, plan_kw) + "|bp_warp"
+    if cache and os.path.exists(cache):
+        table = json.load(open(cache))
+        if key in table:
+            return table[key]
+    timings = {}
+    vol = None
+    for c in candidates:
+        r = Reconstructor(rot, nu, nv, grid, nz_layers=nz_layers, bp_warp=c, **plan_kw)
+        if vol is None:
+            vol = r.new_volume()
+        timings[c] = _time(lambda: r.run(images, vol), repeats)
+        r.close()
+        del r
+        torch.cuda.empty_cache()
+    best = min(timings, key=timings.get)
+    out = {"bp_warp": best, "ms": {str(k): v for k, v in timings.items()}}
     if cache:
         table = json.load(open(cache)) if os.path.exists(cache) else {}
         table[key] = out

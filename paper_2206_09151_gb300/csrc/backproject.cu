@@ -21,8 +21,7 @@ namespace recon {
 namespace {
 
 constexpr int kTX = kGenTile[0], kTY = kGenTile[1], kTZ = kGenTile[2];
-static_assert(kTX % 8 == 0 && kTY % 4 == 0 && (kTX / 8) * (kTY / 4) * 32 == kTX * kTY,
-              "the 8 x 4 warp patches must tile the voxel columns");
+static_assert(kTX == 32 && kTY == 8, "the warp patches (8 x 4, 16 x 2, 32 x 1) tile 32 x 8 voxel columns");
 
 // Integer pixel (floor) and FP32 fraction of a coordinate in 2^-40 pixel units.
 __device__ __forceinline__ int pix_floor(long long x) { return (int)(x >> kPixFracBits); }
@@ -109,10 +108,11 @@ __device__ __forceinline__ void bp_generic_tile(int bx, int by, int bz, const Di
                                                 int dir_begin, int dir_count, float* __restrict__ vol,
                                                 int accumulate, TileDir* s_dir) {
   const int i0 = bx * kTX, j0 = by * kTY, k0 = bz * kTZ;
-  // a warp covers an 8 (x) x 4 (y) patch of voxel columns rather than a line of 32: its
-  // samples in one z plane fall on a compact detector patch in any view orientation, so
-  // a row gather touches fewer cache lines
-  constexpr int kWX = 8, kWY = 32 / kWX;
+  // a warp covers a WX (x) x 32/WX (y) patch of voxel columns (8 x 4 by default rather than
+  // a line of 32: its samples in one z plane fall on a compact detector patch in any view
+  // orientation, so a row gather touches fewer cache lines); the shape only moves voxels
+  // between threads, every voxel's arithmetic is the same
+  const int kWX = c.warp_cols, kWY = 32 / kWX;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int tx = (w % (kTX / kWX)) * kWX + (l % kWX), ty = (w / (kTX / kWX)) * kWY + l / kWX;
   for (int d = threadIdx.x; d < dir_count; d += blockDim.x) {

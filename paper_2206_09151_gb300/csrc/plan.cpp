@@ -137,6 +137,7 @@ void recon_default_options(recon_options* o) {
   o->check_finite = 0;
   o->layer_interp = RECON_LAYER_NEAREST;
   o->mlp_views = 0.0;
+  o->bp_warp = 0;
 }
 
 const char* recon_error_string(int code) {
@@ -193,6 +194,8 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   if (o.filter == RECON_FILTER_MLP && !training && (!(o.nsr > 0.0) || !std::isfinite(o.nsr)))
     return fail(RECON_E_INVALID_ARG, "recon_plan: the learned filter needs nsr > 0");
   if (o.check_finite != 0 && o.check_finite != 1) return fail(RECON_E_INVALID_ARG, "recon_plan: check_finite must be 0 or 1");
+  if (o.bp_warp != 0 && o.bp_warp != 8 && o.bp_warp != 16 && o.bp_warp != 32)
+    return fail(RECON_E_INVALID_ARG, "recon_plan: bp_warp must be 0, 8, 16 or 32");
   if (!(o.mlp_views >= 0.0) || !std::isfinite(o.mlp_views))
     return fail(RECON_E_INVALID_ARG, "recon_plan: mlp_views must be >= 0");
   if (o.layer_interp != RECON_LAYER_NEAREST && o.layer_interp != RECON_LAYER_LINEAR)
@@ -475,6 +478,7 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   }
   cb.staged = o.bp_kernel == RECON_BP_STAGED;
   cb.layer_linear = o.layer_interp == RECON_LAYER_LINEAR;
+  cb.warp_cols = o.bp_warp ? o.bp_warp : 8;
 
   {  // the 3D-Fourier forms: padded grid, per-axis twiddles, per-view gridding constants
     p->uniform_R = true;

@@ -137,6 +137,7 @@ struct BackprojConst {
   float b_frac;   // b_off - floor(b_off), 0 or 1/2
   int staged;     // single-axis kernel with shared-memory staging of each footprint
   int layer_linear;  // blend the two layers whose centres bracket the depth (general kernel)
+  int warp_cols;     // general kernel: a warp's patch of voxel columns is warp_cols x 32/warp_cols
 };
 
 cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,

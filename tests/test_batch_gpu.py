@@ -167,3 +167,22 @@ def test_autotuner_picks_a_measured_candidate():
     assert out["dir_block"] in (8, 32)
     for r in recons:
         r.close()
+
+
+def test_bp_warp_shapes_are_bitwise_equal_and_the_tuner_picks_one():
+    """The general backprojection's warp patch (8 x 4, 16 x 2, 32 x 1 voxel columns) only
+    moves voxels between threads: the volumes are identical bit for bit, and the autotuner
+    returns one of the timed shapes."""
+    from paper_2206_09151_gb300.autotune import tune_bp_warp
+    from paper_2206_09151_gb300.recon import Reconstructor
+    toms = _tomograms()
+    rot, nu, grid, kw, img = toms[3]  # cone geometry: the general kernel
+    vols = []
+    for wc in (8, 16, 32):
+        r = Reconstructor(rot, nu, nu, grid, bp_warp=wc, **kw)
+        vols.append(r.run(img).clone())
+        r.close()
+    assert torch.equal(vols[0], vols[1]) and torch.equal(vols[0], vols[2])
+    out = tune_bp_warp(rot, nu, nu, grid, img, candidates=(8, 16, 32), repeats=2,
+                       **{k: v for k, v in kw.items() if k != "nz_layers"}, nz_layers=kw["nz_layers"])
+    assert out["bp_warp"] in (8, 16, 32) and set(out["ms"]) == {"8", "16", "32"}
