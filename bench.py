@@ -63,6 +63,13 @@ NCU_TRAFFIC: dict = {
     ("k_cols", "mid", "bf16"): {"bytes_per_launch": (21.393664e6 + 612.677376e6) * 3, "src": "d48e06ae03fad5cf"},
     ("k_rows_inv", "mid", "f32"): {"bytes_per_launch": (673.865728e6 + 633.4848e6) * 3, "src": "d48e06ae03fad5cf"},
     ("k_backproject", "mid", "f32"): {"bytes_per_launch": (612.676608e6 + 59.275520e6) * 3, "src": "40408219a6e58e02"},
+    # slab (bf16 stack): the column kernel from one 3-direction sub-block launch (the bench's
+    # launch size); the TMA-staged backprojection from a 6-direction launch, its reads scaled
+    # by 25/6 to the bench's 25-direction blocks (the stack boxes grow with the directions),
+    # plus the volume read of an accumulating block and the volume write (1.07 GB each)
+    ("k_cols", "slab", "bf16"): {"bytes_per_launch": 56.096512e6 + 1.551087e9, "src": "91b6d6728cadad50"},
+    ("k_backproject", "slab", "bf16"): {"bytes_per_launch": 3.058623e9 * 25 / 6 + 1.073742e9 + 1.055004e9,
+                                        "src": "cb17e905eba110ad"},
 }
 
 
@@ -176,10 +183,11 @@ def sample_voxels(cfg):
     return rng.integers(0, nx, n), rng.integers(0, ny, n), rng.integers(0, nz, n)
 
 
-def oracle_sample(cfg, images_np, dirs, mlp=None, voxels=None, workers: int = 1):
+def oracle_sample(cfg, images_np, dirs, mlp=None, voxels=None, workers: int = 1, layer_interp: str = "nearest"):
     """FP64 oracle on the directions ``dirs`` alone (a D = len(dirs) scan), at ``voxels`` or
     over the full volume, in ``workers`` processes; ``mlp`` = (weights, nsr) selects the
-    learned regulariser (with ``views``, the divisor of its eps)."""
+    learned regulariser (with ``views``, the divisor of its eps); ``layer_interp`` the
+    nearest layer or the blend of the two bracketing ones."""
     import oracle as O
     kw = dict(lam=cfg["lam"], delta=cfg["delta"], defocus=cfg["defocus"][dirs], nz_layers=cfg["nz_layers"],
               grid=cfg["grid"], sigma=cfg["sigma"], cs=cfg["cs"], voxels=voxels, workers=workers,
@@ -188,7 +196,8 @@ def oracle_sample(cfg, images_np, dirs, mlp=None, voxels=None, workers: int = 1)
         return O.learned.recon_learned(images_np[dirs], cfg["rot"][dirs], mlp[0].astype(np.float64), nsr=mlp[1],
                                        views=mlp[2],
                                        **kw)
-    return O.recon(images_np[dirs], cfg["rot"][dirs], eps=cfg["eps"], **kw)
+    return O.recon(images_np[dirs], cfg["rot"][dirs], eps=cfg["eps"],
+                   layer_interp=O.LAYER_LINEAR if layer_interp == "linear" else O.LAYER_NEAREST, **kw)
 
 
 # ----------------------------------------------------------------------------- reference arm
@@ -211,11 +220,11 @@ def host_cpu() -> tuple[int, str]:
     return cores, model
 
 
-def oracle_timed(cfg, images_np, dirs, workers, mlp=None, voxels=None):
+def oracle_timed(cfg, images_np, dirs, workers, mlp=None, voxels=None, layer_interp: str = "nearest"):
     """The FP64 oracle on the directions ``dirs`` (a scan of its own) over ``voxels``,
     spread over ``workers`` spawned processes; returns (result, wall seconds)."""
     t0 = time.perf_counter()
-    ref = oracle_sample(cfg, images_np, dirs, mlp, voxels, workers)
+    ref = oracle_sample(cfg, images_np, dirs, mlp, voxels, workers, layer_interp)
     return ref, time.perf_counter() - t0
 
 
@@ -353,7 +362,8 @@ def run_ours(args):
     r = Reconstructor(cfg["rot"], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
                       defocus=cfg["defocus"], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"], eps=cfg["eps"],
                       cs=cfg["cs"], stack_dtype=args.stack, dir_block=args.dir_block, stage_block=args.stage_block,
-                      bp_kernel=args.bp_kernel, ramp=cfg["ramp"], device=dev, **filt_kw)
+                      bp_kernel=args.bp_kernel, ramp=cfg["ramp"], layer_interp=args.layer_interp, device=dev,
+                      **filt_kw)
     vol = r.new_volume()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
@@ -420,11 +430,12 @@ def run_ours(args):
     counts = [min(db, D - b * db) for b in range(nb)]
     algo = algorithmic_bytes(cfg, r, 2 if args.stack == "bf16" else 4, counts)
     kernels = {}
+    bp_src = "backproject_tma.cu" if r.bp_kernel_used == "tma" else "backproject.cu"
     for q, name in enumerate(KERNELS):
         per_launch_ms = kern_ms[q] / max(kern_n[q], 1)
         gbs = algo[q] / (kern_ms[q] / args.steps / 1e3) / 1e9 if kern_ms[q] > 0 else None
         tr = NCU_TRAFFIC.get((name, args.workload, args.stack))
-        src = "backproject.cu" if q == 3 else "stage_a.cu"
+        src = bp_src if q == 3 else "stage_a.cu"
         kernels[name] = {"launches": kern_n[q], "ms_per_launch": per_launch_ms,
                          "share": kern_ms[q] / max(sum(kern_ms), 1e-12), "algorithmic_GBps": gbs,
                          "algorithmic_bytes_per_launch": algo[q] * args.steps / max(kern_n[q], 1),
@@ -435,7 +446,7 @@ def run_ours(args):
                                                if kern_ms[1] > 0 else None)
     dom = max(range(4), key=lambda q: kern_ms[q])
     dom_name = KERNELS[dom]
-    src = "backproject.cu" if dom == 3 else "stage_a.cu"
+    src = bp_src if dom == 3 else "stage_a.cu"
     key = (dom_name, args.workload, args.stack)
     tr = NCU_TRAFFIC.get(key)
     traffic = tr["bytes_per_launch"] if tr and tr["src"] == _src_hash(src) else None
@@ -466,6 +477,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD_TEXT[args.workload] + (f" [first {D} directions only]" if args.dirs else ""),
                        "stack": args.stack, "filter": args.filter, "dir_block": db,
                        "stage_block": r.stage_block, "bp_kernel": args.bp_kernel,
+                       "bp_kernel_used": r.bp_kernel_used, "layer_interp": args.layer_interp,
                        "blocks": nb, "padded_fft": r.padded, "updates_per_step": U,
                        "l2": "flushed between timed steps (256 MiB write outside the timed span)",
                        "parallelism": f"replicas x{world}"},
@@ -519,11 +531,11 @@ def run_ours(args):
         img_np = images.cpu().numpy()
         vox = sample_voxels(cfg)
         workers = min(cores, len(sel))
-        ref, dt = oracle_timed(cfg, img_np, sel, workers, mlp, vox)
+        ref, dt = oracle_timed(cfg, img_np, sel, workers, mlp, vox, args.layer_interp)
         rs = Reconstructor(cfg["rot"][sel], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
                            defocus=cfg["defocus"][sel], nz_layers=cfg["nz_layers"], sigma=cfg["sigma"],
                            eps=cfg["eps"], cs=cfg["cs"], stack_dtype=args.stack, ramp=cfg["ramp"], device=dev,
-                           **filt_kw)
+                           bp_kernel=args.bp_kernel, layer_interp=args.layer_interp, **filt_kw)
         got = rs.run(images[sel].contiguous())
         rs.close()
         if vox is None:
@@ -674,8 +686,10 @@ def main():
                          "analytic one")
     ap.add_argument("--dir-block", type=int, default=0)
     ap.add_argument("--stage-block", type=int, default=0, help="directions per FFT/filter sub-block, 0 = auto")
-    ap.add_argument("--bp-kernel", choices=["auto", "direct", "staged"], default="auto",
-                    help="single-axis backprojection variant")
+    ap.add_argument("--bp-kernel", choices=["auto", "direct", "staged", "tma"], default="auto",
+                    help="backprojection variant (tma: the TMA-staged kernel for any geometry)")
+    ap.add_argument("--layer-interp", choices=["nearest", "linear"], default="nearest",
+                    help="a voxel's layer: the one containing its depth, or the blend of the two bracketing ones")
     ap.add_argument("--dirs", type=int, default=None, help="first N directions only (small profiling cases)")
     ap.add_argument("--cpu-dirs", type=int, default=None, help="oracle directions of the CPU baseline "
                     "(default: one per host core)")
@@ -684,6 +698,8 @@ def main():
     args.warmup = max(args.warmup, 3)  # at least three untimed warm-up steps
     if args.stack is None:
         args.stack = DEFAULT_STACK[args.workload]
+    if args.layer_interp == "linear" and args.filter == "mlp":
+        ap.error("--layer-interp linear is measured with the analytic filter")
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":

@@ -57,6 +57,9 @@ extern "C" {
 #define RECON_E_NONFINITE (-6)        /* an image holds NaN or Inf (checked only when the
                                          plan's check_finite option is set)             */
 #define RECON_E_NO_WEIGHTS (-7)       /* RECON_FILTER_MLP without its network parameters */
+#define RECON_E_DEVICE_CHECK (-8)     /* a kernel's own check failed: a bounded wait ran out
+                                         (2 s) or a footprint left its staging box; the call
+                                         synchronised its stream and the output is incomplete */
 
 /* ---------------------------------------------------------------- option values */
 #define RECON_FILTER_OFF 0       /* H = 1: ramp-filtered backprojection of g (Eq. 15)   */
@@ -90,9 +93,18 @@ extern "C" {
                                     four row gathers per sample instead of two, in the
                                     general backprojection kernel for every geometry      */
 
-#define RECON_BP_AUTO 0          /* the single-axis variant measured faster (DIRECT)     */
-#define RECON_BP_DIRECT 1        /* single-axis: bilinear gathers straight from the stack */
+#define RECON_BP_AUTO 0          /* the variant measured faster on sm_103a: DIRECT for a
+                                    single axis along y with the nearest layer, TMA for
+                                    every other case where its footprint box fits shared
+                                    memory (else the general direct kernel)              */
+#define RECON_BP_DIRECT 1        /* bilinear gathers straight from the stack (single-axis
+                                    kernel, or the general kernel)                       */
 #define RECON_BP_STAGED 2        /* single-axis: footprint staged in shared memory        */
+#define RECON_BP_TMA 3           /* any geometry: each (16 x 16 x 16 voxel tile, direction)
+                                    footprint box copied into a shared-memory ring by one
+                                    TMA load (cp.async.bulk.tensor), gathers from shared
+                                    memory; the call then reads a device status word back
+                                    (one 4-byte copy and a stream synchronisation)        */
 
 /* Limits (RECON_E_UNSUPPORTED_SIZE beyond them). */
 #define RECON_MAX_IMAGE 1024     /* nu, nv <= 1024, so P <= 2048                        */
@@ -127,10 +139,10 @@ typedef struct {
                       the Poisson floor (nsr M)^2 per DFT coefficient of the SNR feature   */
   int stage_block; /* directions per FFT/filter sub-block (their spectra and per-layer
                       intermediates sized for it), 0 = the whole direction block           */
-  int bp_kernel;   /* RECON_BP_*: single-axis backprojection variant (gathers straight from
-                      the stack, or each direction's footprint staged in shared memory);
-                      AUTO picks the measured-faster one on sm_103a; other geometries
-                      always use the general kernel                                         */
+  int bp_kernel;   /* RECON_BP_*: backprojection variant.  DIRECT / STAGED choose between the
+                      single-axis kernels (other geometries then use the general direct
+                      kernel); TMA runs the TMA-staged kernel for every geometry; AUTO picks
+                      the measured-faster kernel for the geometry on sm_103a                 */
   int check_finite; /* 1: recon_run (and recon_run_noalloc) first scans the images for NaN / Inf on the GPU, waits
                        for the scan (the call then synchronises its stream) and returns
                        RECON_E_NONFINITE without touching the volume if it finds any; 0: no
@@ -172,16 +184,21 @@ int recon_workspace_size(recon_plan_t plan, size_t* bytes);
  *   images    device, float32 [n_dir][nv][nu], caller-owned, read only
  *   volume    device, float32 [nz][ny][nx], caller-owned, written (or added to)
  *   workspace device, >= recon_workspace_size bytes, 256-byte aligned, scratch
- * Asynchronous: returns once every kernel is queued.  Uses the current CUDA device. */
+ * Asynchronous: returns once every kernel is queued, except where the plan runs the
+ * TMA-staged backprojection (RECON_BP_TMA, or AUTO for a general geometry or the layer
+ * blend): the call then synchronises `stream` at its end to read that kernel's status
+ * word (RECON_E_DEVICE_CHECK if a bounded wait ran out).  Uses the current CUDA device. */
 int recon_run(recon_plan_t plan, const float* images, float* volume, void* workspace, size_t ws_bytes,
               void* stream);
 
 /* Stage A alone (Sec. 2, Eq. 4-11 per layer): the layer stacks of directions
  * [dir_begin, dir_begin + dir_count), dir_count <= the plan's block size, into the
  * workspace.  *stack_out receives a device pointer into the workspace, laid out
- * [dir_count][Nz][nv + 2][nu + 1] of horizontal tap pairs (two float32, or two
- * bfloat16, per stack_dtype): entry [n][k][v + 1][c] = (Y_{n,k}(c - 1, v), Y_{n,k}(c, v))
- * for c in [0, nu], with Y = 0 outside the image; rows 0 and nv + 1 are zero. */
+ * [dir_count][Nz][nv + 2][su] of horizontal tap pairs (two float32, or two bfloat16, per
+ * stack_dtype), su = nu + 1 rounded up to a multiple of 4 (every row starts on a 16-byte
+ * boundary): entry [n][k][v + 1][c] = (Y_{n,k}(c - 1, v), Y_{n,k}(c, v)) for c in [0, nu],
+ * with Y = 0 outside the image; rows 0 and nv + 1 are zero; entries c > nu are padding
+ * (not written, never read). */
 int recon_filter_stage(recon_plan_t plan, const float* images, int dir_begin, int dir_count, void* workspace,
                        size_t ws_bytes, void* stream, const void** stack_out);
 
@@ -192,6 +209,15 @@ int recon_filter_stage(recon_plan_t plan, const float* images, int dir_begin, in
  * workspace of recon_workspace_size bytes. */
 int recon_backproject(recon_plan_t plan, const void* stack, int dir_begin, int dir_count, float* volume,
                       int accumulate, void* workspace, size_t ws_bytes, void* stream);
+
+/* Self-test of the failure detection of the TMA-staged backprojection: launches it on
+ * one voxel tile whose producer issues no copy, so every consumer's wait on its
+ * stage runs out after the 2 s limit; the kernel then sets its status bit and returns
+ * without touching the GPU's state.  Allocates and frees 16 KB of device memory and
+ * synchronises `stream`.  RECON_OK when the kernel reported the run-out wait (the
+ * expected outcome, after about 2 s), RECON_E_DEVICE_CHECK if it did not, RECON_E_CUDA
+ * on a CUDA error. */
+int recon_selftest_wait_limit(void* stream);
 
 /* ---------------------------------------------------------------- batches
  * Many tomograms of uneven sizes (each with its own plan: grid, images, directions,
@@ -218,6 +244,11 @@ int recon_batch_destroy(recon_batch_t batch); /* NULL is a no-op */
 int recon_run_batch_workspace_size(int n, const recon_plan_t* plans, size_t* bytes);
 int recon_run_batch(int n, const recon_plan_t* plans, const float* const* images, float* const* volumes,
                     void* workspace, size_t ws_bytes, void* stream);
+
+/* The backprojection kernel that recon_run, recon_backproject and recon_swap_ct of this
+ * plan launch (the resolution of RECON_BP_AUTO): RECON_BP_DIRECT (the single-axis or the
+ * general direct kernel), RECON_BP_STAGED or RECON_BP_TMA.  No CUDA call. */
+int recon_plan_bp_kernel(recon_plan_t plan, int* kernel);
 
 /* Depth of field (Sec. 1): DOF = delta^2 / (2 lambda).  Layers thinner than the DOF
  * keep every voxel within its layer's focus; a thicker layer is the plan-time warning of
@@ -349,6 +380,8 @@ int recon_profile_read(recon_plan_t plan, double* ms, int* launches);
  *   Sharing: all calls share the one array and it keeps the last call's contents;
  *   nothing in it needs to start at zero (every kernel writes what it later reads), but
  *   two calls that overlap on the GPU (other streams, other threads) race on it.
+ *   Kernels: the backprojection is always a direct-gather kernel (the plan's TMA-staged
+ *   choice does not apply), so the call never synchronises `stream`.
  * Calls no cudaMalloc, cudaFree or allocating library routine. */
 int recon_run_noalloc(recon_plan_t plan, const float* images, float* volume, void* stream);
 

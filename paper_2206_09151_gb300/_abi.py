@@ -21,6 +21,7 @@ RECON_E_WORKSPACE = -4
 RECON_E_NO_MEMORY = -5
 RECON_E_NONFINITE = -6
 RECON_E_NO_WEIGHTS = -7
+RECON_E_DEVICE_CHECK = -8
 
 RECON_FILTER_OFF = 0
 RECON_FILTER_TIKHONOV = 1
@@ -33,7 +34,7 @@ RECON_STACK_F32 = 0
 RECON_STACK_BF16 = 1
 RECON_RAMP_SINGLE_AXIS = 0
 RECON_RAMP_DENSITY = 1
-RECON_BP_AUTO, RECON_BP_DIRECT, RECON_BP_STAGED = 0, 1, 2
+RECON_BP_AUTO, RECON_BP_DIRECT, RECON_BP_STAGED, RECON_BP_TMA = 0, 1, 2, 3
 RECON_LAYER_NEAREST, RECON_LAYER_LINEAR = 0, 1
 RECON_NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 RECON_MAX_LAYERS = 96
@@ -98,6 +99,7 @@ def load_library(path: str = LIB_PATH):
     L.recon_run_noalloc.argtypes = [vp, vp, vp, vp]
     L.recon_plan_dof.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
     L.recon_plan_layers.argtypes = [vp, ctypes.POINTER(ip)]
+    L.recon_plan_bp_kernel.argtypes = [vp, ctypes.POINTER(ip)]
     L.recon_swap_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
     L.recon_swap_ct.argtypes = [vp, vp, vp, sz, vp]
     L.recon_swap_phase.argtypes = [vp, ctypes.c_double, ctypes.c_double, vp, vp, sz, vp]
@@ -121,6 +123,7 @@ def load_library(path: str = LIB_PATH):
     L.recon_profile_enable.argtypes = [vp, ip]
     L.recon_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ip)]
     L.recon_sync.argtypes = [vp]
+    L.recon_selftest_wait_limit.argtypes = [vp]
     L.recon_destroy.argtypes = [vp]
     L.recon_error_string.argtypes = [ip]
     L.recon_error_string.restype = ctypes.c_char_p
@@ -132,7 +135,7 @@ def load_library(path: str = LIB_PATH):
                  "recon_batch_workspace_size", "recon_batch_run", "recon_batch_run_graph", "recon_batch_destroy",
                  "recon_run_batch_workspace_size", "recon_run_batch", "recon_plan_dof", "recon_layers_for_dof",
                  "recon_plan_layers", "recon_swap_workspace_size", "recon_swap_ct", "recon_swap_phase",
-                 "recon_grid_workspace_size", "recon_grid_run"):
+                 "recon_grid_workspace_size", "recon_grid_run", "recon_selftest_wait_limit", "recon_plan_bp_kernel"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -237,6 +240,12 @@ def recon_plan_layers(plan) -> int:
     n = ctypes.c_int()
     _check(load_library().recon_plan_layers(plan, ctypes.byref(n)), "recon_plan_layers")
     return n.value
+
+
+def recon_plan_bp_kernel(plan) -> int:
+    k = ctypes.c_int()
+    _check(load_library().recon_plan_bp_kernel(plan, ctypes.byref(k)), "recon_plan_bp_kernel")
+    return k.value
 
 
 def recon_plan_warning(plan) -> str:
@@ -359,6 +368,12 @@ def recon_run_batch(plans, image_ptrs, volume_ptrs, ws_ptr: int, ws_bytes: int, 
 
 def recon_sync(stream: int):
     _check(load_library().recon_sync(stream), "recon_sync")
+
+
+def recon_selftest_wait_limit(stream: int) -> int:
+    """The status of the TMA-staged backprojection's wait-limit self-test (RECON_OK when its
+    waits ran out after their limit and the kernel reported it)."""
+    return int(load_library().recon_selftest_wait_limit(stream))
 
 
 def recon_destroy(plan):

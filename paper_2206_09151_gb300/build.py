@@ -16,7 +16,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "librecon.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
-CU_SOURCES = ["stage_a.cu", "backproject.cu", "density.cu", "learned.cu", "noalloc.cu", "fft3.cu", "fourier.cu"]
+CU_SOURCES = ["stage_a.cu", "backproject.cu", "backproject_tma.cu", "density.cu", "learned.cu", "noalloc.cu", "fft3.cu", "fourier.cu"]
 CPP_SOURCES = ["plan.cpp"]
 
 

@@ -93,6 +93,8 @@ struct recon_plan_s {
   bool training = false;
   recon::StageAConst ca;
   recon::BackprojConst cb;
+  recon::TmaBox tma{};   // footprint box of the TMA-staged backprojection
+  bool use_tma = false;  // stage B runs k_backproject_tma
   // workspace layout (byte offsets)
   size_t off_dirs, off_uA, off_ramp, off_tw, off_twp, off_dens, off_dsum, off_theta, off_cnt, off_x2, off_S, off_T,
       off_stack, off_pow, off_eps, ws_bytes, table_bytes;
@@ -150,6 +152,7 @@ const char* recon_error_string(int code) {
     case RECON_E_NO_MEMORY: return "host allocation failed";
     case RECON_E_NONFINITE: return "an image holds NaN or Inf";
     case RECON_E_NO_WEIGHTS: return "the learned filter has no network parameters";
+    case RECON_E_DEVICE_CHECK: return "a device-side check failed (a bounded wait ran out or a footprint left its box)";
     default: return "unknown status";
   }
 }
@@ -216,7 +219,7 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
     return fail(RECON_E_INVALID_ARG, "recon_plan: non-finite sigma, eps or cs");
   if (o.dir_block < 0) return fail(RECON_E_INVALID_ARG, "recon_plan: dir_block < 0");
   if (o.stage_block < 0) return fail(RECON_E_INVALID_ARG, "recon_plan: stage_block < 0");
-  if (o.bp_kernel < RECON_BP_AUTO || o.bp_kernel > RECON_BP_STAGED)
+  if (o.bp_kernel < RECON_BP_AUTO || o.bp_kernel > RECON_BP_TMA)
     return fail(RECON_E_INVALID_ARG, "recon_plan: unknown bp_kernel");
 
   recon_plan_s* p = new (std::nothrow) recon_plan_s();
@@ -392,8 +395,10 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   ca.eps = (float)o.eps;
   ca.pref = (float)(lambda / (4.0 * M_PI * std::sqrt(1.0 + o.sigma * o.sigma)));
   ca.half = p->half;
-  ca.su = p->nu + 1;
-  ca.layer_elems = (size_t)(p->nv + 2) * (p->nu + 1);
+  // row stride: the nu + 1 tap pairs rounded up to 4 entries, so every row starts on a
+  // 16-byte boundary (the TMA-staged backprojection's tensor map needs 16-byte strides)
+  ca.su = (p->nu + 1 + 3) & ~3;
+  ca.layer_elems = (size_t)(p->nv + 2) * ca.su;
   {  // sampling-density grid (density weighting only), see density.cuh
     recon::DensityConst& dc = ca.dens;
     std::memset(&dc, 0, sizeof(dc));
@@ -479,6 +484,19 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   cb.staged = o.bp_kernel == RECON_BP_STAGED;
   cb.layer_linear = o.layer_interp == RECON_LAYER_LINEAR;
   cb.warp_cols = o.bp_warp ? o.bp_warp : 8;
+  // The TMA-staged kernel where the general kernel would run (any geometry but a single
+  // axis along y, or the layer blend), measured faster on sm_103a; on request for any geometry.
+  const bool general = !cb.axis_y || cb.layer_linear;
+  if (o.bp_kernel == RECON_BP_TMA || (o.bp_kernel == RECON_BP_AUTO && general && D > 0)) {
+    p->tma = recon::tma_box_for(cb, p->dirs.data(), D);
+    if (!p->tma.ok && o.bp_kernel == RECON_BP_TMA) {
+      delete p;
+      return fail(RECON_E_UNSUPPORTED_SIZE,
+                  "recon_plan: a footprint box of the TMA-staged backprojection is too large (more than 256 pairs, "
+                  "rows or layers, or 200 KB of shared memory)");
+    }
+    p->use_tma = p->tma.ok != 0;
+  }
 
   {  // the 3D-Fourier forms: padded grid, per-axis twiddles, per-view gridding constants
     p->uniform_R = true;
@@ -634,6 +652,13 @@ int recon_destroy(recon_plan_t p) {
   return RECON_OK;
 }
 
+int recon_plan_bp_kernel(recon_plan_t p, int* kernel) {
+  if (!p || !kernel) return fail(RECON_E_INVALID_ARG, "recon_plan_bp_kernel: null argument");
+  *kernel = p->use_tma ? RECON_BP_TMA : ((p->cb.axis_y && !p->cb.layer_linear && p->cb.staged) ? RECON_BP_STAGED
+                                                                                                 : RECON_BP_DIRECT);
+  return RECON_OK;
+}
+
 int recon_plan_dof(recon_plan_t p, double* pitch_max, double* dof) {
   if (!p) return fail(RECON_E_INVALID_ARG, "recon_plan_dof: null plan");
   if (pitch_max) *pitch_max = p->pitch_max;
@@ -746,6 +771,39 @@ int scan_finite(recon_plan_t p, const float* images, unsigned int* d_count, cuda
   return RECON_OK;
 }
 
+// The TMA-staged backprojection's status word: the second word of the flag slot.
+unsigned int* tma_status(recon_plan_t p, void* ws) { return (unsigned int*)((char*)ws + p->off_flag) + 1; }
+
+// Stage B of one direction block through the plan's backprojection kernel.
+cudaError_t backproject_block(recon_plan_t p, const recon::DirParams* dirs, const void* stack, int d0, int cnt,
+                              float* vol, int accumulate, void* ws, cudaStream_t s) {
+  if (p->use_tma)
+    return recon::launch_backproject_tma(p->cb, p->tma, dirs, stack, d0, cnt, vol, accumulate, tma_status(p, ws), s);
+  return recon::launch_backproject(p->cb, dirs, stack, d0, cnt, vol, accumulate, s);
+}
+
+// Before a call's first TMA-staged launch: clear the status word.
+int tma_begin(recon_plan_t p, void* ws, cudaStream_t s, const char* who) {
+  if (!p->use_tma) return RECON_OK;
+  const cudaError_t e = cudaMemsetAsync(tma_status(p, ws), 0, sizeof(unsigned int), s);
+  return e == cudaSuccess ? RECON_OK : cuda_fail(e, (std::string(who) + ": clearing the status word").c_str());
+}
+
+// After its last: read the status word back (a 4-byte copy and a stream synchronisation).
+int tma_end(recon_plan_t p, void* ws, cudaStream_t s, const char* who) {
+  if (!p->use_tma) return RECON_OK;
+  unsigned int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, tma_status(p, ws), sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e, (std::string(who) + ": reading the backprojection status").c_str());
+  if (h & 1u)
+    return fail(RECON_E_DEVICE_CHECK,
+                std::string(who) + ": a bounded wait of the TMA-staged backprojection ran out; the volume is incomplete");
+  if (h & 2u)
+    return fail(RECON_E_DEVICE_CHECK, std::string(who) + ": a footprint left its TMA staging box; the volume is wrong");
+  return RECON_OK;
+}
+
 // Learned regulariser, between the row FFTs and the column kernel of each block: radial
 // power spectrum of every image (column FFTs), then the eps table of the block.
 struct MlpHookCtx {
@@ -800,18 +858,20 @@ int recon_run(recon_plan_t p, const float* images, float* volume, void* workspac
   MlpHookCtx hctx{p, (const char*)workspace, (float*)((char*)workspace + p->off_pow), w.eps, w.S, w.twp};
   const recon::StageAHook hook{mlp_hook, &hctx};
   const recon::StageAHook* hk = p->ca.filter == RECON_FILTER_MLP ? &hook : nullptr;
+  rc = tma_begin(p, workspace, s, "recon_run");
+  if (rc) return rc;
   if (rec) rec->mark(-1, s);
   for (int b = 0; b < p->n_blocks; ++b) {
     const int d0 = b * p->db;
     const int cnt = (p->D - d0) < p->db ? (p->D - d0) : p->db;
     cudaError_t e = recon::launch_stage_a(p->ca, w, images, d0, cnt, s, rec, hk);
     if (e != cudaSuccess) return cuda_fail(e, "recon_run: stage A launch");
-    e = recon::launch_backproject(p->cb, w.dirs, w.stack, d0, cnt, volume, p->opt.accumulate || b > 0, s);
+    e = backproject_block(p, w.dirs, w.stack, d0, cnt, volume, p->opt.accumulate || b > 0, workspace, s);
     if (e != cudaSuccess) return cuda_fail(e, "recon_run: backprojection launch");
     if (rec) rec->mark(3, s);
   }
   if (rec) p->profiled_events = recorder.n;
-  return RECON_OK;
+  return tma_end(p, workspace, s, "recon_run");
 }
 
 int recon_filter_stage(recon_plan_t p, const float* images, int dir_begin, int dir_count, void* workspace,
@@ -856,8 +916,29 @@ int recon_backproject(recon_plan_t p, const void* stack, int dir_begin, int dir_
   const recon::Workspace w = carve(p, workspace);
   rc = upload_tables(p, w, s);
   if (rc) return rc;
-  cudaError_t e = recon::launch_backproject(p->cb, w.dirs, stack, dir_begin, dir_count, volume, accumulate, s);
+  rc = tma_begin(p, workspace, s, "recon_backproject");
+  if (rc) return rc;
+  cudaError_t e = backproject_block(p, w.dirs, stack, dir_begin, dir_count, volume, accumulate, workspace, s);
   if (e != cudaSuccess) return cuda_fail(e, "recon_backproject: launch");
+  return tma_end(p, workspace, s, "recon_backproject");
+}
+
+int recon_selftest_wait_limit(void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  void* buf = nullptr;
+  cudaError_t e = cudaMalloc(&buf, 16384);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_selftest_wait_limit: allocation");
+  unsigned int* d_status = (unsigned int*)((char*)buf + 12288);
+  unsigned int h = 0;
+  e = cudaMemsetAsync(d_status, 0, sizeof(unsigned int), s);
+  if (e == cudaSuccess) e = recon::launch_tma_wait_probe(buf, 12288, d_status, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d_status, sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  const cudaError_t ef = cudaFree(buf);
+  if (e == cudaSuccess) e = ef;
+  if (e != cudaSuccess) return cuda_fail(e, "recon_selftest_wait_limit");
+  if ((h & 1u) == 0)
+    return fail(RECON_E_DEVICE_CHECK, "recon_selftest_wait_limit: the kernel did not report its run-out wait");
   return RECON_OK;
 }
 
@@ -1023,6 +1104,8 @@ int recon_swap_ct(recon_plan_t p, const float* images, void* workspace, size_t w
   float* vc = (float*)(b + L.vc);
   float* vs = (float*)(b + L.vs);
   const size_t nvox = (size_t)p->nx * p->ny * p->nz;
+  rc = tma_begin(p, workspace, s, "recon_swap_ct");
+  if (rc) return rc;
   for (int mode = 1; mode <= 2; ++mode) {  // cos, then sin of the layer's depth phase, no CTF
     float* vol = mode == 1 ? vc : vs;
     recon::StageAConst ca = p->ca;
@@ -1037,10 +1120,12 @@ int recon_swap_ct(recon_plan_t p, const float* images, void* workspace, size_t w
       const int cnt = (p->D - d0) < p->db ? (p->D - d0) : p->db;
       cudaError_t e = recon::launch_stage_a(ca, w, images, d0, cnt, s);
       if (e != cudaSuccess) return cuda_fail(e, "recon_swap_ct: stage A launch");
-      e = recon::launch_backproject(p->cb, w.dirs, w.stack, d0, cnt, vol, bk > 0, s);
+      e = backproject_block(p, w.dirs, w.stack, d0, cnt, vol, bk > 0, workspace, s);
       if (e != cudaSuccess) return cuda_fail(e, "recon_swap_ct: backprojection launch");
     }
   }
+  rc = tma_end(p, workspace, s, "recon_swap_ct");
+  if (rc) return rc;
   float2* Z = (float2*)(b + L.Z);
   cudaError_t e = recon::launch_swap_pack(vc, vs, Z, p->f3, s);
   const float2* twa[3] = {axis_tw(p, tw[0], 0), axis_tw(p, tw[1], 1), axis_tw(p, tw[2], 2)};

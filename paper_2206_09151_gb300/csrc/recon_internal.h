@@ -143,6 +143,23 @@ struct BackprojConst {
 cudaError_t launch_backproject(const BackprojConst& c, const DirParams* dirs, const void* stack, int dir_begin,
                                int dir_count, float* volume, int accumulate, cudaStream_t stream);
 
+// Footprint box of the TMA-staged backprojection: every (tile, direction) footprint of the
+// plan's directions fits W pairs x H rows x L layers of the stack.
+struct TmaBox {
+  int W, H, L;        // box extents (W a multiple of 4, so a row of the box is 16-byte aligned)
+  int stages;         // shared-memory ring depth
+  size_t stage_bytes; // W H L entries rounded up to 128 bytes
+  int ok;             // 0: the box is too large for the kernel (it then cannot be used)
+};
+TmaBox tma_box_for(const BackprojConst& c, const DirParams* dirs, int n_dirs);
+// status: device word; bit 0 = a bounded wait ran out, bit 1 = a footprint outside its box
+cudaError_t launch_backproject_tma(const BackprojConst& c, const TmaBox& box, const DirParams* dirs, const void* stack,
+                                   int dir_begin, int dir_count, float* volume, int accumulate, unsigned int* status,
+                                   cudaStream_t stream);
+// Diagnostic launch whose producer issues nothing, so every consumer wait runs out (after
+// its 2 s limit) and sets bit 0 of *status; buf: >= 10 KB of device memory, 256-byte aligned.
+cudaError_t launch_tma_wait_probe(void* buf, size_t buf_bytes, unsigned int* status, cudaStream_t stream);
+
 // One tomogram's share of a persistent batched backprojection: its constants, pointers,
 // kernel kind (general 0/1, single-axis 2..5 (float32 / bfloat16 stack, one or two detector
 // rows), general with the layer blend 6/7),

@@ -14,7 +14,8 @@ _FILTERS = {"off": _abi.RECON_FILTER_OFF, "tikhonov": _abi.RECON_FILTER_TIKHONOV
 _INPUTS = {"intensity": _abi.RECON_INPUT_INTENSITY, "contrast": _abi.RECON_INPUT_CONTRAST}
 _STACKS = {"f32": _abi.RECON_STACK_F32, "bf16": _abi.RECON_STACK_BF16}
 _RAMPS = {"single_axis": _abi.RECON_RAMP_SINGLE_AXIS, "density": _abi.RECON_RAMP_DENSITY}
-_BP_KERNELS = {"auto": _abi.RECON_BP_AUTO, "direct": _abi.RECON_BP_DIRECT, "staged": _abi.RECON_BP_STAGED}
+_BP_KERNELS = {"auto": _abi.RECON_BP_AUTO, "direct": _abi.RECON_BP_DIRECT, "staged": _abi.RECON_BP_STAGED,
+               "tma": _abi.RECON_BP_TMA}
 _LAYER_INTERP = {"nearest": _abi.RECON_LAYER_NEAREST, "linear": _abi.RECON_LAYER_LINEAR}
 
 
@@ -55,6 +56,8 @@ class Reconstructor:
         self.stack_dtype = torch.bfloat16 if stack_dtype == "bf16" else torch.float32
         self.plan = _abi.recon_plan(self.rot, nu, nv, lam, delta, defocus, nz_layers, self.grid, o)
         self.nz_layers = _abi.recon_plan_layers(self.plan)
+        # the backprojection kernel the plan runs ("direct", "staged" or "tma")
+        self.bp_kernel_used = {v: k for k, v in _BP_KERNELS.items()}[_abi.recon_plan_bp_kernel(self.plan)]
         self.ws_bytes = _abi.recon_workspace_size(self.plan)
         self.padded, self.dir_block, self.n_blocks, self.stage_block = _abi.recon_plan_info(self.plan)
         self.device = torch.device(device) if device is not None else (
@@ -92,25 +95,45 @@ class Reconstructor:
                        self._stream(stream))
         return volume
 
+    @property
+    def stack_row_stride(self) -> int:
+        """Entries per stack row: the nu + 1 tap pairs rounded up to a multiple of 4 (every
+        row starts on a 16-byte boundary); the entries past nu are padding, never read."""
+        return (self.nu + 4) // 4 * 4
+
     def filter_stage(self, images: torch.Tensor, dir_begin: int, dir_count: int, stream=None) -> torch.Tensor:
         """``recon_filter_stage``: a view of the workspace holding the layer stacks as
-        horizontal tap pairs, shape (dir_count, Nz, nv + 2, nu + 1, 2): entry
-        [n, k, v + 1, c] = (Y[v][c - 1], Y[v][c]), zero outside the image."""
+        horizontal tap pairs, shape (dir_count, Nz, nv + 2, nu + 1, 2) (rows
+        :attr:`stack_row_stride` entries apart): entry [n, k, v + 1, c] = (Y[v][c - 1],
+        Y[v][c]), zero outside the image."""
         self._check_images(images)
         ptr = _abi.recon_filter_stage(self.plan, images.data_ptr(), dir_begin, dir_count,
                                       self.workspace.data_ptr(), self.ws_bytes, self._stream(stream))
         off = ptr - self.workspace.data_ptr()
         esz = 2 if self.stack_dtype == torch.bfloat16 else 4
-        n = dir_count * self.nz_layers * (self.nv + 2) * (self.nu + 1) * 2
+        su = self.stack_row_stride
+        n = dir_count * self.nz_layers * (self.nv + 2) * su * 2
         return self.workspace[off:off + n * esz].view(self.stack_dtype).view(
-            dir_count, self.nz_layers, self.nv + 2, self.nu + 1, 2)
+            dir_count, self.nz_layers, self.nv + 2, su, 2)[:, :, :, :self.nu + 1, :]
 
     def backproject(self, stack: torch.Tensor, dir_begin: int, dir_count: int, volume: torch.Tensor,
                     accumulate: bool, stream=None) -> torch.Tensor:
         """``recon_backproject``: layered backprojection of ``stack`` (tap-pair layout of
-        :meth:`filter_stage`) into ``volume``."""
-        if stack.dtype != self.stack_dtype or not stack.is_contiguous():
-            raise ValueError("stack dtype/layout does not match the plan")
+        :meth:`filter_stage`: its views are passed as they are; a contiguous
+        (dir_count, Nz, nv + 2, nu + 1, 2) tensor is first copied into the plan's row
+        stride) into ``volume``."""
+        su = self.stack_row_stride
+        shape = (dir_count, self.nz_layers, self.nv + 2, self.nu + 1, 2)
+        strides = (self.nz_layers * (self.nv + 2) * su * 2, (self.nv + 2) * su * 2, su * 2, 2, 1)
+        if stack.dtype != self.stack_dtype or tuple(stack.shape) != shape:
+            raise ValueError("stack dtype/shape does not match the plan")
+        if tuple(stack.stride()) != strides:
+            if not stack.is_contiguous():
+                raise ValueError("stack layout does not match the plan")
+            padded = torch.zeros((dir_count, self.nz_layers, self.nv + 2, su, 2), dtype=stack.dtype,
+                                 device=stack.device)
+            padded[:, :, :, :self.nu + 1, :] = stack
+            stack = padded
         _abi.recon_backproject(self.plan, stack.data_ptr(), dir_begin, dir_count, volume.data_ptr(),
                                int(bool(accumulate)), self.workspace.data_ptr(), self.ws_bytes, self._stream(stream))
         return volume

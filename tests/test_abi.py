@@ -140,8 +140,8 @@ def test_null_arguments_are_errors_not_crashes(lib):
 
 
 def test_error_strings(lib):
-    texts = {_abi.recon_error_string(c) for c in (0, -1, -2, -3, -4, -5, -6, -7)}
-    assert len(texts) == 8 and "unknown status" not in texts
+    texts = {_abi.recon_error_string(c) for c in (0, -1, -2, -3, -4, -5, -6, -7, -8)}
+    assert len(texts) == 9 and "unknown status" not in texts
 
 
 def test_learned_filter_without_weights_is_its_own_error(lib):

@@ -128,7 +128,7 @@ def _stage_b_case(grid, nu, nv, nzl, D, seed, start=0.1, span=math.pi, axis=None
     ((64, 64, 64), 64, 64, 96, 12, None),       # thin layers: staged boxes overflow to direct loads
 ], ids=["y-half", "y-64", "y-tall", "y-rows-outside", "y-rows-outside-half", "y-1", "tilted", "tilted-2",
         "y-thin-layers"])
-@pytest.mark.parametrize("bp_kernel", ["direct", "staged"])
+@pytest.mark.parametrize("bp_kernel", ["direct", "staged", "tma"])
 def test_stage_b_backprojection_matches_oracle(grid, nu, nv, nzl, D, axis, bp_kernel):
     got, ref = _stage_b_case(grid, nu, nv, nzl, D, seed=sum(grid) + D, axis=axis, bp_kernel=bp_kernel)
     assert rel_l2(got, ref) <= TOL_F32
@@ -144,10 +144,12 @@ def test_stage_b_backprojection_matches_oracle(grid, nu, nv, nzl, D, axis, bp_ke
     ((20, 20, 20), 24, 24, 1, 4, (0.2, 1.0, 0.1)),   # one layer: the blend is that layer
     ((64, 64, 64), 64, 64, 96, 12, (0.1, 1.0, 0.3)),
 ], ids=["y", "y-tall", "tilted", "tilted-2", "one-layer", "thin-layers"])
-def test_stage_b_layer_blend_matches_oracle(grid, nu, nv, nzl, D, axis):
+@pytest.mark.parametrize("bp_kernel", ["auto", "tma"])
+def test_stage_b_layer_blend_matches_oracle(grid, nu, nv, nzl, D, axis, bp_kernel):
     """The blend of the two layers whose centres bracket each voxel's depth (exact 2^-24
-    weights on both sides), voxel by voxel."""
-    got, ref = _stage_b_case(grid, nu, nv, nzl, D, seed=sum(grid) + 3 * D, axis=axis, interp="linear")
+    weights on both sides), voxel by voxel, in the general kernel and the TMA-staged one."""
+    got, ref = _stage_b_case(grid, nu, nv, nzl, D, seed=sum(grid) + 3 * D, axis=axis, interp="linear",
+                             bp_kernel=bp_kernel)
     assert rel_l2(got, ref) <= TOL_F32
     assert np.max(np.abs(got - ref)) <= 1e-4 * max(np.max(np.abs(ref)), 1.0)
 
