@@ -30,7 +30,6 @@ namespace fft16 {
 using fft::cadd;
 using fft::cmul;
 using fft::csub;
-using fft::mul_mi;
 
 __host__ __device__ constexpr int pad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int buffer_len(int P) { return P + P / 16; }
@@ -51,19 +50,21 @@ __device__ __forceinline__ void dft16(float2* v) {
   constexpr float h = 0.70710678118654752f;   // 1/sqrt(2)
   constexpr float sg = INV ? 1.f : -1.f;      // sign of the twiddle angle
 #pragma unroll
-  for (int a = 0; a < 4; ++a) fft::dft4<INV>(v[a], v[a + 4], v[a + 8], v[a + 12]);
+  for (int a = 0; a < 4; ++a) fft::dft4_packed<INV>(v[a], v[a + 4], v[a + 8], v[a + 12]);
   // column a now holds k1 = 0..3 at v[a], v[a+4], v[a+8], v[a+12]
   v[1 + 4] = cmulc(v[1 + 4], c1, sg * s1);     // W^1
   v[1 + 8] = cmulc(v[1 + 8], h, sg * h);       // W^2
   v[1 + 12] = cmulc(v[1 + 12], s1, sg * c1);   // W^3
   v[2 + 4] = cmulc(v[2 + 4], h, sg * h);       // W^2
-  v[2 + 8] = mul_mi<INV>(v[2 + 8]);            // W^4
+  // W^4 = mul_mi on v[2 + 8], applied inside the k1 = 2 length-4 DFT below
   v[2 + 12] = cmulc(v[2 + 12], -h, sg * h);    // W^6
   v[3 + 4] = cmulc(v[3 + 4], s1, sg * c1);     // W^3
   v[3 + 8] = cmulc(v[3 + 8], -h, sg * h);      // W^6
   v[3 + 12] = cmulc(v[3 + 12], -c1, -sg * s1); // W^9
-#pragma unroll
-  for (int k1 = 0; k1 < 4; ++k1) fft::dft4<INV>(v[4 * k1], v[4 * k1 + 1], v[4 * k1 + 2], v[4 * k1 + 3]);
+  fft::dft4_packed<INV>(v[0], v[1], v[2], v[3]);
+  fft::dft4_packed<INV>(v[4], v[5], v[6], v[7]);
+  fft::dft4_packed_cmi<INV>(v[8], v[9], v[10], v[11]);
+  fft::dft4_packed<INV>(v[12], v[13], v[14], v[15]);
   // v[4 k1 + k2] holds X[k1 + 4 k2]: transpose the 4 x 4 index
   float2 t[16];
 #pragma unroll
@@ -77,6 +78,8 @@ __device__ __forceinline__ void dft16(float2* v) {
 template <int R, bool INV>
 __device__ __forceinline__ void dftR(float2* v) {
   if constexpr (R == 16) dft16<INV>(v);
+  else if constexpr (R == 8) fft::dft8_packed<INV>(v);
+  else if constexpr (R == 4) fft::dft4_packed<INV>(v[0], v[1], v[2], v[3]);
   else fft::dftR<R, INV>(v);
 }
 

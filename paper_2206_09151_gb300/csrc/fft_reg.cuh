@@ -23,10 +23,26 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 }
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// The same as one packed FP32x2 instruction each (sm_100 family): each half is rounded as
+// its scalar add, so the bits are those of cadd / csub (a - b as the fused b * (-1) + a,
+// one rounding of the exact difference).  Used by the 16-value FFT; in the 8-value one,
+// held to 80 registers, the register pairs they need measured slower.
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 // multiply by -i (forward) or +i (inverse)
 template <bool INV>
 __device__ __forceinline__ float2 mul_mi(float2 a) {
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+// t + mul_mi(u) and t - mul_mi(u), written out per component (scalar adds: a packed add
+// would first have to build the swapped, negated pair)
+template <bool INV>
+__device__ __forceinline__ float2 add_mi(float2 t, float2 u) {
+  return INV ? make_float2(t.x - u.y, t.y + u.x) : make_float2(t.x + u.y, t.y - u.x);
+}
+template <bool INV>
+__device__ __forceinline__ float2 sub_mi(float2 t, float2 u) {
+  return INV ? make_float2(t.x + u.y, t.y - u.x) : make_float2(t.x - u.y, t.y + u.x);
 }
 
 // Exchange-buffer index of element i: bits 0-3 XORed with bits 3-6, a permutation of
@@ -56,6 +72,27 @@ __device__ __forceinline__ void dft4(float2& a, float2& b, float2& c, float2& d)
   d = csub(t1, t3);
 }
 
+// The length-4 DFT with packed adds (the same bits): the terms multiplied by -+i are
+// combined per component, since a packed add would first have to build the swapped pair.
+template <bool INV>
+__device__ __forceinline__ void dft4_packed(float2& a, float2& b, float2& c, float2& d) {
+  const float2 t0 = padd(a, c), t1 = psub(a, c), t2 = padd(b, d), u = psub(b, d);
+  a = padd(t0, t2);
+  c = psub(t0, t2);
+  b = add_mi<INV>(t1, u);  // t1 + mul_mi(u)
+  d = sub_mi<INV>(t1, u);
+}
+
+// dft4_packed of (a, b, mul_mi(c), d), without forming mul_mi(c)
+template <bool INV>
+__device__ __forceinline__ void dft4_packed_cmi(float2& a, float2& b, float2& c, float2& d) {
+  const float2 t0 = add_mi<INV>(a, c), t1 = sub_mi<INV>(a, c), t2 = padd(b, d), u = psub(b, d);
+  a = padd(t0, t2);
+  c = psub(t0, t2);
+  b = add_mi<INV>(t1, u);
+  d = sub_mi<INV>(t1, u);
+}
+
 template <bool INV>
 __device__ __forceinline__ void dft4(float2* v) {
   dft4<INV>(v[0], v[1], v[2], v[3]);
@@ -80,6 +117,26 @@ __device__ __forceinline__ void dft8(float2* v) {
   v[6] = csub(e2, o2);
   v[3] = cadd(e3, o3);
   v[7] = csub(e3, o3);
+}
+
+// dft8 with packed adds (the same bits)
+template <bool INV>
+__device__ __forceinline__ void dft8_packed(float2* v) {
+  constexpr float h = 0.70710678118654752f;  // 1/sqrt(2)
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4_packed<INV>(e0, e1, e2, e3);
+  dft4_packed<INV>(o0, o1, o2, o3);
+  o1 = INV ? make_float2(h * (o1.x - o1.y), h * (o1.x + o1.y)) : make_float2(h * (o1.x + o1.y), h * (o1.y - o1.x));
+  o3 = INV ? make_float2(-h * (o3.x + o3.y), h * (o3.x - o3.y)) : make_float2(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+  v[0] = padd(e0, o0);
+  v[4] = psub(e0, o0);
+  v[1] = padd(e1, o1);
+  v[5] = psub(e1, o1);
+  v[2] = add_mi<INV>(e2, o2);  // o2 times W8^2 = mul_mi
+  v[6] = sub_mi<INV>(e2, o2);
+  v[3] = padd(e3, o3);
+  v[7] = psub(e3, o3);
 }
 
 template <int R, bool INV>
