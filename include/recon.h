@@ -155,6 +155,8 @@ typedef struct {
                        network's eps, a per-view noise-to-signal power (Wiener), is divided by
                        it, since the reconstruction averages that many independent views;
                        0 or 1 = a single view's eps                                          */
+  int bp_tile_z;    /* TMA-staged backprojection: the voxel tile is 16 x 16 x bp_tile_z, 8 or
+                       16; 0 = 16 (measured faster on the slab; the autotuner can time 8)   */
 } recon_options;
 
 /* Fills *opts with defaults: sigma 0, eps 0.1 (the value of Sec. 3), cs 0, Tikhonov

@@ -55,7 +55,8 @@ class ReconOptions(ctypes.Structure):
                 ("ramp_mode", ctypes.c_int), ("accumulate", ctypes.c_int), ("dir_block", ctypes.c_int),
                 ("mlp_weights", ctypes.POINTER(ctypes.c_float)), ("nsr", ctypes.c_double),
                 ("stage_block", ctypes.c_int), ("bp_kernel", ctypes.c_int), ("check_finite", ctypes.c_int),
-                ("layer_interp", ctypes.c_int), ("bp_warp", ctypes.c_int), ("mlp_views", ctypes.c_double)]
+                ("layer_interp", ctypes.c_int), ("bp_warp", ctypes.c_int), ("mlp_views", ctypes.c_double),
+                ("bp_tile_z", ctypes.c_int)]
 
 
 class ReconTrainCfg(ctypes.Structure):

@@ -3,12 +3,14 @@
 The kernels' voxel tiles and FFT groups are fixed at compile time for sm_103a; what
 varies per problem is how many directions share one block of layer stacks (``dir_block``
 of a run: a larger block means fewer volume read-modify-writes but a larger workspace),
-how a warp of the general backprojection covers its tile's voxel columns (``bp_warp``:
-8 x 4, 16 x 2 or 32 x 1, which sets how many detector rows and cache lines one gather
-touches for the scan's view orientations), and how many directions a batch round holds.
-Each ``tune_*`` times ``recon_run`` (or a batch run) for every candidate with CUDA events
-after a warm-up run and returns the fastest; ``tune_dir_block`` and ``tune_bp_warp`` cache
-their result per problem shape in a JSON file when ``cache`` is given."""
+how a warp of the direct general backprojection covers its tile's voxel columns
+(``bp_warp``: 8 x 4, 16 x 2 or 32 x 1, which sets how many detector rows and cache lines one
+gather touches for the scan's view orientations), the voxel tile of the TMA-staged
+backprojection (``bp_tile_z``: 16 x 16 x 8 or 16 x 16 x 16), and how many directions a
+batch round holds.  Each ``tune_*`` times ``recon_run`` (or a batch run) for every
+candidate with CUDA events after a warm-up run and returns the fastest; ``tune_dir_block``,
+``tune_bp_warp`` and ``tune_bp_tile`` cache their result per problem shape in a JSON file
+when ``cache`` is given."""
 from __future__ import annotations
 
 import json
@@ -98,6 +100,38 @@ def tune_bp_warp(rot, nu: int, nv: int, grid, images: torch.Tensor, *, nz_layers
         torch.cuda.empty_cache()
     best = min(timings, key=timings.get)
     out = {"bp_warp": best, "ms": {str(k): v for k, v in timings.items()}}
+    if cache:
+        table = json.load(open(cache)) if os.path.exists(cache) else {}
+        table[key] = out
+        with open(cache, "w") as f:
+            json.dump(table, f, indent=1)
+    return out
+
+
+def tune_bp_tile(rot, nu: int, nv: int, grid, images: torch.Tensor, *, nz_layers: int, candidates=(8, 16),
+                 repeats: int = 3, cache: str | None = None, **plan_kw) -> dict:
+    """Fastest voxel-tile depth of the TMA-staged backprojection (16 x 16 x 8 or 16 x 16 x 16
+    tiles): {"bp_tile_z": best, "ms": {...}}.  Timed with ``bp_kernel="tma"``; a deeper
+    tile shares each direction's set-up over more voxels, a shallower one wastes less at
+    the volume's z edge and stages smaller boxes."""
+    plan_kw = dict(plan_kw, bp_kernel="tma")
+    key = _key(rot, nu, nv, grid, nz_layers, plan_kw) + "|bp_tile_z"
+    if cache and os.path.exists(cache):
+        table = json.load(open(cache))
+        if key in table:
+            return table[key]
+    timings = {}
+    vol = None
+    for c in candidates:
+        r = Reconstructor(rot, nu, nv, grid, nz_layers=nz_layers, bp_tile_z=c, **plan_kw)
+        if vol is None:
+            vol = r.new_volume()
+        timings[c] = _time(lambda: r.run(images, vol), repeats)
+        r.close()
+        del r
+        torch.cuda.empty_cache()
+    best = min(timings, key=timings.get)
+    out = {"bp_tile_z": best, "ms": {str(k): v for k, v in timings.items()}}
     if cache:
         table = json.load(open(cache)) if os.path.exists(cache) else {}
         table[key] = out

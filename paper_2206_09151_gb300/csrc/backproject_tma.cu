@@ -47,13 +47,9 @@ namespace {
 #ifndef RECON_TMA_ODD_PITCH
 #define RECON_TMA_ODD_PITCH 1
 #endif
-// voxels along z per thread (the tile is 16 x 16 x RECON_TMA_TILE_Z)
-#ifndef RECON_TMA_TILE_Z
-#define RECON_TMA_TILE_Z 16
-#endif
-
-constexpr int kMX = 16, kMY = 16, kMZ = RECON_TMA_TILE_Z;
-static_assert(kMZ % 2 == 0 && kMZ >= 2 && kMZ <= 32, "a thread's voxels along z are processed in pairs");
+// The tile is 16 x 16 x TZ voxels, TZ (voxels along z per thread) a run-time choice of
+// the plan: 16 (the default, measured faster on the slab) or 8.
+constexpr int kMX = 16, kMY = 16;
 constexpr int kConsumerWarps = 8;
 constexpr int kThreads = (kConsumerWarps + 1) * 32;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded waits: 2 s
@@ -158,7 +154,7 @@ struct TmaArgs {
   int stall;             // diagnostic: the producer issues nothing, so every consumer wait runs out
 };
 
-template <typename ST, bool LIN>
+template <typename ST, bool LIN, int kMZ>
 __global__ void __launch_bounds__(kThreads, RECON_TMA_MIN_CTAS) k_backproject_tma(const __grid_constant__ CUtensorMap map,
                                                                  const TmaArgs g) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -427,10 +423,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
-template <typename ST, bool LIN>
+template <typename ST, bool LIN, int kMZ>
 cudaError_t launch_tma_t(const BackprojConst& c, const TmaBox& box, const DirParams* dirs, const void* stack,
                          int dir_begin, int dir_count, float* volume, int accumulate, unsigned int* status,
                          cudaStream_t stream, int stall = 0) {
+  static_assert(kMZ == 8 || kMZ == 16, "tile depth 8 or 16");
   PFN_cuTensorMapEncodeTiled_v12000 enc = encode_tiled();
   if (!enc) return cudaErrorNotSupported;
   constexpr size_t es = sizeof(ST);
@@ -471,24 +468,40 @@ cudaError_t launch_tma_t(const BackprojConst& c, const TmaBox& box, const DirPar
   g.box_bytes = (uint32_t)((size_t)box.W * box.H * box.L * es);
   g.stall = stall;
   const size_t smem = (size_t)box.stages * (box.stage_bytes + 16 + sizeof(Rec));
-  cudaError_t e = cudaFuncSetAttribute(k_backproject_tma<ST, LIN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(k_backproject_tma<ST, LIN, kMZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backproject_tma<ST, LIN>, kThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_backproject_tma<ST, LIN, kMZ>, kThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
   const long long ctas = (long long)device_sm_count() * per_sm;
   const unsigned grid = (unsigned)(ctas < tiles ? ctas : tiles);
-  k_backproject_tma<ST, LIN><<<grid, kThreads, smem, stream>>>(map, g);
+  k_backproject_tma<ST, LIN, kMZ><<<grid, kThreads, smem, stream>>>(map, g);
   return cudaGetLastError();
+}
+
+template <int kMZ>
+cudaError_t launch_tz(const BackprojConst& c, const TmaBox& box, const DirParams* dirs, const void* stack, int dir_begin,
+                      int dir_count, float* volume, int accumulate, unsigned int* status, cudaStream_t stream) {
+  if (c.stack_bf16)
+    return c.layer_linear ? launch_tma_t<__nv_bfloat162, true, kMZ>(c, box, dirs, stack, dir_begin, dir_count, volume,
+                                                                    accumulate, status, stream)
+                          : launch_tma_t<__nv_bfloat162, false, kMZ>(c, box, dirs, stack, dir_begin, dir_count,
+                                                                     volume, accumulate, status, stream);
+  return c.layer_linear ? launch_tma_t<float2, true, kMZ>(c, box, dirs, stack, dir_begin, dir_count, volume,
+                                                          accumulate, status, stream)
+                        : launch_tma_t<float2, false, kMZ>(c, box, dirs, stack, dir_begin, dir_count, volume,
+                                                           accumulate, status, stream);
 }
 
 }  // namespace
 
-TmaBox tma_box_for(const BackprojConst& c, const DirParams* dirs, int n_dirs) {
+TmaBox tma_box_for(const BackprojConst& c, const DirParams* dirs, int n_dirs, int tile_z) {
   TmaBox b{};
-  const long long ext[3] = {kMX - 1, kMY - 1, kMZ - 1};
+  if (tile_z != 8 && tile_z != 16) return b;  // ok = 0
+  b.tile_z = tile_z;
+  const long long ext[3] = {kMX - 1, kMY - 1, tile_z - 1};
   long long W = 4, H = 2, L = 1;
   for (int n = 0; n < n_dirs; ++n) {
     const DirParams& p = dirs[n];
@@ -533,15 +546,8 @@ cudaError_t launch_backproject_tma(const BackprojConst& c, const TmaBox& box, co
                                    cudaStream_t stream) {
   if (dir_count <= 0 || c.nx <= 0 || c.ny <= 0 || c.nz <= 0) return cudaSuccess;
   if (!box.ok) return cudaErrorInvalidValue;
-  if (c.stack_bf16)
-    return c.layer_linear ? launch_tma_t<__nv_bfloat162, true>(c, box, dirs, stack, dir_begin, dir_count, volume,
-                                                               accumulate, status, stream)
-                          : launch_tma_t<__nv_bfloat162, false>(c, box, dirs, stack, dir_begin, dir_count, volume,
-                                                                accumulate, status, stream);
-  return c.layer_linear ? launch_tma_t<float2, true>(c, box, dirs, stack, dir_begin, dir_count, volume, accumulate,
-                                                     status, stream)
-                        : launch_tma_t<float2, false>(c, box, dirs, stack, dir_begin, dir_count, volume, accumulate,
-                                                      status, stream);
+  if (box.tile_z == 8) return launch_tz<8>(c, box, dirs, stack, dir_begin, dir_count, volume, accumulate, status, stream);
+  return launch_tz<16>(c, box, dirs, stack, dir_begin, dir_count, volume, accumulate, status, stream);
 }
 
 cudaError_t launch_tma_wait_probe(void* buf, size_t buf_bytes, unsigned int* status, cudaStream_t stream) {
@@ -565,7 +571,8 @@ cudaError_t launch_tma_wait_probe(void* buf, size_t buf_bytes, unsigned int* sta
   b.stage_bytes = 128;
   b.ok = 1;
   float* vol = reinterpret_cast<float*>(static_cast<char*>(buf) + 2048);
-  return launch_tma_t<__nv_bfloat162, false>(c, b, nullptr, buf, 0, 1, vol, 0, status, stream, 1);
+  b.tile_z = 16;
+  return launch_tma_t<__nv_bfloat162, false, 16>(c, b, nullptr, buf, 0, 1, vol, 0, status, stream, 1);
 }
 
 }  // namespace recon

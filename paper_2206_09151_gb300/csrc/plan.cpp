@@ -139,6 +139,7 @@ void recon_default_options(recon_options* o) {
   o->check_finite = 0;
   o->layer_interp = RECON_LAYER_NEAREST;
   o->mlp_views = 0.0;
+  o->bp_tile_z = 0;
   o->bp_warp = 0;
 }
 
@@ -201,6 +202,8 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
     return fail(RECON_E_INVALID_ARG, "recon_plan: bp_warp must be 0, 8, 16 or 32");
   if (!(o.mlp_views >= 0.0) || !std::isfinite(o.mlp_views))
     return fail(RECON_E_INVALID_ARG, "recon_plan: mlp_views must be >= 0");
+  if (o.bp_tile_z != 0 && o.bp_tile_z != 8 && o.bp_tile_z != 16)
+    return fail(RECON_E_INVALID_ARG, "recon_plan: bp_tile_z must be 0, 8 or 16");
   if (o.layer_interp != RECON_LAYER_NEAREST && o.layer_interp != RECON_LAYER_LINEAR)
     return fail(RECON_E_INVALID_ARG, "recon_plan: unknown layer_interp");
   if (o.input_mode != RECON_INPUT_INTENSITY && o.input_mode != RECON_INPUT_CONTRAST)
@@ -488,7 +491,7 @@ static int plan_create(const recon_geometry* geom, double lambda, double delta, 
   // axis along y, or the layer blend), measured faster on sm_103a; on request for any geometry.
   const bool general = !cb.axis_y || cb.layer_linear;
   if (o.bp_kernel == RECON_BP_TMA || (o.bp_kernel == RECON_BP_AUTO && general && D > 0)) {
-    p->tma = recon::tma_box_for(cb, p->dirs.data(), D);
+    p->tma = recon::tma_box_for(cb, p->dirs.data(), D, o.bp_tile_z ? o.bp_tile_z : 16);
     if (!p->tma.ok && o.bp_kernel == RECON_BP_TMA) {
       delete p;
       return fail(RECON_E_UNSUPPORTED_SIZE,

@@ -150,8 +150,9 @@ struct TmaBox {
   int stages;         // shared-memory ring depth
   size_t stage_bytes; // W H L entries rounded up to 128 bytes
   int ok;             // 0: the box is too large for the kernel (it then cannot be used)
+  int tile_z;         // voxel tile 16 x 16 x tile_z (8 or 16)
 };
-TmaBox tma_box_for(const BackprojConst& c, const DirParams* dirs, int n_dirs);
+TmaBox tma_box_for(const BackprojConst& c, const DirParams* dirs, int n_dirs, int tile_z);
 // status: device word; bit 0 = a bounded wait ran out, bit 1 = a footprint outside its box
 cudaError_t launch_backproject_tma(const BackprojConst& c, const TmaBox& box, const DirParams* dirs, const void* stack,
                                    int dir_begin, int dir_count, float* volume, int accumulate, unsigned int* status,

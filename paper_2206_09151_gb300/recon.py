@@ -32,7 +32,8 @@ class Reconstructor:
                  input_mode: str = "intensity", stack_dtype: str = "f32", accumulate: bool = False,
                  dir_block: int = 0, ramp: str = "single_axis", mlp_weights=None, nsr: float = 0.0,
                  stage_block: int = 0, bp_kernel: str = "auto", check_finite: bool = False,
-                 layer_interp: str = "nearest", mlp_views: float = 0.0, bp_warp: int = 0, device=None,
+                 layer_interp: str = "nearest", mlp_views: float = 0.0, bp_warp: int = 0, bp_tile_z: int = 0,
+                 device=None,
                  allocate: bool = True):
         o = _abi.recon_default_options()
         o.sigma, o.eps, o.cs = float(sigma), float(eps), float(cs)
@@ -45,6 +46,7 @@ class Reconstructor:
         o.check_finite = int(bool(check_finite))
         o.layer_interp = _LAYER_INTERP[layer_interp]
         o.mlp_views = float(mlp_views)
+        o.bp_tile_z = int(bp_tile_z)
         o.bp_warp = int(bp_warp)
         self._weights = None
         if mlp_weights is not None:

@@ -169,6 +169,35 @@ def test_check_finite_option_is_validated(lib):
     _abi.recon_destroy(_plan(opts=o))
 
 
+def test_backprojection_kernel_choice_is_reported_and_validated(lib):
+    """AUTO resolves to the single-axis direct kernel for a scan about y with the nearest
+    layer, to the TMA-staged kernel for a tilted axis or the layer blend; the tile depth of
+    the TMA kernel is 0, 8 or 16."""
+    rot_y = ph.single_axis_rotations(12)
+    rot_t = ph.single_axis_rotations(12, axis=(0.3, 1.0, 0.2))
+    for rot, interp, want in ((rot_y, _abi.RECON_LAYER_NEAREST, _abi.RECON_BP_DIRECT),
+                              (rot_t, _abi.RECON_LAYER_NEAREST, _abi.RECON_BP_TMA),
+                              (rot_y, _abi.RECON_LAYER_LINEAR, _abi.RECON_BP_TMA)):
+        o = _abi.recon_default_options()
+        o.layer_interp = interp
+        p = _plan(rot=rot, opts=o)
+        assert _abi.recon_plan_bp_kernel(p) == want
+        _abi.recon_destroy(p)
+    for bad in (4, 12, -1, 32):
+        o = _abi.recon_default_options()
+        o.bp_tile_z = bad
+        with pytest.raises(_abi.ReconError) as e:
+            _plan(rot=rot_t, opts=o)
+        assert e.value.code == _abi.RECON_E_INVALID_ARG
+    for ok in (0, 8, 16):
+        o = _abi.recon_default_options()
+        o.bp_tile_z = ok
+        o.bp_kernel = _abi.RECON_BP_TMA
+        p = _plan(rot=rot_y, opts=o)
+        assert _abi.recon_plan_bp_kernel(p) == _abi.RECON_BP_TMA
+        _abi.recon_destroy(p)
+
+
 def test_depth_of_field_report_and_layer_count(lib):
     """DOF = Delta^2 / (2 lambda) (Sec. 1).  A 64^3 single-axis scan with Delta = 1 nm,
     lambda = 0.1 nm: DOF = 5 nm; the bounding-box extent along a beam at angle t in the

@@ -134,3 +134,18 @@ def test_tma_wait_limit_reports_and_leaves_the_context_usable():
     a = _run(rot, nu, grid, img, kw, nz_layers=3, bp_kernel="direct")
     b = _run(rot, nu, grid, img, kw, nz_layers=3, bp_kernel="tma")
     assert rel_l2(b, a) <= TOL_F32
+
+
+def test_tile_depths_agree_and_the_tuner_picks_one():
+    """16 x 16 x 8 and 16 x 16 x 16 tiles: both match the oracle and each other to rounding
+    (the box-local origins differ), and the autotuner returns one of the timed depths."""
+    from paper_2206_09151_gb300.autotune import tune_bp_tile
+    rot, nu, grid, img, kw = _cone_case()
+    ref = _oracle("nearest")
+    vols = {}
+    for tz in (8, 16):
+        vols[tz] = _run(rot, nu, grid, img, kw, nz_layers=7, bp_kernel="tma", bp_tile_z=tz)
+        assert rel_l2(vols[tz], ref) <= TOL_F32, (tz, rel_l2(vols[tz], ref))
+    assert rel_l2(vols[8], vols[16]) <= TOL_F32
+    out = tune_bp_tile(rot, nu, nu, grid, img, nz_layers=7, candidates=(8, 16), repeats=2, **kw)
+    assert out["bp_tile_z"] in (8, 16) and set(out["ms"]) == {"8", "16"}
