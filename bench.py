@@ -55,21 +55,20 @@ DEFAULT_STACK = {"mid": "f32", "small": "f32", "learned": "bf16", "slab": "bf16"
 
 # DRAM traffic per launch (bytes) from ncu captures, keyed by kernel and workload and
 # valid only for the kernel source they were taken on (sha256 of the .cu file).
-# Taken from a --set full capture of one 40-direction launch, scaled by 120/40 to the
-# bench's 120-direction blocks. The stack read grows in proportion; the backprojection's
-# volume read-modify-write does not, and its figure overstates that part.
 NCU_TRAFFIC: dict = {
-    ("k_cols", "mid", "f32"): {"bytes_per_launch": (21.393664e6 + 612.677376e6) * 3, "src": "d48e06ae03fad5cf"},
-    ("k_cols", "mid", "bf16"): {"bytes_per_launch": (21.393664e6 + 612.677376e6) * 3, "src": "d48e06ae03fad5cf"},
-    ("k_rows_inv", "mid", "f32"): {"bytes_per_launch": (673.865728e6 + 633.4848e6) * 3, "src": "d48e06ae03fad5cf"},
-    ("k_backproject", "mid", "f32"): {"bytes_per_launch": (612.676608e6 + 59.275520e6) * 3, "src": "40408219a6e58e02"},
+    # mid (float32): one 40-direction launch each, scaled by 120/40 to the bench's blocks (the
+    # backprojection's volume read-modify-write does not scale; its figure overstates it)
+    ("k_cols", "mid", "f32"): {"bytes_per_launch": (21.161984e6 + 613.005568e6) * 3, "src": "91b6d6728cadad50"},
+    ("k_rows_inv", "mid", "f32"): {"bytes_per_launch": (683.59168e6 + 645.783808e6) * 3, "src": "91b6d6728cadad50"},
+    ("k_backproject", "mid", "f32"): {"bytes_per_launch": (617.094656e6 + 59.883008e6) * 3,
+                                      "src": "b7ee0b8780a4373d"},
     # slab (bf16 stack): the column kernel from one 3-direction sub-block launch (the bench's
     # launch size); the TMA-staged backprojection from a 6-direction launch, its reads scaled
     # by 25/6 to the bench's 25-direction blocks (the stack boxes grow with the directions),
     # plus the volume read of an accumulating block and the volume write (1.07 GB each)
     ("k_cols", "slab", "bf16"): {"bytes_per_launch": 56.096512e6 + 1.551087e9, "src": "91b6d6728cadad50"},
-    ("k_backproject", "slab", "bf16"): {"bytes_per_launch": 3.058623e9 * 25 / 6 + 1.073742e9 + 1.055004e9,
-                                        "src": "cb17e905eba110ad"},
+    ("k_backproject", "slab", "bf16"): {"bytes_per_launch": 3.059654e9 * 25 / 6 + 1.073742e9 + 1.055155e9,
+                                        "src": "f76a56888e3e5455"},
 }
 
 
