@@ -255,8 +255,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_cols(const float2* __restrict__
     fft::block_fft<P, true>(x, buf, tw, j, gsync);
     if (ok) {
       float2* out = Tn + ((size_t)k * c.half + col) * c.nv;
+      // nv <= P/2: elements s >= 4 (v >= P/2) are never kept (their last butterflies drop)
 #pragma unroll
-      for (int s = 0; s < 8; ++s) {
+      for (int s = 0; s < 4; ++s) {
         const int v = j + s * TT;
         if (v < c.nv) out[v] = x[s];
       }
@@ -328,9 +329,12 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(const float2* __restrict_
   fft::block_fft<P, true>(x, buf, tw, j);
   // rows v0 (real part) and v0 + 1 (imaginary part) at u = j + s*TT; pair them with
   // their right-hand neighbours through the (now free) exchange buffer
+  // nu <= P/2 (P is at least twice the image size): the pairs of columns cc <= nu read
+  // u < P/2 only, i.e. x[s] for s < 4, so the last pass's butterflies feeding s >= 4 drop;
+  // column P/2 (s = 4, thread 0, when nu = P/2) is (Y[nu - 1], 0)
   __syncthreads();
 #pragma unroll
-  for (int s = 0; s < 8; ++s) buf[padded(j + s * TT)] = x[s];
+  for (int s = 0; s < 4; ++s) buf[padded(j + s * TT)] = x[s];
   __syncthreads();
   PairT* Lk = stack + ((size_t)n * c.nz_layers + k) * c.layer_elems;
   const int sp = c.su;
@@ -339,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) k_rows_inv(const float2* __restrict_
     PairT* r1 = Lk + (size_t)(v0 + 1) * sp;
     PairT* r2 = r1 + sp;
 #pragma unroll
-    for (int s = 0; s < 8; ++s) {
+    for (int s = 0; s < 5; ++s) {
       const int cc = j + s * TT;  // pair column: (Y[cc - 1], Y[cc])
       if (cc <= c.nu) {
         const float2 left = cc >= 1 ? buf[padded(cc - 1)] : make_float2(0.f, 0.f);
@@ -495,8 +499,10 @@ __global__ void __launch_bounds__(kThreads16, FILT == 3 ? 1 : 2) k_cols16(const 
     fft16::group_fft_db<P, true>(x, buf0, buf1, tw, j, gsync);
     if (ok) {
       float2* out = Tn + ((size_t)k * c.half + col) * c.nv;
+      // nv <= P/2 (P is at least twice the image size): elements s >= 8 (v >= P/2) are
+      // never kept, so the last pass's butterflies that only feed them are dropped
 #pragma unroll
-      for (int s = 0; s < 16; ++s) {
+      for (int s = 0; s < 8; ++s) {
         const int v = j + s * TT;
         if (v < c.nv) out[v] = x[s];
       }
@@ -603,9 +609,12 @@ __global__ void __launch_bounds__(rows16_threads<P>(), 2) k_rows_inv16(const flo
   gsync();  // the last pass's reads of the buffer are done
   const int lane = threadIdx.x & 31, wg = j >> 5;
   float2* edge = buf;  // [TT / 32][16]
+  // nu <= P/2 (P is at least twice the image size): the pair columns cc <= nu need
+  // x[s] for s < 8 only (and column P/2, when nu = P/2, the left value x[7] of the last
+  // thread and a zero right value), so the last pass's butterflies feeding s >= 8 drop
   if (lane == 31) {
 #pragma unroll
-    for (int s = 0; s < 16; ++s) edge[wg * 16 + s] = x[s];
+    for (int s = 0; s < 8; ++s) edge[wg * 16 + s] = x[s];
   }
   gsync();
   PairT* Lk = stack + ((size_t)n * c.nz_layers + k) * c.layer_elems;
@@ -614,7 +623,7 @@ __global__ void __launch_bounds__(rows16_threads<P>(), 2) k_rows_inv16(const flo
   PairT* r1 = Lk + (size_t)(v0 + 1) * sp;
   PairT* r2 = r1 + sp;
 #pragma unroll
-  for (int s = 0; s < 16; ++s) {
+  for (int s = 0; s < 8; ++s) {
     if (s * TT > c.nu) break;  // the same for every thread of the group
     const int cc = j + s * TT;  // pair column: (Y[cc - 1], Y[cc])
     float2 left = make_float2(__shfl_up_sync(0xffffffffu, x[s].x, 1), __shfl_up_sync(0xffffffffu, x[s].y, 1));
@@ -627,6 +636,11 @@ __global__ void __launch_bounds__(rows16_threads<P>(), 2) k_rows_inv16(const flo
       r1[cc] = make_pair<PairT>(left.x, right.x);
       if (two) r2[cc] = make_pair<PairT>(left.y, right.y);
     }
+  }
+  if (j == 0 && row1 && c.nu == P / 2) {  // pair column P/2 = nu: (Y[nu - 1], 0)
+    const float2 left = edge[(TT / 32 - 1) * 16 + 7];
+    r1[P / 2] = make_pair<PairT>(left.x, 0.f);
+    if (two) r2[P / 2] = make_pair<PairT>(left.y, 0.f);
   }
   if (blockIdx.x == 0)  // top border row
     for (int i = threadIdx.x; i < sp; i += NTH) Lk[i] = make_pair<PairT>(0.f, 0.f);
