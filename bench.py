@@ -58,15 +58,14 @@ DEFAULT_STACK = {"mid": "f32", "small": "f32", "learned": "bf16", "slab": "bf16"
 NCU_TRAFFIC: dict = {
     # mid (float32): one 40-direction launch each, scaled by 120/40 to the bench's blocks (the
     # backprojection's volume read-modify-write does not scale; its figure overstates it)
-    ("k_cols", "mid", "f32"): {"bytes_per_launch": (21.161984e6 + 613.005568e6) * 3, "src": "91b6d6728cadad50"},
-    ("k_rows_inv", "mid", "f32"): {"bytes_per_launch": (683.59168e6 + 645.783808e6) * 3, "src": "91b6d6728cadad50"},
+    ("k_cols", "mid", "f32"): {"bytes_per_launch": (21.171456e6 + 612.15744e6) * 3, "src": "bed4d9ddf41aaddd"},
     ("k_backproject", "mid", "f32"): {"bytes_per_launch": (617.094656e6 + 59.883008e6) * 3,
                                       "src": "b7ee0b8780a4373d"},
     # slab (bf16 stack): the column kernel from one 3-direction sub-block launch (the bench's
     # launch size); the TMA-staged backprojection from a 6-direction launch, its reads scaled
     # by 25/6 to the bench's 25-direction blocks (the stack boxes grow with the directions),
     # plus the volume read of an accumulating block and the volume write (1.07 GB each)
-    ("k_cols", "slab", "bf16"): {"bytes_per_launch": 56.096512e6 + 1.551087e9, "src": "91b6d6728cadad50"},
+    ("k_cols", "slab", "bf16"): {"bytes_per_launch": 55.945984e6 + 1.550934e9, "src": "bed4d9ddf41aaddd"},
     ("k_backproject", "slab", "bf16"): {"bytes_per_launch": 3.059654e9 * 25 / 6 + 1.073742e9 + 1.055155e9,
                                         "src": "f76a56888e3e5455"},
 }
