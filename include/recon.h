@@ -193,6 +193,23 @@ int recon_workspace_size(recon_plan_t plan, size_t* bytes);
 int recon_run(recon_plan_t plan, const float* images, float* volume, void* workspace, size_t ws_bytes,
               void* stream);
 
+/* recon_run with the images in host memory, their upload overlapped with the compute:
+ * block b + 1's images are copied (cudaMemcpyAsync on a stream of the plan's own) into one
+ * of two device slots while block b is reconstructed on `stream`.
+ *   host_images host, float32 [n_dir][nv][nu]; page-locked (cudaHostAlloc / pinned) for
+ *             the copies to overlap (pageable memory works, copied without overlap); it must
+ *             stay valid until the work queued on `stream` has finished
+ *   workspace device, >= recon_run_host_workspace_size bytes (recon_workspace_size plus
+ *             two image slots of the plan's direction block), 256-byte aligned
+ * Same result as recon_run on the same images.  The plan keeps the copy stream and five
+ * events (created on the first call, on the current device), so one plan must not run
+ * recon_run_host from two threads at once.  check_finite is not supported here
+ * (RECON_E_INVALID_ARG).  Asynchronous like recon_run (including its end-of-call status read
+ * for the TMA-staged backprojection). */
+int recon_run_host_workspace_size(recon_plan_t plan, size_t* bytes);
+int recon_run_host(recon_plan_t plan, const float* host_images, float* volume, void* workspace, size_t ws_bytes,
+                   void* stream);
+
 /* Stage A alone (Sec. 2, Eq. 4-11 per layer): the layer stacks of directions
  * [dir_begin, dir_begin + dir_count), dir_count <= the plan's block size, into the
  * workspace.  *stack_out receives a device pointer into the workspace, laid out

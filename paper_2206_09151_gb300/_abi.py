@@ -94,6 +94,8 @@ def load_library(path: str = LIB_PATH):
                              ctypes.POINTER(ReconOptions), ctypes.POINTER(vp)]
     L.recon_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
     L.recon_run.argtypes = [vp, vp, vp, vp, sz, vp]
+    L.recon_run_host.argtypes = [vp, vp, vp, vp, sz, vp]
+    L.recon_run_host_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
     L.recon_filter_stage.argtypes = [vp, vp, ip, ip, vp, sz, vp, ctypes.POINTER(vp)]
     L.recon_backproject.argtypes = [vp, vp, ip, ip, vp, ip, vp, sz, vp]
     L.recon_plan_info.argtypes = [vp, ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip), ctypes.POINTER(ip)]
@@ -136,7 +138,8 @@ def load_library(path: str = LIB_PATH):
                  "recon_batch_workspace_size", "recon_batch_run", "recon_batch_run_graph", "recon_batch_destroy",
                  "recon_run_batch_workspace_size", "recon_run_batch", "recon_plan_dof", "recon_layers_for_dof",
                  "recon_plan_layers", "recon_swap_workspace_size", "recon_swap_ct", "recon_swap_phase",
-                 "recon_grid_workspace_size", "recon_grid_run", "recon_selftest_wait_limit", "recon_plan_bp_kernel"):
+                 "recon_grid_workspace_size", "recon_grid_run", "recon_selftest_wait_limit", "recon_plan_bp_kernel",
+                 "recon_run_host", "recon_run_host_workspace_size"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -266,6 +269,17 @@ def recon_layers_for_dof(rot: np.ndarray, grid, lam: float, delta: float) -> int
 
 def recon_run(plan, images_ptr: int, volume_ptr: int, ws_ptr: int, ws_bytes: int, stream: int):
     _check(load_library().recon_run(plan, images_ptr, volume_ptr, ws_ptr, ws_bytes, stream), "recon_run")
+
+
+def recon_run_host_workspace_size(plan) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().recon_run_host_workspace_size(plan, ctypes.byref(n)), "recon_run_host_workspace_size")
+    return n.value
+
+
+def recon_run_host(plan, host_images_ptr: int, volume_ptr: int, ws_ptr: int, ws_bytes: int, stream: int):
+    _check(load_library().recon_run_host(plan, host_images_ptr, volume_ptr, ws_ptr, ws_bytes, stream),
+           "recon_run_host")
 
 
 def recon_swap_workspace_size(plan) -> int:

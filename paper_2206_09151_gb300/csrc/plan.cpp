@@ -114,8 +114,21 @@ struct recon_plan_s {
   std::vector<cudaEvent_t> events;
   std::vector<int> event_kind;
   int profiled_events = 0;
+  // recon_run_host: the copy stream and its events (created on first use, per device)
+  int copy_dev = -1;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  void release_copy_stream() {
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    for (cudaEvent_t e : {ev_start, ev_ready[0], ev_ready[1], ev_free[0], ev_free[1]})
+      if (e) cudaEventDestroy(e);
+    copy_stream = nullptr;
+    ev_start = ev_ready[0] = ev_ready[1] = ev_free[0] = ev_free[1] = nullptr;
+    copy_dev = -1;
+  }
   ~recon_plan_s() {
     for (cudaEvent_t e : events) cudaEventDestroy(e);
+    release_copy_stream();
   }
 };
 
@@ -875,6 +888,99 @@ int recon_run(recon_plan_t p, const float* images, float* volume, void* workspac
   }
   if (rec) p->profiled_events = recorder.n;
   return tma_end(p, workspace, s, "recon_run");
+}
+
+// One device image slot of recon_run_host: a direction block's images.
+static size_t host_slot_bytes(recon_plan_t p) {
+  return align256(sizeof(float) * (size_t)p->db * p->nv * p->nu);
+}
+
+int recon_run_host_workspace_size(recon_plan_t p, size_t* bytes) {
+  if (!p || !bytes) return fail(RECON_E_INVALID_ARG, "recon_run_host_workspace_size: null argument");
+  *bytes = p->ws_bytes + 2 * host_slot_bytes(p);
+  return RECON_OK;
+}
+
+int recon_run_host(recon_plan_t p, const float* host_images, float* volume, void* workspace, size_t ws_bytes,
+                   void* stream) {
+  if (!p) return fail(RECON_E_INVALID_ARG, "recon_run_host: null plan");
+  const size_t nvox = (size_t)p->nx * p->ny * p->nz;
+  if (nvox > 0 && !volume) return fail(RECON_E_INVALID_ARG, "recon_run_host: null volume");
+  if (p->D > 0 && !host_images) return fail(RECON_E_INVALID_ARG, "recon_run_host: null host images");
+  if (p->opt.check_finite)
+    return fail(RECON_E_INVALID_ARG, "recon_run_host: check_finite is not supported with host images");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->D == 0 || nvox == 0) {
+    if (nvox > 0 && !p->opt.accumulate) {
+      cudaError_t e = cudaMemsetAsync(volume, 0, nvox * sizeof(float), s);
+      if (e != cudaSuccess) return cuda_fail(e, "recon_run_host: clearing the volume");
+    }
+    return RECON_OK;
+  }
+  const size_t slot = host_slot_bytes(p), need = p->ws_bytes + 2 * slot;
+  if (!workspace || ((uintptr_t)workspace & 255) != 0 || ws_bytes < need)
+    return fail(RECON_E_WORKSPACE, "recon_run_host: workspace too small or misaligned (needs " +
+                                       std::to_string(need) + " bytes)");
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_run_host: current device");
+  if (p->copy_dev != dev) {  // the copy stream and its events, on this device
+    p->release_copy_stream();
+    e = cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&p->ev_start, &p->ev_ready[0], &p->ev_ready[1], &p->ev_free[0], &p->ev_free[1]})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      p->release_copy_stream();
+      return cuda_fail(e, "recon_run_host: creating the copy stream");
+    }
+    p->copy_dev = dev;
+  }
+  const recon::Workspace w = carve(p, workspace);
+  int rc = upload_tables(p, w, s);
+  if (rc) return rc;
+  rc = tma_begin(p, workspace, s, "recon_run_host");
+  if (rc) return rc;
+  float* slots[2] = {(float*)((char*)workspace + p->ws_bytes), (float*)((char*)workspace + p->ws_bytes + slot)};
+  const size_t img = (size_t)p->nv * p->nu;
+  // the copies overwrite the slots only after everything queued on `stream` before this call
+  e = cudaEventRecord(p->ev_start, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(p->copy_stream, p->ev_start, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_run_host: ordering the copy stream");
+  auto issue_copy = [&](int b) -> cudaError_t {
+    const int d0 = b * p->db, cnt = (p->D - d0) < p->db ? (p->D - d0) : p->db;
+    cudaError_t ec = cudaSuccess;
+    if (b >= 2) ec = cudaStreamWaitEvent(p->copy_stream, p->ev_free[b % 2], 0);  // block b - 2 read the slot
+    if (ec == cudaSuccess)
+      ec = cudaMemcpyAsync(slots[b % 2], host_images + (size_t)d0 * img, sizeof(float) * (size_t)cnt * img,
+                           cudaMemcpyHostToDevice, p->copy_stream);
+    if (ec == cudaSuccess) ec = cudaEventRecord(p->ev_ready[b % 2], p->copy_stream);
+    return ec;
+  };
+  MlpHookCtx hctx{p, (const char*)workspace, (float*)((char*)workspace + p->off_pow), w.eps, w.S, w.twp};
+  const recon::StageAHook hook{mlp_hook, &hctx};
+  const recon::StageAHook* hk = p->ca.filter == RECON_FILTER_MLP ? &hook : nullptr;
+  e = issue_copy(0);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_run_host: image copy");
+  for (int b = 0; b < p->n_blocks; ++b) {
+    const int d0 = b * p->db;
+    const int cnt = (p->D - d0) < p->db ? (p->D - d0) : p->db;
+    if (b + 1 < p->n_blocks) {
+      e = issue_copy(b + 1);
+      if (e != cudaSuccess) return cuda_fail(e, "recon_run_host: image copy");
+    }
+    e = cudaStreamWaitEvent(s, p->ev_ready[b % 2], 0);
+    if (e != cudaSuccess) return cuda_fail(e, "recon_run_host: waiting for the images");
+    // the kernels index images by absolute direction: the slot's address shifted back by d0
+    // images puts direction d0 at the slot's start (only the slot itself is read)
+    const float* images = (const float*)((uintptr_t)slots[b % 2] - (uintptr_t)d0 * img * sizeof(float));
+    e = recon::launch_stage_a(p->ca, w, images, d0, cnt, s, nullptr, hk);
+    if (e != cudaSuccess) return cuda_fail(e, "recon_run_host: stage A launch");
+    e = cudaEventRecord(p->ev_free[b % 2], s);  // stage A has read the slot once this point passes
+    if (e != cudaSuccess) return cuda_fail(e, "recon_run_host: slot release");
+    e = backproject_block(p, w.dirs, w.stack, d0, cnt, volume, p->opt.accumulate || b > 0, workspace, s);
+    if (e != cudaSuccess) return cuda_fail(e, "recon_run_host: backprojection launch");
+  }
+  return tma_end(p, workspace, s, "recon_run_host");
 }
 
 int recon_filter_stage(recon_plan_t p, const float* images, int dir_begin, int dir_count, void* workspace,

@@ -61,12 +61,14 @@ class Reconstructor:
         # the backprojection kernel the plan runs ("direct", "staged" or "tma")
         self.bp_kernel_used = {v: k for k, v in _BP_KERNELS.items()}[_abi.recon_plan_bp_kernel(self.plan)]
         self.ws_bytes = _abi.recon_workspace_size(self.plan)
+        # recon_run_host's workspace: the same head plus two direction blocks of images
+        self.ws_bytes_host = _abi.recon_run_host_workspace_size(self.plan)
         self.padded, self.dir_block, self.n_blocks, self.stage_block = _abi.recon_plan_info(self.plan)
         self.device = torch.device(device) if device is not None else (
             torch.device("cuda", torch.cuda.current_device()) if torch.cuda.is_available() else None)
         self.workspace = None
         if allocate:
-            self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=self.device)
+            self.workspace = torch.empty(max(self.ws_bytes_host, 256), dtype=torch.uint8, device=self.device)
 
     # -------------------------------------------------------------- helpers
     @staticmethod
@@ -102,6 +104,25 @@ class Reconstructor:
         """Entries per stack row: the nu + 1 tap pairs rounded up to a multiple of 4 (every
         row starts on a 16-byte boundary); the entries past nu are padding, never read."""
         return (self.nu + 4) // 4 * 4
+
+    def run_host(self, host_images: torch.Tensor, volume: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """``recon_run_host``: the whole operator with the images in host memory (a CPU
+        tensor, pinned for the copies to overlap the compute); they must stay untouched until
+        the stream's work has finished."""
+        if host_images.dtype != torch.float32 or host_images.is_cuda or not host_images.is_contiguous():
+            raise ValueError("host_images must be a contiguous float32 CPU tensor")
+        if tuple(host_images.shape) != (self.D, self.nv, self.nu):
+            raise ValueError(f"images shape {tuple(host_images.shape)} != {(self.D, self.nv, self.nu)}")
+        if volume is None:
+            volume = self.new_volume()
+        nx, ny, nz = self.grid
+        if volume.dtype != torch.float32 or not volume.is_contiguous() or tuple(volume.shape) != (nz, ny, nx):
+            raise ValueError("volume must be a contiguous float32 tensor of shape (nz, ny, nx)")
+        if self.workspace.numel() < self.ws_bytes_host:
+            raise ValueError("the workspace is smaller than recon_run_host_workspace_size")
+        _abi.recon_run_host(self.plan, host_images.data_ptr(), volume.data_ptr(), self.workspace.data_ptr(),
+                            self.workspace.numel(), self._stream(stream))
+        return volume
 
     def filter_stage(self, images: torch.Tensor, dir_begin: int, dir_count: int, stream=None) -> torch.Tensor:
         """``recon_filter_stage``: a view of the workspace holding the layer stacks as

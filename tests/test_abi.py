@@ -139,6 +139,26 @@ def test_null_arguments_are_errors_not_crashes(lib):
     _abi.recon_destroy(p)
 
 
+def test_host_input_run_is_validated_before_any_cuda_call(lib):
+    """recon_run_host: its workspace is recon_workspace_size plus two 256-aligned slots of a
+    direction block's images; null host images, check_finite plans and short or misaligned
+    workspaces are refused on the host."""
+    o = _abi.recon_default_options()
+    o.dir_block = 5
+    p = _plan(opts=o)
+    ws, wh = _abi.recon_workspace_size(p), _abi.recon_run_host_workspace_size(p)
+    slot = -(-(4 * 5 * 33 * 40) // 256) * 256
+    assert wh == ws + 2 * slot
+    assert lib.recon_run_host(p, None, 16, 256, wh, None) == _abi.RECON_E_INVALID_ARG
+    assert lib.recon_run_host(p, 16, 16, 256, wh - 256, None) == _abi.RECON_E_WORKSPACE
+    assert lib.recon_run_host(p, 16, 16, 8, 1 << 40, None) == _abi.RECON_E_WORKSPACE
+    _abi.recon_destroy(p)
+    o.check_finite = 1
+    p = _plan(opts=o)
+    assert lib.recon_run_host(p, 16, 16, 256, 1 << 40, None) == _abi.RECON_E_INVALID_ARG
+    _abi.recon_destroy(p)
+
+
 def test_error_strings(lib):
     texts = {_abi.recon_error_string(c) for c in (0, -1, -2, -3, -4, -5, -6, -7, -8)}
     assert len(texts) == 9 and "unknown status" not in texts
