@@ -63,10 +63,10 @@ NCU_TRAFFIC: dict = {
                                       "src": "b7ee0b8780a4373d"},
     # slab (bf16 stack): the column kernel from one 3-direction sub-block launch (the bench's
     # launch size); the TMA-staged backprojection from a 6-direction launch, its reads scaled
-    # by 25/6 to the bench's 25-direction blocks (the stack boxes grow with the directions),
+    # by 56/6 to the bench's 56-direction blocks (the stack boxes grow with the directions),
     # plus the volume read of an accumulating block and the volume write (1.07 GB each)
     ("k_cols", "slab", "bf16"): {"bytes_per_launch": 55.945984e6 + 1.550934e9, "src": "bed4d9ddf41aaddd"},
-    ("k_backproject", "slab", "bf16"): {"bytes_per_launch": 3.059654e9 * 25 / 6 + 1.073742e9 + 1.055155e9,
+    ("k_backproject", "slab", "bf16"): {"bytes_per_launch": 3.059654e9 * 56 / 6 + 1.073742e9 + 1.055155e9,
                                         "src": "f76a56888e3e5455"},
 }
 

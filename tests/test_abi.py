@@ -57,7 +57,7 @@ def test_workspace_grows_with_the_direction_block(lib):
 def test_block_sizing_follows_the_per_direction_intermediates(lib):
     """Small images: stage A runs the whole direction block (as many directions as 4 GiB
     holds, balanced).  Large images (one direction's spectra and intermediates above 64 MiB):
-    stage A runs in sub-blocks within 2 GiB, and the rest of an 8 GiB budget holds stacks."""
+    stage A runs in sub-blocks within 2 GiB, and the rest of a 16 GiB budget holds stacks."""
     o = _abi.recon_default_options()
     # 256^2 images, Nz = 32, float32 stacks: 120 directions per block, whole-block stage A
     p = _plan(rot=ph.single_axis_rotations(360), nu=256, nv=256, defocus=np.full(360, 1e-6), nz_layers=32,
@@ -65,15 +65,16 @@ def test_block_sizing_follows_the_per_direction_intermediates(lib):
     assert _abi.recon_plan_info(p) == (512, 120, 3, 120)
     _abi.recon_destroy(p)
     # 1024^2 images, Nz = 64, bfloat16 stacks, density weights: 546 MB of intermediates per
-    # direction, so sub-blocks of 3 (1.64 GB) and 25 directions per block (6.7 GB of stacks)
+    # direction, so sub-blocks of 3 (1.64 GB) and 56 directions per block (15.1 GB of stacks;
+    # 57 fit, balanced over 27 blocks)
     o.stack_dtype = _abi.RECON_STACK_BF16
     o.ramp_mode = _abi.RECON_RAMP_DENSITY
     rot = ph.cone_rotations(1500, 60.0, seed=3)
     p = _plan(rot=rot, nu=1024, nv=1024, defocus=np.full(1500, 1e-6), nz_layers=64, grid=(1024, 1024, 256),
               delta=5e-11, lam=1.97e-12, opts=o)
     P, db, nb, sb = _abi.recon_plan_info(p)
-    assert (P, sb) == (2048, 3) and db == 25 and nb == 60
-    assert _abi.recon_workspace_size(p) < (8 << 30) + (256 << 20)
+    assert (P, sb) == (2048, 3) and db == 56 and nb == 27
+    assert _abi.recon_workspace_size(p) < (16 << 30) + (256 << 20)
     _abi.recon_destroy(p)
     # an explicit stage_block still wins
     o.stage_block = 3
