@@ -258,6 +258,16 @@ int recon_batch_run(recon_batch_t batch, const float* const* images, float* cons
                     size_t ws_bytes, void* stream);
 int recon_batch_run_graph(recon_batch_t batch, const float* const* images, float* const* volumes, void* workspace,
                           size_t ws_bytes, void* stream);
+/* The batch with its images in host memory: round r + 1's images (every tomogram's
+ * directions of that round) are copied on a stream of the batch's own into one of two
+ * device round slots while round r runs on `stream`.  host_images: [n] host arrays laid out
+ * as recon_run's images (page-locked for the copies to overlap; valid until the queued
+ * work has finished); workspace >= recon_batch_run_host_workspace_size bytes (the batch
+ * workspace plus two round slots).  Same volumes as recon_batch_run on the same images; not
+ * captured as a graph.  One batch must not run it from two threads at once. */
+int recon_batch_run_host_workspace_size(recon_batch_t batch, size_t* bytes);
+int recon_batch_run_host(recon_batch_t batch, const float* const* host_images, float* const* volumes, void* workspace,
+                         size_t ws_bytes, void* stream);
 int recon_batch_destroy(recon_batch_t batch); /* NULL is a no-op */
 /* One-call form: create, run, destroy (default rounds of 32 directions). */
 int recon_run_batch_workspace_size(int n, const recon_plan_t* plans, size_t* bytes);

@@ -120,6 +120,8 @@ def load_library(path: str = LIB_PATH):
     L.recon_batch_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
     L.recon_batch_run.argtypes = [vp, pp, pp, vp, sz, vp]
     L.recon_batch_run_graph.argtypes = [vp, pp, pp, vp, sz, vp]
+    L.recon_batch_run_host.argtypes = [vp, pp, pp, vp, sz, vp]
+    L.recon_batch_run_host_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
     L.recon_batch_destroy.argtypes = [vp]
     L.recon_run_batch_workspace_size.argtypes = [ip, pp, ctypes.POINTER(sz)]
     L.recon_run_batch.argtypes = [ip, pp, pp, pp, vp, sz, vp]
@@ -139,7 +141,8 @@ def load_library(path: str = LIB_PATH):
                  "recon_run_batch_workspace_size", "recon_run_batch", "recon_plan_dof", "recon_layers_for_dof",
                  "recon_plan_layers", "recon_swap_workspace_size", "recon_swap_ct", "recon_swap_phase",
                  "recon_grid_workspace_size", "recon_grid_run", "recon_selftest_wait_limit", "recon_plan_bp_kernel",
-                 "recon_run_host", "recon_run_host_workspace_size"):
+                 "recon_run_host", "recon_run_host_workspace_size", "recon_batch_run_host",
+                 "recon_batch_run_host_workspace_size"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -356,6 +359,18 @@ def recon_batch_workspace_size(batch) -> int:
     n = ctypes.c_size_t()
     _check(load_library().recon_batch_workspace_size(batch, ctypes.byref(n)), "recon_batch_workspace_size")
     return n.value
+
+
+def recon_batch_run_host_workspace_size(batch) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().recon_batch_run_host_workspace_size(batch, ctypes.byref(n)),
+           "recon_batch_run_host_workspace_size")
+    return n.value
+
+
+def recon_batch_run_host(batch, host_image_ptrs, volume_ptrs, ws_ptr: int, ws_bytes: int, stream: int):
+    _check(load_library().recon_batch_run_host(batch, _ptrs(host_image_ptrs), _ptrs(volume_ptrs), ws_ptr, ws_bytes,
+                                               stream), "recon_batch_run_host")
 
 
 def recon_batch_run(batch, image_ptrs, volume_ptrs, ws_ptr: int, ws_bytes: int, stream: int, graph: bool = False):

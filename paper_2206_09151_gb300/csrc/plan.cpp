@@ -1592,9 +1592,25 @@ struct recon_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
   std::vector<const void*> graph_ptrs;     // pointers the captured graph was built for
+  // recon_batch_run_host: per tomogram a sub-slot of dbb images in each of two round slots,
+  // the copy stream and its events (created on first use, per device)
+  std::vector<size_t> off_img;             // sub-slot offsets within a round slot
+  size_t slot_bytes = 0;
+  int copy_dev = -1;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_ready[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr};
+  void release_copy_stream() {
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    for (cudaEvent_t e : {ev_start, ev_ready[0], ev_ready[1], ev_free[0], ev_free[1]})
+      if (e) cudaEventDestroy(e);
+    copy_stream = nullptr;
+    ev_start = ev_ready[0] = ev_ready[1] = ev_free[0] = ev_free[1] = nullptr;
+    copy_dev = -1;
+  }
   ~recon_batch_s() {
     if (gexec) cudaGraphExecDestroy(gexec);
     if (graph) cudaGraphDestroy(graph);
+    release_copy_stream();
   }
 };
 
@@ -1635,7 +1651,32 @@ int batch_prepare(recon_batch_t bt, const float* const* images, float* const* vo
 }
 
 // The kernels of one batch run (capturable: no host copies).
-int batch_launch(recon_batch_t bt, const float* const* images, float* const* volumes, char* base, cudaStream_t s) {
+// recon_batch_run_host's uploads: host images, round slots in the workspace.
+struct HostUpload {
+  const float* const* host;  // [n] host images
+  char* slots[2];            // round slots
+};
+
+// The images of round r, tomogram by tomogram, into round slot r % 2 on the copy stream
+// (after the stage A that read that slot two rounds earlier).
+cudaError_t batch_upload_round(recon_batch_t bt, const HostUpload* up, int r) {
+  cudaError_t e = cudaSuccess;
+  if (r >= 2) e = cudaStreamWaitEvent(bt->copy_stream, bt->ev_free[r % 2], 0);
+  for (int q = 0; q < bt->n && e == cudaSuccess; ++q) {
+    recon_plan_t p = bt->plans[q];
+    const int d0 = r * bt->dbb;
+    if (d0 >= p->D) continue;
+    const int cnt = (p->D - d0) < bt->dbb ? (p->D - d0) : bt->dbb;
+    const size_t img = (size_t)p->nv * p->nu;
+    e = cudaMemcpyAsync(up->slots[r % 2] + bt->off_img[q], up->host[q] + (size_t)d0 * img,
+                        sizeof(float) * (size_t)cnt * img, cudaMemcpyHostToDevice, bt->copy_stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(bt->ev_ready[r % 2], bt->copy_stream);
+  return e;
+}
+
+int batch_launch(recon_batch_t bt, const float* const* images, float* const* volumes, char* base, cudaStream_t s,
+                 const HostUpload* up = nullptr) {
   cudaError_t e = cudaMemsetAsync(base + bt->off_ctr, 0, sizeof(unsigned long long) * bt->n_rounds, s);
   if (e != cudaSuccess) return cuda_fail(e, "recon_batch: counters");
   for (int q = 0; q < bt->n; ++q) {  // tomograms without directions: clear the volume
@@ -1646,12 +1687,27 @@ int batch_launch(recon_batch_t bt, const float* const* images, float* const* vol
       if (e != cudaSuccess) return cuda_fail(e, "recon_batch: clearing a volume");
     }
   }
+  if (up && bt->n_rounds > 0) {
+    e = batch_upload_round(bt, up, 0);
+    if (e != cudaSuccess) return cuda_fail(e, "recon_batch: image copy");
+  }
   for (int r = 0; r < bt->n_rounds; ++r) {
+    if (up) {  // the next round's images upload while this round runs
+      if (r + 1 < bt->n_rounds) e = batch_upload_round(bt, up, r + 1);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(s, bt->ev_ready[r % 2], 0);
+      if (e != cudaSuccess) return cuda_fail(e, "recon_batch: image copy");
+    }
     for (int q = 0; q < bt->n; ++q) {
       recon_plan_t p = bt->plans[q];
       const int d0 = r * bt->dbb;
       if (d0 >= p->D) continue;
       const int cnt = (p->D - d0) < bt->dbb ? (p->D - d0) : bt->dbb;
+      // host input: the sub-slot shifted back by d0 images (the kernels index images by
+      // absolute direction; only the sub-slot is read)
+      const float* img_q =
+          up ? (const float*)((uintptr_t)(up->slots[r % 2] + bt->off_img[q]) -
+                              (uintptr_t)d0 * p->nv * p->nu * sizeof(float))
+             : images[q];
       recon::Workspace w = carve(p, base + bt->off_tables[q]);
       w.S = (float2*)(base + bt->off_S);
       w.T = (float2*)(base + bt->off_T);
@@ -1661,9 +1717,13 @@ int batch_launch(recon_batch_t bt, const float* const* images, float* const* vol
       const recon::StageAHook hook{mlp_hook, &hctx};
       recon::StageAConst ca = p->ca;
       if (p->P >= 16) ca.sub_block = std::min(bt->dbb, p->ca.sub_block > 0 ? p->ca.sub_block : 1);
-      e = recon::launch_stage_a(ca, w, images[q], d0, cnt, s, nullptr,
+      e = recon::launch_stage_a(ca, w, img_q, d0, cnt, s, nullptr,
                                 p->ca.filter == RECON_FILTER_MLP ? &hook : nullptr);
       if (e != cudaSuccess) return cuda_fail(e, "recon_batch: stage A launch");
+    }
+    if (up) {  // this round's stage A has read its slot once this point passes
+      e = cudaEventRecord(bt->ev_free[r % 2], s);
+      if (e != cudaSuccess) return cuda_fail(e, "recon_batch: slot release");
     }
     e = recon::launch_backproject_persistent((const recon::BatchBp*)(base + bt->off_desc) + (size_t)r * bt->n,
                                              bt->round_count[r], bt->round_total[r],
@@ -1738,6 +1798,13 @@ int recon_batch_create(int n, const recon_plan_t* plans, int dir_block, recon_ba
   off = align256(off + sizeof(unsigned long long) * (size_t)(rounds > 0 ? rounds : 1));
   bt->ws_bytes = off;
   bt->smem = smem;
+  bt->off_img.resize(n);
+  size_t soff = 0;
+  for (int q = 0; q < n; ++q) {
+    bt->off_img[q] = soff;
+    if (plans[q]->D > 0) soff = align256(soff + sizeof(float) * (size_t)bt->dbb * plans[q]->nv * plans[q]->nu);
+  }
+  bt->slot_bytes = soff;
   bt->desc.assign((size_t)rounds * n, recon::BatchBp{});
   bt->round_count.assign(rounds, 0);
   bt->round_total.assign(rounds, 0);
@@ -1805,6 +1872,49 @@ int recon_batch_run_graph(recon_batch_t bt, const float* const* images, float* c
   cudaError_t e = cudaGraphLaunch(bt->gexec, s);
   if (e != cudaSuccess) return cuda_fail(e, "recon_batch_run_graph: launch");
   return RECON_OK;
+}
+
+int recon_batch_run_host_workspace_size(recon_batch_t bt, size_t* bytes) {
+  if (!bt || !bytes) return fail(RECON_E_INVALID_ARG, "recon_batch_run_host_workspace_size: null argument");
+  *bytes = bt->ws_bytes + 2 * bt->slot_bytes;
+  return RECON_OK;
+}
+
+int recon_batch_run_host(recon_batch_t bt, const float* const* host_images, float* const* volumes, void* ws,
+                         size_t ws_bytes, void* stream) {
+  if (!bt) return fail(RECON_E_INVALID_ARG, "recon_batch_run_host: null batch");
+  const size_t need = bt->ws_bytes + 2 * bt->slot_bytes;
+  if (need > 0 && (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < need))
+    return fail(RECON_E_WORKSPACE, "recon_batch_run_host: workspace too small or misaligned (needs " +
+                                       std::to_string(need) + " bytes)");
+  int rc = batch_args(bt, host_images, volumes, ws, ws_bytes, "recon_batch_run_host");
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_batch_run_host: current device");
+  if (bt->copy_dev != dev) {
+    bt->release_copy_stream();
+    e = cudaStreamCreateWithFlags(&bt->copy_stream, cudaStreamNonBlocking);
+    for (cudaEvent_t* ev : {&bt->ev_start, &bt->ev_ready[0], &bt->ev_ready[1], &bt->ev_free[0], &bt->ev_free[1]})
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      bt->release_copy_stream();
+      return cuda_fail(e, "recon_batch_run_host: creating the copy stream");
+    }
+    bt->copy_dev = dev;
+  }
+  rc = batch_prepare(bt, host_images, volumes, (char*)ws, s);
+  if (rc) return rc;
+  // the copies overwrite the slots only after everything queued on `stream` before this call
+  e = cudaEventRecord(bt->ev_start, s);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->copy_stream, bt->ev_start, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "recon_batch_run_host: ordering the copy stream");
+  HostUpload up;
+  up.host = host_images;
+  up.slots[0] = (char*)ws + bt->ws_bytes;
+  up.slots[1] = up.slots[0] + bt->slot_bytes;
+  return batch_launch(bt, host_images, volumes, (char*)ws, s, &up);
 }
 
 int recon_batch_destroy(recon_batch_t bt) {

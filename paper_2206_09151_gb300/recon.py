@@ -237,8 +237,10 @@ class Batch:
         self.recons = list(recons)
         self.batch = _abi.recon_batch_create([r.plan for r in self.recons], dir_block)
         self.ws_bytes = _abi.recon_batch_workspace_size(self.batch)
+        # recon_batch_run_host's workspace: the same plus two round slots of images
+        self.ws_bytes_host = _abi.recon_batch_run_host_workspace_size(self.batch)
         dev = device if device is not None else self.recons[0].device if self.recons else None
-        self.workspace = torch.empty(max(self.ws_bytes, 256), dtype=torch.uint8, device=dev)
+        self.workspace = torch.empty(max(self.ws_bytes_host, 256), dtype=torch.uint8, device=dev)
         self.stream = None
 
     def run(self, images, volumes=None, graph: bool = False, stream=None):
@@ -257,6 +259,22 @@ class Batch:
                              self.workspace.data_ptr(), self.ws_bytes, int(s.cuda_stream), graph)
         if graph:
             torch.cuda.current_stream().wait_stream(stream)
+        return volumes
+
+    def run_host(self, host_images, volumes=None, stream=None):
+        """``recon_batch_run_host``: the images as contiguous float32 CPU tensors (pinned for the
+        uploads to overlap the rounds); they must stay untouched until the stream's work has
+        finished."""
+        if volumes is None:
+            volumes = [r.new_volume() for r in self.recons]
+        for r, im in zip(self.recons, host_images):
+            if im.dtype != torch.float32 or im.is_cuda or not im.is_contiguous():
+                raise ValueError("host images must be contiguous float32 CPU tensors")
+            if tuple(im.shape) != (r.D, r.nv, r.nu):
+                raise ValueError(f"images shape {tuple(im.shape)} != {(r.D, r.nv, r.nu)}")
+        s = stream if stream is not None else torch.cuda.current_stream()
+        _abi.recon_batch_run_host(self.batch, [im.data_ptr() for im in host_images], [v.data_ptr() for v in volumes],
+                                  self.workspace.data_ptr(), self.workspace.numel(), int(s.cuda_stream))
         return volumes
 
     def close(self):

@@ -194,3 +194,22 @@ def test_bp_warp_shapes_are_bitwise_equal_and_the_tuner_picks_one(interp):
     assert torch.equal(vols[0], vols[1]) and torch.equal(vols[0], vols[2])
     out = tune_bp_warp(rot, nu, nu, grid, img, nz_layers=3, candidates=(8, 16, 32), repeats=2, **kw)
     assert out["bp_warp"] in (8, 16, 32) and set(out["ms"]) == {"8", "16", "32"}
+
+
+def test_batch_with_host_images_matches_the_device_image_run():
+    """recon_batch_run_host (round r + 1's images uploaded while round r runs) gives the
+    volumes of recon_batch_run, over several rounds, from pinned host memory, twice in a row."""
+    from paper_2206_09151_gb300.recon import Batch
+    toms = _tomograms()
+    recons, _ = _single_runs(toms)
+    b = Batch(recons, dir_block=16)
+    ref = b.run([t[4] for t in toms], [torch.full((g[2], g[1], g[0]), 0.5, device="cuda") for _, _, g, _, _ in toms])
+    host = [t[4].cpu().pin_memory() for t in toms]
+    for _ in range(2):
+        got = b.run_host(host, [torch.full((g[2], g[1], g[0]), 0.5, device="cuda") for _, _, g, _, _ in toms])
+        torch.cuda.synchronize()
+        for q, (a, c) in enumerate(zip(got, ref)):
+            assert _same(q, toms, a, c), q
+    b.close()
+    for r in recons:
+        r.close()
