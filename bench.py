@@ -58,17 +58,31 @@ DEFAULT_STACK = {"mid": "f32", "small": "f32", "learned": "bf16", "slab": "bf16"
 NCU_TRAFFIC: dict = {
     # mid (float32): one 40-direction launch each, scaled by 120/40 to the bench's blocks (the
     # backprojection's volume read-modify-write does not scale; its figure overstates it)
-    ("k_cols", "mid", "f32"): {"bytes_per_launch": (21.171456e6 + 612.15744e6) * 3, "src": "bed4d9ddf41aaddd"},
-    ("k_backproject", "mid", "f32"): {"bytes_per_launch": (617.094656e6 + 59.883008e6) * 3,
+    ("k_cols", "mid", "f32"): {"bytes_per_launch": (21.171456e6 + 612.15744e6) * 3, "l2_hit_pct": 3.8,
+                               "src": "bed4d9ddf41aaddd"},
+    ("k_backproject", "mid", "f32"): {"bytes_per_launch": (617.094656e6 + 59.883008e6) * 3, "l2_hit_pct": 51.1,
+                                      # 171.8 M warp instructions for 40 x 256^3 updates
+                                      "warp_inst_per_update": 171823104 / (40 * 256 ** 3),
                                       "src": "b7ee0b8780a4373d"},
     # slab (bf16 stack): the column kernel from one 3-direction sub-block launch (the bench's
     # launch size); the TMA-staged backprojection from a 6-direction launch, its reads scaled
     # by 56/6 to the bench's 56-direction blocks (the stack boxes grow with the directions),
     # plus the volume read of an accumulating block and the volume write (1.07 GB each)
-    ("k_cols", "slab", "bf16"): {"bytes_per_launch": 55.945984e6 + 1.550934e9, "src": "bed4d9ddf41aaddd"},
+    ("k_cols", "slab", "bf16"): {"bytes_per_launch": 55.945984e6 + 1.550934e9, "l2_hit_pct": 8.4,
+                                 "src": "bed4d9ddf41aaddd"},
     ("k_backproject", "slab", "bf16"): {"bytes_per_launch": 3.059654e9 * 56 / 6 + 1.073742e9 + 1.055155e9,
+                                        "l2_hit_pct": 56.2,
+                                        # 1.553 G warp instructions for 6 x 1024^2 x 256 updates
+                                        "warp_inst_per_update": 1553227094 / (6 * 1024 * 1024 * 256),
                                         "src": "f76a56888e3e5455"},
 }
+
+
+# The roof that binds each stage-A kernel (ncu evidence in profiles/): FP32 arithmetic for the
+# column FFT and filter, the L1 / shared-memory pipe for the row stage; the forward row FFTs
+# are small and memory-bound.  The backprojection's depends on the kernel that ran.
+KERNEL_BOUND = {"k_rows_fwd": "hbm", "k_cols": "alu (FP32)", "k_rows_inv": "l1/shared-memory pipe"}
+ISSUE_PEAK = 152 * 4 * 2.07e9  # warp instructions per second
 
 
 def _src_hash(name: str) -> str:
@@ -434,11 +448,22 @@ def run_ours(args):
         gbs = algo[q] / (kern_ms[q] / args.steps / 1e3) / 1e9 if kern_ms[q] > 0 else None
         tr = NCU_TRAFFIC.get((name, args.workload, args.stack))
         src = bp_src if q == 3 else "stage_a.cu"
+        valid = tr is not None and tr["src"] == _src_hash(src)
         kernels[name] = {"launches": kern_n[q], "ms_per_launch": per_launch_ms,
                          "share": kern_ms[q] / max(sum(kern_ms), 1e-12), "algorithmic_GBps": gbs,
                          "algorithmic_bytes_per_launch": algo[q] * args.steps / max(kern_n[q], 1),
-                         "ncu_dram_bytes_per_launch": tr["bytes_per_launch"] if tr and tr["src"] == _src_hash(src)
-                         else None}
+                         "ncu_dram_bytes_per_launch": tr["bytes_per_launch"] if valid else None,
+                         "bound": KERNEL_BOUND[name] if q < 3 else
+                         ("issue (FMA/ALU pipes)" if r.bp_kernel_used == "tma" else "l1 (gathers)")}
+        if valid and per_launch_ms > 0:
+            # the captured bytes at the bench's launch time, against the measured HBM peak
+            kernels[name]["ncu_dram_frac"] = tr["bytes_per_launch"] / (per_launch_ms / 1e3) / 1e9 / peaks["hbm_gbs"]
+            kernels[name]["ncu_l2_hit_pct"] = tr.get("l2_hit_pct")
+            if "warp_inst_per_update" in tr and kern_ms[q] > 0:
+                # issue roofline: warp instructions per update (ncu) x updates/s, against
+                # 152 SMs x 4 schedulers x 2070 MHz
+                ups = V * D * args.steps / (kern_ms[q] / 1e3)
+                kernels[name]["issue_frac"] = tr["warp_inst_per_update"] * ups / ISSUE_PEAK
     flops = cols_flops(cfg, r, counts)
     kernels["k_cols"]["algorithmic_TFLOPs"] = (flops / (kern_ms[1] / args.steps / 1e3) / 1e12
                                                if kern_ms[1] > 0 else None)
