@@ -695,6 +695,145 @@ def run_batch(args):
     return 0
 
 
+def run_fourier(args):
+    """The two 3D-Fourier forms on one GPU: Eq. 12's swapped order (``--form swap``: the CT step
+    with the Ewald placement, then one 3D CTF inversion) and the Fourier-gridding UTR
+    (``--form grid``: the bracket per view splatted onto the Ewald paraboloids, S_eps^-1, one
+    inverse 3D FFT).  A step is one whole reconstruction; the swap's 3D inversion alone (the
+    cost of every further (sigma, eps)) is reported beside it."""
+    import torch
+    if int(os.environ.get("WORLD_SIZE", "1")) > 1:
+        raise SystemExit("--form swap / grid runs on one GPU")
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2206_09151_gb300.build import build
+    from paper_2206_09151_gb300.recon import Reconstructor
+    build()
+    cfg = workload(args.workload, 0, args.dirs)
+    images = make_images(cfg, dev)
+    torch.cuda.synchronize()
+    V = int(np.prod(cfg["grid"]))
+    D = cfg["n_dir"]
+    U = V * D
+    R = float(np.mean(cfg["defocus"]))  # Eq. 12 needs one defocus for every view
+    r = Reconstructor(cfg["rot"], cfg["nu"], cfg["nv"], cfg["grid"], lam=cfg["lam"], delta=cfg["delta"],
+                      defocus=np.full(D, R), nz_layers=cfg["nz_layers"], sigma=cfg["sigma"], eps=cfg["eps"],
+                      cs=cfg["cs"], stack_dtype="f32", ramp=cfg["ramp"],
+                      filter="pair" if args.form == "swap" else "tikhonov", device=dev)
+    vol = r.new_volume()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    nsr = float(cfg["photons"]) ** -0.5 if args.form == "grid" else 0.0
+
+    def step():
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        if args.form == "swap":
+            ws = r.swap_ct(images)
+            e1.record(stream)
+            r.swap_phase(ws, cfg["sigma"], cfg["eps"], vol)
+        else:
+            r.grid_run(images, nsr, vol)
+            e1.record(stream)
+        e2.record(stream)  # e1 -> e2: the swap's 3D inversion inside the step
+        e2.synchronize()
+        return e0.elapsed_time(e2), e1.elapsed_time(e2)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    sampler = ClockSampler(gpu_index(0))
+    sampler.start()
+    time.sleep(0.3)
+    ms, tail_ms = [], []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = step()
+        ms.append(a)
+        tail_ms.append(b)
+    clocks = sampler.stop()
+    ms_step = sum(ms) / args.steps
+    # the swap's 3D inversion alone, timed on its own (the per-(sigma, eps) cost)
+    phase_ms = None
+    if args.form == "swap":
+        ws = r.swap_ct(images)
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r.swap_phase(ws, cfg["sigma"], cfg["eps"], vol)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        phase_ms = sum(ts) / len(ts)
+        del ws
+    # end to end: pinned host images in, volume out
+    host_img = images.cpu().pin_memory()
+    host_vol = torch.empty(vol.shape, dtype=torch.float32).pin_memory()
+    dimg = torch.empty_like(images)
+    e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dimg.copy_(host_img, non_blocking=True)
+        if args.form == "swap":
+            r.swap_phase(r.swap_ct(dimg), cfg["sigma"], cfg["eps"], vol)
+        else:
+            r.grid_run(dimg, nsr, vol)
+        host_vol.copy_(vol, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e.append(e0.elapsed_time(e1))
+    # launches per step: the layered CT step twice (cos and sin volumes) or the per-view
+    # spectra and splats, plus the 3D passes
+    P3 = [1 << int(np.ceil(np.log2(2 * n))) for n in cfg["grid"]]
+    fft3 = sum(1 for q in P3 if q > 1)
+    sub = max(r.stage_block, 1)
+    nsub = sum(-(-min(r.dir_block, D - b * r.dir_block) // sub) for b in range(r.n_blocks))
+    dens = 2 if cfg["ramp"] == "density" else 0  # the sampling density, once per call
+    if args.form == "swap":
+        launches = dens + 2 * (3 * nsub + r.n_blocks) + 1 + fft3 + (1 + fft3 + 1)
+        # the inversion: the phase kernel reads Z and writes the work grid, each 3D pass reads
+        # and writes it, the crop reads the kept voxels and writes the volume
+        cells = float(np.prod(P3))
+        algo = cells * 8 * 2 + fft3 * cells * 8 * 2 + V * 12
+        peaks, peak_src = load_peaks()
+        achieved = algo / (phase_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": achieved / peaks["hbm_gbs"], "kernel": "swap_phase (k_swap_phase, k_fft3_lines x3, "
+                    "k_crop_real)", "traffic": None, "algorithmic_bytes_per_launch": algo, "launches": 1,
+                    "ms_per_launch": phase_ms, "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)"}
+    else:
+        gsub = -(-D // max(1, min(D, (1 << 30) // (cfg["nv"] * (r.padded // 2 + 1) * 8 + (r.padded // 2 + 1)
+                                                   * r.padded * 8))))
+        launches = dens + 3 * gsub + 2 + fft3 + 1
+        roofline = None
+    line = {"metric": METRIC, "value": U / (ms_step / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload] + (f" [first {D} directions only]" if args.dirs else ""),
+                       "form": {"swap": "Eq. 12 swapped order (one defocus for every view: the workload's mean)",
+                                "grid": "Fourier-gridding UTR with the NSR noise filter"}[args.form],
+                       "padded_grid": P3, "updates_per_step": U,
+                       "l2": "flushed between timed steps (256 MiB write outside the timed span)",
+                       "parallelism": "replicas x1"},
+            "e2e": {"value": U / (sum(e2e) / len(e2e) / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": images.numel() * 4, "d2h_bytes_per_step": vol.numel() * 4},
+            "gpu_launches": launches * args.steps, "roofline": roofline, "clocks": clocks,
+            "accuracy": {"note": "parity against the FP64 oracle in tests/test_fourier_gpu.py (1e-5 rel-L2; 1e-3 "
+                                 "with the noise filter)"}}
+    if args.form == "swap":
+        line["swap_ct_ms"] = ms_step - sum(tail_ms) / args.steps
+        line["swap_phase_ms"] = phase_ms
+    else:
+        line["roofline_note"] = ("one call; its per-view splat (8 float atomics per accumulator and sample) and "
+                                 "3D passes are broken down by the launch list in profiles/")
+    print(json.dumps(line))
+    r.close()
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
@@ -712,6 +851,8 @@ def main():
     ap.add_argument("--stage-block", type=int, default=0, help="directions per FFT/filter sub-block, 0 = auto")
     ap.add_argument("--bp-kernel", choices=["auto", "direct", "staged", "tma"], default="auto",
                     help="backprojection variant (tma: the TMA-staged kernel for any geometry)")
+    ap.add_argument("--form", choices=["layered", "swap", "grid"], default="layered",
+                    help="swap: Eq. 12's CT step and 3D CTF inversion; grid: the Fourier-gridding UTR")
     ap.add_argument("--layer-interp", choices=["nearest", "linear"], default="nearest",
                     help="a voxel's layer: the one containing its depth, or the blend of the two bracketing ones")
     ap.add_argument("--dirs", type=int, default=None, help="first N directions only (small profiling cases)")
@@ -728,6 +869,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch":
         return run_batch(args)
+    if args.form != "layered":
+        return run_fourier(args)
     return run_ours(args)
 
 

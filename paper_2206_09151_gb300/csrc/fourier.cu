@@ -9,7 +9,8 @@
 //   V_c^(q) = (Z(q) + conj Z(-q)) / 2,  V_s^(q) = (Z(q) - conj Z(-q)) / (2 i),
 //   s' = sin chi / (sin^2 chi + eps), c' = cos chi / (cos^2 chi + eps), chi at the
 //   in-plane frequency q_perp of the Ewald-paraboloid point q (q_perp^2 = 2 q^2 /
-//   (sqrt(1 + lambda^2 q^2) + 1)), computed in FP64 (chi reaches hundreds of radians).
+//   (sqrt(1 + lambda^2 q^2) + 1)); chi reaches hundreds of radians, so its exact part is
+//   taken modulo one turn in 64-bit fixed point and only a small correction in FP32.
 // The spectrum of the CT step stays in the workspace, so other (sigma, eps) rerun only the
 // phase pass and the inverse transform.
 //
@@ -23,6 +24,9 @@
 // NSR M / sqrt(S).  The phase back to the grid origin and 1/Delta are applied before the
 // inverse transform.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
 
 #include "recon_internal.h"
 
@@ -42,30 +46,50 @@ __global__ void k_swap_pack(const float* __restrict__ vc, const float* __restric
   }
 }
 
-__global__ void k_swap_phase(const float2* __restrict__ Z, float2* __restrict__ out, Fourier3Const f, double R,
-                             double sigma, double eps, double cs) {
+// Constants of the phase pass (host-built in FP64 per call).  With power-of-two grid sides,
+// K = sum_a (Pmax / P3_a)^2 m_a^2 is an integer and q^2 = K / (Pmax Delta)^2, so the phase in
+// turns, chi / (2 pi) = (lambda R / 2) q_perp^2 + (Cs lambda^3 / 4) q_perp^4 - omega / (2 pi),
+// splits into an exact part, uR K + uC K^2 - uW in 64-bit fixed point (2^-64 turns, modulo
+// 1; uR, uC, uW the fractional parts of the per-unit constants) with q_perp^2 replaced by
+// q^2, and the Ewald correction q_perp^2 = q^2 c(x), c = 2 / (1 + sqrt(1 + x)), x =
+// lambda^2 q^2: (lambda R / 2) q^2 (c - 1) + (Cs lambda^3 / 4) q^4 (c^2 - 1), a fraction of a
+// turn, in FP32.
+struct SwapPhaseConst {
+  uint64_t uR, uC, uW;
+  float kx;          // x per unit K
+  float uRf, uCf;    // lambda R / (2 (Pmax Delta)^2) and Cs lambda^3 / (4 (Pmax Delta)^4), turns
+  float pref, eps;   // lambda / (4 pi sqrt(1 + sigma^2)), the Tikhonov eps
+  int lx, ly;        // log2 of P3[0], P3[1]
+  int sx, sy, sz;    // (Pmax / P3_a)^2
+};
+
+__global__ void k_swap_phase(const float2* __restrict__ Z, float2* __restrict__ out, Fourier3Const f,
+                             SwapPhaseConst k) {
   const long long nb = (long long)f.P3[0] * f.P3[1] * f.P3[2];
-  const double pref = f.lam / (4.0 * 3.14159265358979323846 * sqrt(1.0 + sigma * sigma));
-  const double omega = atan(sigma);
+  const int mx = f.P3[0] - 1, my = f.P3[1] - 1, mz = f.P3[2] - 1;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
-    const int ix = (int)(i % f.P3[0]), iy = (int)((i / f.P3[0]) % f.P3[1]), iz = (int)(i / ((long long)f.P3[0] * f.P3[1]));
-    const int jx = (f.P3[0] - ix) & (f.P3[0] - 1), jy = (f.P3[1] - iy) & (f.P3[1] - 1), jz = (f.P3[2] - iz) & (f.P3[2] - 1);
+    const int ix = (int)(i & mx), iy = (int)((i >> k.lx) & my), iz = (int)(i >> (k.lx + k.ly));
+    const int jx = (f.P3[0] - ix) & mx, jy = (f.P3[1] - iy) & my, jz = (f.P3[2] - iz) & mz;
     const float2 a = Z[i];
-    const float2 b = Z[((long long)jz * f.P3[1] + jy) * f.P3[0] + jx];  // Z(-q); conj is (b.x, -b.y)
+    const float2 b = Z[(((long long)jz << k.ly) + jy << k.lx) + jx];  // Z(-q); conj is (b.x, -b.y)
     // V_c = (a + conj b) / 2, V_s = (a - conj b) / (2 i)
-    const double vcr = 0.5 * ((double)a.x + b.x), vci = 0.5 * ((double)a.y - b.y);
-    const double vsr = 0.5 * ((double)a.y + b.y), vsi = -0.5 * ((double)a.x - b.x);
-    const double qx = signed_bin(ix, f.P3[0]) / (f.P3[0] * f.delta);
-    const double qy = signed_bin(iy, f.P3[1]) / (f.P3[1] * f.delta);
-    const double qz = signed_bin(iz, f.P3[2]) / (f.P3[2] * f.delta);
-    const double q2 = qx * qx + qy * qy + qz * qz;
-    const double qp2 = 2.0 * q2 / (sqrt(1.0 + f.lam * f.lam * q2) + 1.0);
-    const double chi = 3.14159265358979323846 * f.lam * R * qp2 +
-                       0.5 * 3.14159265358979323846 * cs * f.lam * f.lam * f.lam * qp2 * qp2 - omega;
-    double sn, cn;
-    sincos(chi, &sn, &cn);
-    const double sp = pref * sn / (sn * sn + eps), cp = pref * cn / (cn * cn + eps);
-    out[i] = make_float2((float)(sp * vcr - cp * vsr), (float)(sp * vci - cp * vsi));
+    const float vcr = 0.5f * (a.x + b.x), vci = 0.5f * (a.y - b.y);
+    const float vsr = 0.5f * (a.y + b.y), vsi = -0.5f * (a.x - b.x);
+    const int ux = signed_bin(ix, f.P3[0]), uy = signed_bin(iy, f.P3[1]), uz = signed_bin(iz, f.P3[2]);
+    const uint64_t K = (uint64_t)k.sx * (uint64_t)(ux * ux) + (uint64_t)k.sy * (uint64_t)(uy * uy) +
+                       (uint64_t)k.sz * (uint64_t)(uz * uz);
+    const uint64_t ph = k.uR * K + k.uC * (K * K) - k.uW;  // modulo 2^64 = modulo one turn
+    const float Kf = (float)K;
+    const float x = k.kx * Kf;
+    const float r = 1.f + sqrtf(1.f + x);
+    const float cm1 = -x / (r * r);  // c - 1
+    const float corr = k.uRf * Kf * cm1 + k.uCf * Kf * Kf * (cm1 * (cm1 + 2.f));  // turns
+    const int32_t h = (int32_t)(uint32_t)(ph >> 32) + __float2int_rn((corr - rintf(corr)) * 4294967296.0f);
+    float sn, cn;
+    __sincosf((float)h * 1.4629180792671596e-09f, &sn, &cn);  // h * 2 pi / 2^32
+    const float sp = k.pref * __fdividef(sn, fmaf(sn, sn, k.eps));
+    const float cp = k.pref * __fdividef(cn, fmaf(cn, cn, k.eps));
+    out[i] = make_float2(sp * vcr - cp * vsr, sp * vci - cp * vsi);
   }
 }
 
@@ -159,34 +183,42 @@ __global__ void k_grid_splat(const float2* __restrict__ G, const GridDir* __rest
   }
 }
 
+// Sum and count of the non-zero cells of S: per thread in FP32 over its strided cells, then
+// in FP64 across the warp and the grid.
 __global__ void k_grid_stats(const float* __restrict__ S, long long n, double* __restrict__ stats) {
-  double sum = 0.0, cnt = 0.0;
+  float sum = 0.f;
+  unsigned int cnt = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const float s = S[i];
     if (s > 0.f) {
       sum += s;
-      cnt += 1.0;
+      ++cnt;
     }
   }
+  double ds = sum, dc = (double)cnt;
   for (int o = 16; o > 0; o >>= 1) {
-    sum += __shfl_down_sync(0xffffffffu, sum, o);
-    cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+    ds += __shfl_down_sync(0xffffffffu, ds, o);
+    dc += __shfl_down_sync(0xffffffffu, dc, o);
   }
-  if ((threadIdx.x & 31) == 0 && cnt > 0.0) {
-    atomicAdd(&stats[0], sum);
-    atomicAdd(&stats[1], cnt);
+  if ((threadIdx.x & 31) == 0 && dc > 0.0) {
+    atomicAdd(&stats[0], ds);
+    atomicAdd(&stats[1], dc);
   }
 }
 
-// F = acc / (S + eps_S) (zero where the noise filter drops it), times the phase back to the
-// grid origin and 1 / delta, in place.
 __global__ void k_grid_finish(float2* __restrict__ acc, const float2* __restrict__ raw, const float* __restrict__ S,
-                              const double* __restrict__ stats, Fourier3Const f, float nsr_m) {
+                              const double* __restrict__ stats, Fourier3Const f, float nsr_m, int lx, int ly,
+                              int Pmax) {
   const long long nb = (long long)f.P3[0] * f.P3[1] * f.P3[2];
   const float eps_s = stats[1] > 0.0 ? (float)(1e-3 * stats[0] / stats[1]) : 1.f;
   const float inv_delta = (float)(1.0 / f.delta);
+  const int mx = f.P3[0] - 1, my = f.P3[1] - 1;
+  // centre offsets c_a = off_a + (n_a - 1) / 2 as 2 c_a, and Pmax / P3_a
+  const int c2[3] = {2 * f.off[0] + f.n[0] - 1, 2 * f.off[1] + f.n[1] - 1, 2 * f.off[2] + f.n[2] - 1};
+  const int sc[3] = {Pmax / f.P3[0], Pmax / f.P3[1], Pmax / f.P3[2]};
+  const float inv_pmax = 1.f / (float)Pmax;  // a power of two: exact
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += (long long)gridDim.x * blockDim.x) {
-    const int ix = (int)(i % f.P3[0]), iy = (int)((i / f.P3[0]) % f.P3[1]), iz = (int)(i / ((long long)f.P3[0] * f.P3[1]));
+    const int ix = (int)(i & mx), iy = (int)((i >> lx) & my), iz = (int)(i >> (lx + ly));
     const float s = S[i];
     const float inv = 1.f / (s + eps_s);
     float2 F = make_float2(acc[i].x * inv, acc[i].y * inv);
@@ -195,20 +227,28 @@ __global__ void k_grid_finish(float2* __restrict__ acc, const float2* __restrict
       const bool keep = s > 0.f && sqrtf(r.x * r.x + r.y * r.y) * inv >= nsr_m * rsqrtf(fmaxf(s, 1e-30f));
       if (!keep) F = make_float2(0.f, 0.f);
     }
-    // exp(-2 pi i sum_a m_a c_a / P3_a), c_a = off_a + (n_a - 1) / 2: turns as an exact sum
-    // of fractions with power-of-two denominators (2 P3_a), reduced modulo 1 in FP64
-    double t = 0.0;
-    const int mm[3] = {signed_bin(ix, f.P3[0]), signed_bin(iy, f.P3[1]), signed_bin(iz, f.P3[2])};
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const long long num = ((long long)mm[a] * (2LL * f.off[a] + f.n[a] - 1)) % (2LL * f.P3[a]);
-      t += (double)num / (2.0 * f.P3[a]);
-    }
-    t -= floor(t);
+    // exp(-2 pi i sum_a m_a c_a / P3_a): the turns are T / (2 Pmax), T = sum_a m_a (2 c_a)
+    // (Pmax / P3_a) an exact integer, reduced modulo 2 Pmax (a power of two)
+    const int T = (signed_bin(ix, f.P3[0]) * c2[0] * sc[0] + signed_bin(iy, f.P3[1]) * c2[1] * sc[1] +
+                   signed_bin(iz, f.P3[2]) * c2[2] * sc[2]) & (2 * Pmax - 1);
     float ps, pc;
-    sincospif(-2.f * (float)t, &ps, &pc);
+    sincospif(-(float)T * inv_pmax, &ps, &pc);
     acc[i] = make_float2((F.x * pc - F.y * ps) * inv_delta, (F.x * ps + F.y * pc) * inv_delta);
   }
+}
+
+// frac(t) in 2^-64 turns (t >= 0)
+uint64_t turns_fixed(double t) {
+  double fr = t - std::floor(t);
+  if (!(fr < 1.0)) fr = 0.0;
+  const double scaled = std::ldexp(fr, 64);
+  return scaled >= 18446744073709551616.0 ? 0 : (uint64_t)scaled;
+}
+
+int log2_int(int p) {
+  int l = 0;
+  while ((1 << l) < p) ++l;
+  return l;
 }
 
 unsigned grid_blocks(long long n) {
@@ -229,7 +269,26 @@ cudaError_t launch_swap_pack(const float* vc, const float* vs, float2* grid, con
 
 cudaError_t launch_swap_phase(const float2* Z, float2* out, const Fourier3Const& f, double R, double sigma, double eps,
                               double cs, cudaStream_t s) {
-  k_swap_phase<<<grid_blocks((long long)f.P3[0] * f.P3[1] * f.P3[2]), 256, 0, s>>>(Z, out, f, R, sigma, eps, cs);
+  SwapPhaseConst k;
+  const int Pmax = std::max(f.P3[0], std::max(f.P3[1], f.P3[2]));
+  const double pd2 = (double)Pmax * f.delta * (double)Pmax * f.delta;  // (Pmax Delta)^2
+  const double cR = f.lam * R / (2.0 * pd2);                            // turns per unit K
+  const double cC = cs * f.lam * f.lam * f.lam / (4.0 * pd2 * pd2);     // turns per unit K^2
+  const double cW = std::atan(sigma) / (2.0 * 3.14159265358979323846);
+  k.uR = turns_fixed(cR);
+  k.uC = turns_fixed(cC);
+  k.uW = turns_fixed(cW);
+  k.kx = (float)(f.lam * f.lam / pd2);
+  k.uRf = (float)cR;
+  k.uCf = (float)cC;
+  k.pref = (float)(f.lam / (4.0 * 3.14159265358979323846 * std::sqrt(1.0 + sigma * sigma)));
+  k.eps = (float)eps;
+  k.lx = log2_int(f.P3[0]);
+  k.ly = log2_int(f.P3[1]);
+  k.sx = (Pmax / f.P3[0]) * (Pmax / f.P3[0]);
+  k.sy = (Pmax / f.P3[1]) * (Pmax / f.P3[1]);
+  k.sz = (Pmax / f.P3[2]) * (Pmax / f.P3[2]);
+  k_swap_phase<<<grid_blocks((long long)f.P3[0] * f.P3[1] * f.P3[2]), 256, 0, s>>>(Z, out, f, k);
   return cudaGetLastError();
 }
 
@@ -254,7 +313,9 @@ cudaError_t launch_grid_finish(float2* acc, const float2* raw, const float* S, d
   cudaError_t e = cudaMemsetAsync(stats, 0, 2 * sizeof(double), s);
   if (e != cudaSuccess) return e;
   k_grid_stats<<<grid_blocks(nb), 256, 0, s>>>(S, nb, stats);
-  k_grid_finish<<<grid_blocks(nb), 256, 0, s>>>(acc, raw, S, stats, f, nsr_m);
+  const int Pmax = std::max(f.P3[0], std::max(f.P3[1], f.P3[2]));
+  k_grid_finish<<<grid_blocks(nb), 256, 0, s>>>(acc, raw, S, stats, f, nsr_m, log2_int(f.P3[0]), log2_int(f.P3[1]),
+                                                Pmax);
   return cudaGetLastError();
 }
 
