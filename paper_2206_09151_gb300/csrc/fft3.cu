@@ -27,9 +27,11 @@ struct Engine {
 };
 
 // Lines: line (o, i) starts at o * outer_stride + i and has element stride es; lines are
-// numbered i fastest (n_inner of them per o).  Along x: n_inner = 1, es = 1.
+// numbered i fastest (2^inner_log2 of them per o: the grid sides are powers of two, so the
+// split is a shift and a mask, not a 64-bit division per element).  Along x: one line per o,
+// es = 1.
 template <int P, bool INV>
-__global__ void __launch_bounds__(kThreads3) k_fft3_lines(float2* __restrict__ data, long long n_lines, int n_inner,
+__global__ void __launch_bounds__(kThreads3) k_fft3_lines(float2* __restrict__ data, long long n_lines, int inner_log2,
                                                           long long outer_stride, long long es,
                                                           const float2* __restrict__ twg) {
   using E = Engine<P>;
@@ -47,7 +49,7 @@ __global__ void __launch_bounds__(kThreads3) k_fft3_lines(float2* __restrict__ d
     const long long l = l0 + t;
     float2 val = make_float2(0.f, 0.f);
     if (l < n_lines) {
-      const long long o = l / n_inner, i = l % n_inner;
+      const long long o = l >> inner_log2, i = l & ((1LL << inner_log2) - 1);
       val = data[o * outer_stride + i + v * es];
     }
     buf_all[t * E::L + E::idx(v)] = val;
@@ -76,7 +78,7 @@ __global__ void __launch_bounds__(kThreads3) k_fft3_lines(float2* __restrict__ d
     const int t = along_x ? q / P : q % E::CB, v = along_x ? q % P : q / E::CB;
     const long long l = l0 + t;
     if (l < n_lines) {
-      const long long o = l / n_inner, i = l % n_inner;
+      const long long o = l >> inner_log2, i = l & ((1LL << inner_log2) - 1);
       data[o * outer_stride + i + v * es] = buf_all[t * E::L + E::idx(v)];
     }
   }
@@ -115,7 +117,10 @@ cudaError_t lines_p(float2* data, long long n_lines, int n_inner, long long oute
     if (e != cudaSuccess) return e;
   }
   const long long ctas = (n_lines + E::CB - 1) / E::CB;
-  k_fft3_lines<P, INV><<<(unsigned)ctas, kThreads3, smem, s>>>(data, n_lines, n_inner, outer_stride, es, tw);
+  int inner_log2 = 0;  // n_inner is 1, X or X Y: a power of two
+  while ((1LL << inner_log2) < n_inner) ++inner_log2;
+  if ((1LL << inner_log2) != n_inner) return cudaErrorInvalidValue;
+  k_fft3_lines<P, INV><<<(unsigned)ctas, kThreads3, smem, s>>>(data, n_lines, inner_log2, outer_stride, es, tw);
   return cudaGetLastError();
 }
 
