@@ -43,16 +43,28 @@ __global__ void __launch_bounds__(kThreads3) k_fft3_lines(float2* __restrict__ d
   for (int i = threadIdx.x; i < E::NT; i += kThreads3) tw[i] = twg[i];
   const long long l0 = (long long)blockIdx.x * E::CB;
   const bool along_x = es == 1;
-  // fill: along x row by row (consecutive elements), else CB neighbours in x per element
-  for (int q = threadIdx.x; q < E::CB * P; q += kThreads3) {
+  // fill: along x row by row (consecutive elements), else CB neighbours in x per element;
+  // every load of the thread is issued before the first shared-memory store, so that they
+  // are all in flight at once (one at a time left the kernel waiting on DRAM latency)
+  constexpr int NQ = E::CB * P / kThreads3;  // elements per thread
+  static_assert(NQ * kThreads3 == E::CB * P, "whole lines per CTA");
+  float2 val[NQ];
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const int q = threadIdx.x + k * kThreads3;
     const int t = along_x ? q / P : q % E::CB, v = along_x ? q % P : q / E::CB;
     const long long l = l0 + t;
-    float2 val = make_float2(0.f, 0.f);
+    val[k] = make_float2(0.f, 0.f);
     if (l < n_lines) {
       const long long o = l >> inner_log2, i = l & ((1LL << inner_log2) - 1);
-      val = data[o * outer_stride + i + v * es];
+      val[k] = data[o * outer_stride + i + v * es];
     }
-    buf_all[t * E::L + E::idx(v)] = val;
+  }
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const int q = threadIdx.x + k * kThreads3;
+    const int t = along_x ? q / P : q % E::CB, v = along_x ? q % P : q / E::CB;
+    buf_all[t * E::L + E::idx(v)] = val[k];
   }
   __syncthreads();
   const fft::GroupSync gsync{1 + g, E::T};
@@ -74,12 +86,20 @@ __global__ void __launch_bounds__(kThreads3) k_fft3_lines(float2* __restrict__ d
     for (int s = 0; s < 8; ++s) buf[E::idx(j + s * E::T)] = x[s];
   }
   __syncthreads();
-  for (int q = threadIdx.x; q < E::CB * P; q += kThreads3) {
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const int q = threadIdx.x + k * kThreads3;
+    const int t = along_x ? q / P : q % E::CB, v = along_x ? q % P : q / E::CB;
+    val[k] = buf_all[t * E::L + E::idx(v)];
+  }
+#pragma unroll
+  for (int k = 0; k < NQ; ++k) {
+    const int q = threadIdx.x + k * kThreads3;
     const int t = along_x ? q / P : q % E::CB, v = along_x ? q % P : q / E::CB;
     const long long l = l0 + t;
     if (l < n_lines) {
       const long long o = l >> inner_log2, i = l & ((1LL << inner_log2) - 1);
-      data[o * outer_stride + i + v * es] = buf_all[t * E::L + E::idx(v)];
+      data[o * outer_stride + i + v * es] = val[k];
     }
   }
 }
