@@ -87,7 +87,51 @@ __device__ __forceinline__ void dftR(float2* v) {
 // A buffer `out` receives this pass's values (unless it is the last), `in` holds the
 // previous pass's (unless it is the first); `sync_in` runs before reading `in`,
 // `sync_out` before writing `out` (both no-ops when the caller double-buffers).
-template <int P, int R, int Ns, bool INV, typename Sync>
+// Twiddles of one radix-16 or radix-8 column from a few table entries: w[r] = W^r for
+// r = 1..R-1 given W^1, W^4 (and W^8, W^12 for R = 16), each other power one or two complex
+// products away (W^2 = (W^1)^2, W^3 = W^2 W^1, W^(4a+b) = W^(4a) W^b), so its rounding error
+// stays within a few units in the last place.  Four (R = 16) or two (R = 8) shared-memory loads
+// instead of R - 1.
+template <int R>
+__device__ __forceinline__ void twiddle_powers(const float2* twk, bool inv, float2 (&w)[16]) {
+  float2 w1 = twk[1], w4 = twk[4];
+  float2 w8, w12;
+  if constexpr (R == 16) {
+    w8 = twk[8];
+    w12 = twk[12];
+  }
+  if (inv) {  // conj of a product = product of the conjs
+    w1.y = -w1.y;
+    w4.y = -w4.y;
+    if constexpr (R == 16) {
+      w8.y = -w8.y;
+      w12.y = -w12.y;
+    }
+  }
+  const float2 w2 = make_float2(fmaf(w1.x, w1.x, -w1.y * w1.y), 2.f * w1.x * w1.y);
+  const float2 w3 = cmul(w2, w1);
+  w[1] = w1;
+  w[2] = w2;
+  w[3] = w3;
+  w[4] = w4;
+  w[5] = cmul(w4, w1);
+  w[6] = cmul(w4, w2);
+  w[7] = cmul(w4, w3);
+  if constexpr (R == 16) {
+    w[8] = w8;
+    w[9] = cmul(w8, w1);
+    w[10] = cmul(w8, w2);
+    w[11] = cmul(w8, w3);
+    w[12] = w12;
+    w[13] = cmul(w12, w1);
+    w[14] = cmul(w12, w2);
+    w[15] = cmul(w12, w3);
+  }
+}
+
+// TWR: the inter-pass twiddles from twiddle_powers (for kernels whose shared-memory queue,
+// not their arithmetic, is the limit) instead of one table load each.
+template <int P, int R, int Ns, bool INV, typename Sync, bool TWR = false>
 __device__ __forceinline__ void pass(float2 (&x)[16], const float2* in, float2* out, const float2* tw, int j, int jp,
                                      Sync sync_in, bool do_sync_out) {
   constexpr int T = P / 16, NB = 16 / R, STRIDE = P / R;
@@ -108,11 +152,18 @@ __device__ __forceinline__ void pass(float2 (&x)[16], const float2* in, float2* 
 #pragma unroll
     for (int q = 0; q < NB; ++q) {
       const float2* twk = tw + (Ns - 16) + ((j + q * T) & (Ns - 1)) * (R - 1) - 1;
+      if constexpr (TWR && (R == 16 || R == 8)) {
+        float2 w[16];
+        twiddle_powers<R>(twk, INV, w);
 #pragma unroll
-      for (int r = 1; r < R; ++r) {
-        float2 w = twk[r];
-        if (INV) w.y = -w.y;
-        v[q * R + r] = cmul(v[q * R + r], w);
+        for (int r = 1; r < R; ++r) v[q * R + r] = cmul(v[q * R + r], w[r]);
+      } else {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          float2 w = twk[r];
+          if (INV) w.y = -w.y;
+          v[q * R + r] = cmul(v[q * R + r], w);
+        }
       }
     }
   }
@@ -170,19 +221,19 @@ __device__ __forceinline__ void group_fft_db(float2 (&x)[16], float2* buf0, floa
 
 // Single-buffer variant: a barrier before every exchange read and write (for kernels whose
 // buffer aliases other data).
-template <int P, int Ns, bool INV, typename Sync>
+template <int P, int Ns, bool INV, typename Sync, bool TWR>
 __device__ __forceinline__ void stockham_sb(float2 (&x)[16], float2* buf, const float2* tw, int j, int jp,
                                             Sync sync) {
   constexpr int rem = P / Ns;
   constexpr int R = (rem % 16 == 0) ? 16 : rem;
-  pass<P, R, Ns, INV, Sync>(x, buf, buf, tw, j, jp, sync, true);
-  if constexpr (Ns * R < P) stockham_sb<P, Ns * R, INV, Sync>(x, buf, tw, j, jp, sync);
+  pass<P, R, Ns, INV, Sync, TWR>(x, buf, buf, tw, j, jp, sync, true);
+  if constexpr (Ns * R < P) stockham_sb<P, Ns * R, INV, Sync, TWR>(x, buf, tw, j, jp, sync);
 }
 
-template <int P, bool INV, typename Sync>
+template <int P, bool INV, typename Sync, bool TWR = false>
 __device__ __forceinline__ void group_fft_sb(float2 (&x)[16], float2* buf, const float2* tw, int j, Sync sync) {
   static_assert(P >= 256 && (P & (P - 1)) == 0, "16-value FFT: P >= 256, a power of two");
-  stockham_sb<P, 1, INV, Sync>(x, buf, tw, j, pad(j), sync);
+  stockham_sb<P, 1, INV, Sync, TWR>(x, buf, tw, j, pad(j), sync);
 }
 
 }  // namespace fft16

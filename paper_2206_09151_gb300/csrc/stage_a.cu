@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(rows16_threads<P>(), 2) k_rows_inv16(const flo
   }
   __syncthreads();  // every group has read its rows: the tile is free for the exchange buffers
   const fft::GroupSync gsync{1 + g, TT};
-  fft16::group_fft_sb<P, true>(x, buf, tw, j, gsync);
+  fft16::group_fft_sb<P, true, fft::GroupSync, true>(x, buf, tw, j, gsync);
   // rows v0 (real part) and v0 + 1 (imaginary part) at u = j + s*TT.  The tap pair of column
   // cc = j + s*TT is (Y[cc - 1], Y[cc]): the left value comes from lane l - 1 by a warp
   // shuffle; lane 0 takes the last lane of the group's previous warp (same s), and thread 0
