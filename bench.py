@@ -88,6 +88,14 @@ KERNEL_BOUND = {"k_rows_fwd": "hbm", "k_cols": "alu (FP32)", "k_rows_inv": "l1/s
 ISSUE_PEAK = 152 * 4 * 2.07e9  # warp instructions per second
 
 
+def ncu_traffic(kernel: str, workload: str, stack: str, filt: str):
+    """The captured entry for this kernel and workload, or None.  The stage-A captures are of
+    the Tikhonov filter's kernels; another filter is another kernel instantiation."""
+    if kernel != "k_backproject" and filt != "tikhonov":
+        return None
+    return NCU_TRAFFIC.get((kernel, workload, stack))
+
+
 def _src_hash(name: str) -> str:
     p = os.path.join(ROOT, "paper_2206_09151_gb300", "csrc", name)
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
@@ -207,6 +215,9 @@ def oracle_sample(cfg, images_np, dirs, mlp=None, voxels=None, workers: int = 1,
     kw = dict(lam=cfg["lam"], delta=cfg["delta"], defocus=cfg["defocus"][dirs], nz_layers=cfg["nz_layers"],
               grid=cfg["grid"], sigma=cfg["sigma"], cs=cfg["cs"], voxels=voxels, workers=workers,
               density=cfg.get("ramp", "single_axis") == "density")
+    if cfg.get("filter") == "pair":
+        return O.recon(images_np[dirs], cfg["rot"][dirs], eps=cfg["eps"], filt=O.FILTER_PAIR,
+                       layer_interp=O.LAYER_LINEAR if layer_interp == "linear" else O.LAYER_NEAREST, **kw)
     if mlp is not None:
         return O.learned.recon_learned(images_np[dirs], cfg["rot"][dirs], mlp[0].astype(np.float64), nsr=mlp[1],
                                        views=mlp[2],
@@ -362,12 +373,18 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     cfg = workload(args.workload, rank, args.dirs)
+    if args.filter == "pair":
+        # the opposite-pair form needs every view's opposite: the same number of single-axis
+        # views spread over 360 degrees instead of 180
+        from paper_2206_09151_gb300 import phantoms as ph
+        cfg["rot"] = ph.single_axis_rotations(cfg["n_dir"], span=2 * np.pi)
+        cfg["filter"] = "pair"
     images = make_images(cfg, dev)
     torch.cuda.synchronize()
     V = int(np.prod(cfg["grid"]))
     D = cfg["n_dir"]
     U = V * D
-    filt_kw = {}
+    filt_kw = {"filter": "pair"} if args.filter == "pair" else {}
     mlp = None
     if args.filter == "mlp":
         # the trained regulariser; its per-view eps divided by the D views the volume averages
@@ -449,7 +466,7 @@ def run_ours(args):
     for q, name in enumerate(KERNELS):
         per_launch_ms = kern_ms[q] / max(kern_n[q], 1)
         gbs = algo[q] / (kern_ms[q] / args.steps / 1e3) / 1e9 if kern_ms[q] > 0 else None
-        tr = NCU_TRAFFIC.get((name, args.workload, args.stack))
+        tr = ncu_traffic(name, args.workload, args.stack, args.filter)
         src = bp_src if q == 3 else "stage_a.cu"
         valid = tr is not None and tr["src"] == _src_hash(src)
         kernels[name] = {"launches": kern_n[q], "ms_per_launch": per_launch_ms,
@@ -473,8 +490,7 @@ def run_ours(args):
     dom = max(range(4), key=lambda q: kern_ms[q])
     dom_name = KERNELS[dom]
     src = bp_src if dom == 3 else "stage_a.cu"
-    key = (dom_name, args.workload, args.stack)
-    tr = NCU_TRAFFIC.get(key)
+    tr = ncu_traffic(dom_name, args.workload, args.stack, args.filter)
     traffic = tr["bytes_per_launch"] if tr and tr["src"] == _src_hash(src) else None
     launches = max(kern_n[dom], 1)
     common = {"kernel": dom_name, "traffic": traffic,
@@ -500,7 +516,9 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": args.stack, "data": "synthetic",
-            "config": {"workload": WORKLOAD_TEXT[args.workload] + (f" [first {D} directions only]" if args.dirs else ""),
+            "config": {"workload": WORKLOAD_TEXT[args.workload] + (f" [first {D} directions only]" if args.dirs else "")
+                       + (" [the views spread over 360 degrees for the opposite-pair filter]"
+                          if args.filter == "pair" else ""),
                        "stack": args.stack, "filter": args.filter, "dir_block": db,
                        "stage_block": r.stage_block, "bp_kernel": args.bp_kernel,
                        "bp_kernel_used": r.bp_kernel_used, "layer_interp": args.layer_interp,
@@ -847,9 +865,10 @@ def main():
                     help="slab (the default) is the largest single-GPU workload")
     ap.add_argument("--stack", choices=["f32", "bf16"], default=None,
                     help="layer-stack precision (default: the workload's, f32 for mid/small, bf16 otherwise)")
-    ap.add_argument("--filter", choices=["tikhonov", "mlp"], default="tikhonov",
+    ap.add_argument("--filter", choices=["tikhonov", "mlp", "pair"], default="tikhonov",
                     help="mlp: the trained learned regulariser (data/regulariser.npz), reported beside the "
-                         "analytic one")
+                         "analytic one; pair: the opposite-pair form of Eq. 10/11 on a single-axis workload, its "
+                         "views spread over 360 degrees")
     ap.add_argument("--dir-block", type=int, default=0)
     ap.add_argument("--stage-block", type=int, default=0, help="directions per FFT/filter sub-block, 0 = auto")
     ap.add_argument("--bp-kernel", choices=["auto", "direct", "staged", "tma"], default="auto",
@@ -868,6 +887,9 @@ def main():
         args.stack = DEFAULT_STACK[args.workload]
     if args.layer_interp == "linear" and args.filter == "mlp":
         ap.error("--layer-interp linear is measured with the analytic filter")
+    if args.filter == "pair" and (args.workload not in ("mid", "small") or args.form != "layered"
+                                  or args.impl != "ours"):
+        ap.error("--filter pair runs the layered form on a single-axis workload (mid or small)")
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch":
