@@ -59,3 +59,18 @@ def test_work_counts_follow_the_shapes():
     assert np.allclose(b, [3 * (120 * 256 * 256 * 4 + spec), 3 * (spec + inter), 3 * (inter + stack),
                            3 * stack + V * 4 + 2 * V * 8])
     assert bench.aggregate_rate(6.0e9, 10, 2, 100.0) == 2 * 6.0e9 * 10 / 0.1
+
+
+def test_pair_filter_option_is_refused_outside_single_axis_layered_runs():
+    """The opposite-pair filter needs every view's opposite: only the single-axis workloads
+    (views respread over 360 degrees) in the layered form take it."""
+    import bench
+    for extra in (["--workload", "slab"], ["--workload", "learned"], ["--workload", "mid", "--form", "swap"],
+                  ["--workload", "mid", "--impl", "reference"]):
+        out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--filter", "pair"] + extra,
+                             capture_output=True, text=True, timeout=120, cwd=ROOT)
+        assert out.returncode == 2 and "--filter pair" in out.stderr, (extra, out.stderr[-500:])
+    # the stage-A traffic captures are of the Tikhonov kernels only
+    assert bench.ncu_traffic("k_cols", "mid", "f32", "pair") is None
+    assert bench.ncu_traffic("k_cols", "mid", "f32", "tikhonov") is not None
+    assert bench.ncu_traffic("k_backproject", "mid", "f32", "pair") is not None
