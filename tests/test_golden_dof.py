@@ -57,7 +57,9 @@ def test_electron_example_dof_is_about_8_angstrom_and_needs_layers(lib):
     e = _examples()["electron_200kev"]
     n = int(round(e["thickness"] / e["delta"]))  # 112 voxels of 0.625 Angstrom
     beam_z = np.eye(3)[None]
-    p = _plan(beam_z, n, e["lam"], e["delta"], 3.25e-8, 1)  # image planes 300-350 Angstrom away
+    # image planes 300-350 Angstrom from the cube's z = 0 face, i.e. 200-250 Angstrom downstream of
+    # the rotation centre, from which R is measured here (the DOF does not depend on R)
+    p = _plan(beam_z, n, e["lam"], e["delta"], 2.25e-8, 1)
     h, dof = _abi.recon_plan_dof(p)
     assert dof == pytest.approx(e["delta"] ** 2 / (2 * e["lam"]), rel=1e-12)
     assert abs(dof - e["dof_printed"]) <= e["rel_tol"] * e["dof_printed"]
@@ -66,7 +68,7 @@ def test_electron_example_dof_is_about_8_angstrom_and_needs_layers(lib):
     _abi.recon_destroy(p)
     nz = _abi.recon_layers_for_dof(beam_z, (n, n, n), e["lam"], e["delta"])
     assert nz == math.ceil(e["thickness"] / dof) == 9
-    p = _plan(beam_z, n, e["lam"], e["delta"], 3.25e-8, nz)
+    p = _plan(beam_z, n, e["lam"], e["delta"], 2.25e-8, nz)
     assert _abi.recon_plan_warning(p) == ""
     _abi.recon_destroy(p)
     # the paper's scan: orientations uniform on the sphere; any view sees at least the cube's side
