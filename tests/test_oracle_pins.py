@@ -550,8 +550,13 @@ def test_first_born_and_multislice_images_agree_to_first_order():
     import torch
     n, rot = 32, ph.single_axis_rotations(8)
     R = np.full(8, -24e-9)
-    for amp, lo, hi in ((2e-6, 0.0, 0.01), (2e-4, 0.05, np.inf)):  # measured 0.2 % and 12.7 %
-        phan = ph.ball_phantom((n, n, n), 6, seed=3, r_range=(2.5, 4.0), delta_range=(amp / 2, amp))
+    cases = []
+    for amp, lo, hi in ((2e-6, 0.0, 0.01), (2e-4, 0.05, np.inf)):  # spheres: 0.2 % and 12.7 % measured
+        cases.append((ph.ball_phantom((n, n, n), 6, seed=3, r_range=(2.5, 4.0), delta_range=(amp / 2, amp)), lo, hi))
+    for amp, lo, hi in ((2e-6, 0.0, 0.01), (2e-4, 0.05, np.inf)):  # Gaussian blobs: 0.5 % and 59 %
+        cases.append((ph.blob_phantom((n, n, n), 10, seed=4, s_vox=1.5, amp_unit=amp), lo, hi))
+    for phan, lo, hi in cases:
+        amp = float(phan.amp.max())
         born = ph.born_images(phan, rot, n, n, 1e-9, 8e-11, R, 0.3)
         ms = ph.multislice_images(phan, rot, n, n, 1e-9, 8e-11, R, 0.3, n_slabs=64, dtype=torch.float64).numpy()
         d = np.linalg.norm(np.log(born) - np.log(ms)) / np.linalg.norm(np.log(ms))
