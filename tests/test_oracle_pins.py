@@ -620,6 +620,22 @@ def test_density_weighted_fbp_of_a_ball_from_random_directions():
     assert np.sqrt(np.mean((vol[inner] - 1.0) ** 2)) < 0.04
 
 
+def test_density_weighting_is_invariant_to_repeating_the_scan():
+    """S counts every view's samples, so recording each view twice doubles S (and the band
+    mean that sets eps_S) and halves every weight: the reconstruction is unchanged.  A
+    weight that is not the inverse of the gridded density would change with the repeat."""
+    n, D = 24, 10
+    grid = (n, n, n)
+    ball = ph.Phantom("ball", np.array([[1.0, -2.0, 2.5]]), np.array([6.0]), np.array([1.0]))
+    rot = ph.cone_rotations(D, 70.0, seed=11)
+    proj = ph.ball_projections(ball, rot, n, n)
+    kw = dict(lam=1.0, delta=1.0, nz_layers=1, grid=grid, filt=O.FILTER_OFF, input_mode=O.INPUT_CONTRAST,
+              density=True)
+    once = O.recon(proj, rot, defocus=np.zeros(D), **kw)
+    twice = O.recon(np.concatenate([proj, proj]), np.concatenate([rot, rot]), defocus=np.zeros(2 * D), **kw)
+    assert np.linalg.norm(twice - once) <= 1e-10 * np.linalg.norm(once)
+
+
 def test_process_pool_sums_the_same_terms():
     """The spawned pool (used for the full-size parity cases) splits the directions over
     workers: the same terms summed in another order."""
